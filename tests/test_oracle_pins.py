@@ -1,0 +1,571 @@
+"""Pins for the FP64 oracle: each test checks an oracle routine against something
+other than the oracle itself (closed forms, finite differences, the information
+form of the update, a global least-squares fit, brute force, statistics on
+simulated truth).  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1711_06571_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+KAPPA = 0.299792458e-2
+BZ = 3.8
+
+
+def _barrel(R, x_x0=0.02):
+    return dict(kind=0, pos=R, half_or_rin=30 + 1.6 * R, r_out=0.0, x_x0=x_x0, sig_n=0.01, sig_rphi=0.01,
+                sig_3=0.1)
+
+
+def _disk(Z, x_x0=0.02):
+    return dict(kind=1, pos=Z, half_or_rin=abs(Z) / 7 + 5, r_out=100.0, x_x0=x_x0, sig_n=0.01, sig_rphi=0.01,
+                sig_3=0.1)
+
+
+# ---------------------------------------------------------------------- Highland (Sec. 2)
+
+def test_highland_pdg_values(oracle_mod):
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "highland_pdg.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for p, t, th0 in rows:
+        got = oracle_mod.highland(float(p), synth.PION_MASS, float(t))
+        assert got == pytest.approx(float(th0), rel=2e-7)
+
+
+def test_highland_scaling_invariants(oracle_mod):
+    # massless: beta = 1, so theta0 is exactly proportional to 1/p
+    a = oracle_mod.highland(1.0, 0.0, 0.02)
+    b = oracle_mod.highland(4.0, 0.0, 0.02)
+    assert a / b == pytest.approx(4.0, rel=1e-14)
+    # at beta = 1 and t = 1 the log term vanishes: theta0 = 13.6 MeV / p
+    assert oracle_mod.highland(2.0, 0.0, 1.0) == pytest.approx(0.0136 / 2.0, rel=1e-14)
+    # infinite momentum: no scattering
+    assert oracle_mod.highland(math.inf, 0.14, 0.02) == 0.0
+
+
+def test_ms_noise_placement(oracle_mod):
+    # barrel crossed at normal incidence, theta = 60 deg: t = x/X0 / sin(theta)
+    th = math.pi / 3
+    st = np.array([10.0, 0.0, 0.0, 1.0, 0.0, th])
+    rc, P = oracle_mod.ms_noise(st, 0.13957039, _barrel(10.0), np.zeros((6, 6)))
+    p = 1.0 / math.sin(th)
+    th0 = oracle_mod.highland(p, 0.13957039, 0.02 / math.sin(th))
+    expect = np.zeros((6, 6))
+    expect[5, 5] = th0 ** 2
+    expect[4, 4] = th0 ** 2 / math.sin(th) ** 2
+    assert rc == 0
+    np.testing.assert_allclose(P, expect, rtol=1e-13, atol=0)
+    # disk: incidence from cos(theta)
+    st = np.array([10.0, 0.0, 50.0, 1.0, 0.0, 0.3])
+    rc, P = oracle_mod.ms_noise(st, 0.13957039, _disk(50.0), np.zeros((6, 6)))
+    th0 = oracle_mod.highland(1.0 / math.sin(0.3), 0.13957039, 0.02 / math.cos(0.3))
+    assert P[5, 5] == pytest.approx(th0 ** 2, rel=1e-13)
+    # grazing guard
+    st = np.array([10.0, 0.0, 0.0, 1.0, math.pi / 2, math.pi / 2])
+    rc, P = oracle_mod.ms_noise(st, 0.13957039, _barrel(10.0), np.zeros((6, 6)))
+    assert rc == oracle_mod.ST_GRAZING
+    th0 = oracle_mod.highland(1.0, 0.13957039, 0.02 / 0.05)
+    assert P[5, 5] == pytest.approx(th0 ** 2, rel=1e-13)
+
+
+# ---------------------------------------------------------------------- helix (Sec. 3, Sec. 4.1)
+
+@pytest.mark.parametrize("q", [-1, 1])
+@pytest.mark.parametrize("pt", [0.5, 1.3, 10.0])
+def test_barrel_crossing_from_origin_closed_form(oracle_mod, q, pt):
+    # a helix from the origin crosses r = R after s = 2 rho asin(R / (2 rho)), at azimuth
+    # phi0 + c s / 2 (the chord direction), with direction phi0 + c s
+    phi0, th = 0.7, 1.1
+    st = np.array([0.0, 0.0, 0.0, 1.0 / pt, phi0, th])
+    c = -q * KAPPA * BZ / pt
+    rho = 1.0 / abs(c)
+    for R in (4.0, 22.0, 58.0):
+        if R > 2 * rho:
+            continue
+        rc, out, _ = oracle_mod.propagate(st, q, BZ, _barrel(R), want_jac=False)
+        s = 2 * rho * math.asin(R / (2 * rho))
+        assert rc == 0
+        assert out[0] == pytest.approx(R * math.cos(phi0 + c * s / 2), abs=1e-11)
+        assert out[1] == pytest.approx(R * math.sin(phi0 + c * s / 2), abs=1e-11)
+        assert out[2] == pytest.approx(s / math.tan(th), abs=1e-11)
+        assert out[4] == pytest.approx(phi0 + c * s, abs=1e-13)
+
+
+def test_barrel_unreachable(oracle_mod):
+    # pT = 0.5 GeV: rho = 43.9 cm, the circle from the origin never gets beyond 2 rho = 87.8 cm
+    st = np.array([0.0, 0.0, 0.0, 2.0, 0.3, 1.2])
+    rc, _, _ = oracle_mod.propagate(st, 1, BZ, _barrel(94.0), want_jac=False)
+    assert rc == oracle_mod.ST_NO_INTERSECT
+    rc, _, _ = oracle_mod.propagate(st, 1, BZ, _barrel(82.0), want_jac=False)
+    assert rc == 0
+
+
+def test_disk_crossing_closed_form(oracle_mod):
+    q, pt, phi0, th = 1, 0.8, -2.0, 0.4
+    st = np.array([0.0, 0.0, 0.0, 1.0 / pt, phi0, th])
+    c = -q * KAPPA * BZ / pt
+    Z = 60.0
+    rc, out, _ = oracle_mod.propagate(st, q, BZ, _disk(Z), want_jac=False)
+    s = Z * math.tan(th)
+    assert rc == 0
+    assert out[2] == Z
+    assert math.hypot(out[0], out[1]) == pytest.approx(2 / abs(c) * abs(math.sin(c * s / 2)), rel=1e-12)
+    assert out[4] == pytest.approx(phi0 + c * s, abs=1e-13)
+    # a disk behind the state is reached backwards, s = -Z tan(theta) < 0
+    rc, out, _ = oracle_mod.propagate(st, q, BZ, _disk(-Z), want_jac=False)
+    assert rc == 0 and out[2] == -Z
+    assert out[4] == pytest.approx(phi0 - c * s, abs=1e-13)
+    # theta = pi/2 (up to rounding) never meets a disk
+    rc, _, _ = oracle_mod.propagate(np.array([0, 0, 0, 1.0, 0.1, math.pi / 2]), q, BZ, _disk(Z), want_jac=False)
+    assert rc == oracle_mod.ST_NO_INTERSECT
+
+
+def test_barrel_backward_when_outside(oracle_mod):
+    # a state just outside r = R (pulled there by a measurement) goes back to the
+    # crossing behind it, not around the whole circle
+    q, pt, phi0, th = -1, 2.0, 0.3, 1.2
+    c = -q * KAPPA * BZ / pt
+    rho = 1 / abs(c)
+    st0 = np.array([0.0, 0.0, 0.0, 1 / pt, phi0, th])
+    rc, a, _ = oracle_mod.propagate(st0, q, BZ, _barrel(30.0), want_jac=False)
+    rc2, b, _ = oracle_mod.propagate(a, q, BZ, _barrel(29.9), want_jac=False)
+    s_ab = 2 * rho * math.asin(29.9 / (2 * rho)) - 2 * rho * math.asin(30.0 / (2 * rho))
+    assert rc == 0 and rc2 == 0
+    assert math.hypot(b[0], b[1]) == pytest.approx(29.9, abs=1e-11)
+    assert b[2] - a[2] == pytest.approx(s_ab / math.tan(th), abs=1e-11)
+    # straight line, same rule
+    st = np.array([10.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    rc, o, _ = oracle_mod.propagate(st, 1, 0.0, _barrel(9.0), want_jac=False)
+    assert rc == 0 and o[0] == pytest.approx(9.0, abs=1e-13)
+
+
+def test_seed_hit_choice(oracle_mod):
+    # barrel layers 4 cm apart: hits 0, 1, 2
+    x = np.array([4, 8, 12, 16], np.float32)
+    assert oracle_mod.seed_hits(x, np.zeros(4, np.float32))[1:] == (1, 2)
+    # a disk/barrel pair 0.03 cm apart is skipped
+    x = np.array([4, 9.97, 10.0, 16, 22], np.float32)
+    assert oracle_mod.seed_hits(x, np.zeros(5, np.float32))[1:] == (1, 3)
+    x = np.array([4, 5.0, 7.0, 7.5, 9.5], np.float32)
+    assert oracle_mod.seed_hits(x, np.zeros(5, np.float32))[1:] == (2, 4)
+    # nothing far enough: fall back to 1, 2
+    x = np.array([4, 4.5, 5.0], np.float32)
+    assert oracle_mod.seed_hits(x, np.zeros(3, np.float32))[1:] == (1, 2)
+
+
+def test_helix_straight_line_limit(oracle_mod):
+    st = np.array([1.0, -2.0, 3.0, 0.0, 0.4, 1.0])
+    out = oracle_mod.helix_at(st, 0.0, 7.5)
+    np.testing.assert_allclose(out[:3], [1 + 7.5 * math.cos(0.4), -2 + 7.5 * math.sin(0.4), 3 + 7.5 / math.tan(1.0)],
+                               atol=1e-13)
+    # small curvature: x = x0 + s cos(phi) - c s^2/2 sin(phi) + O(c^2 s^3), same for y
+    for c in (1e-6, -1e-6, 3e-5):
+        a = oracle_mod.helix_at(st, c, 7.5)
+        ex = 1 + 7.5 * math.cos(0.4) - c * 7.5 ** 2 / 2 * math.sin(0.4)
+        ey = -2 + 7.5 * math.sin(0.4) + c * 7.5 ** 2 / 2 * math.cos(0.4)
+        np.testing.assert_allclose(a[:2], [ex, ey], atol=5 * c * c * 7.5 ** 3)
+    # the chord form equals the textbook form (sin phi(s) - sin phi) / c away from c = 0
+    c = 0.02
+    a = oracle_mod.helix_at(st, c, 7.5)
+    np.testing.assert_allclose(a[:2], [1 + (math.sin(0.4 + c * 7.5) - math.sin(0.4)) / c,
+                                       -2 - (math.cos(0.4 + c * 7.5) - math.cos(0.4)) / c], atol=1e-12)
+
+
+def test_noise_free_propagation_matches_simulated_truth(oracle_mod):
+    # the generator computes crossings from angles about the helix centre, independently
+    for gname in ("barrel17", "lids"):
+        g = synth.geometry(gname)
+        tk = synth.gen_tracks(g, 300, 11, eta_max=2.5 if gname == "lids" else 1.0, ms_on=False, smear=False,
+                              keep_truth=True)
+        off = tk["offsets"]
+        q = tk["truth_q"]
+        worst = 0.0
+        for t in range(tk["n"]):
+            o0, o1 = off[t], off[t + 1]
+            st = tk["truth"][o0].copy()
+            for k in range(o0 + 1, o1):
+                rc, st, _ = oracle_mod.propagate(st, int(q[t]), g["bz"], g["surfaces"][tk["layer"][k]],
+                                                 want_jac=False)
+                assert rc == 0
+                d = np.abs(st[:3] - tk["truth"][k][:3]).max()
+                worst = max(worst, d)
+                np.testing.assert_allclose(st[3:], tk["truth"][k][3:], atol=1e-11)
+        assert worst < 1e-9, (gname, worst)
+
+
+# ---------------------------------------------------------------------- Jacobian (Sec. 2.1)
+
+@pytest.mark.parametrize("case", range(8))
+def test_jacobian_vs_central_differences(oracle_mod, case):
+    rng = np.random.default_rng(100 + case)
+    q = int(rng.choice([-1, 1]))
+    pt = float(np.exp(rng.uniform(math.log(0.6), math.log(10))))
+    r0 = rng.uniform(5, 30)
+    a0 = rng.uniform(-math.pi, math.pi)
+    st = np.array([r0 * math.cos(a0), r0 * math.sin(a0), rng.uniform(-10, 10), 1.0 / pt,
+                   a0 + rng.uniform(-0.3, 0.3), rng.uniform(0.6, 2.5)])
+    surf = _barrel(r0 + rng.uniform(3, 12)) if case < 5 else _disk(
+        float(np.sign(math.cos(st[5])) * (abs(st[2]) + rng.uniform(5, 20))))
+    rc, out, J = oracle_mod.propagate(st, q, BZ, surf)
+    assert rc == 0
+    Jn = np.zeros((6, 6))
+    for j in range(6):
+        h = 1e-6 * max(1.0, abs(st[j]))
+        a = st.copy()
+        b = st.copy()
+        a[j] += h
+        b[j] -= h
+        _, oa, _ = oracle_mod.propagate(a, q, BZ, surf, want_jac=False)
+        _, ob, _ = oracle_mod.propagate(b, q, BZ, surf, want_jac=False)
+        d = oa - ob
+        d[4] = (d[4] + math.pi) % (2 * math.pi) - math.pi
+        Jn[:, j] = d / (2 * h)
+    scale = np.maximum(np.abs(Jn), 1.0)
+    assert np.max(np.abs(J - Jn) / scale) < 1e-6
+
+
+# ---------------------------------------------------------------------- update (Sec. 4.1)
+
+def test_update_equals_information_form(oracle_mod):
+    # textbook information form: P+ = (P^-1 + H^T R^-1 H)^-1, x+ = P+ (P^-1 x + H^T R^-1 m),
+    # chi2 = r^T (H P H^T + R)^-1 r
+    rng = np.random.default_rng(5)
+    H = np.hstack([np.eye(3), np.zeros((3, 3))])
+    for _ in range(20):
+        A = rng.normal(size=(6, 6))
+        P = A @ A.T * 0.01 + np.eye(6) * 1e-3
+        B = rng.normal(size=(3, 3))
+        R = B @ B.T * 1e-4 + np.eye(3) * 1e-5
+        x = rng.normal(size=6)
+        x[4] = 0.3
+        m = x[:3] + rng.normal(size=3) * 0.05
+        rc, xo, Po, chi2 = oracle_mod.update(x, P, m, R)
+        Pi = np.linalg.inv(np.linalg.inv(P) + H.T @ np.linalg.inv(R) @ H)
+        xi = Pi @ (np.linalg.solve(P, x) + H.T @ np.linalg.solve(R, m))
+        r = m - x[:3]
+        assert rc == 0
+        np.testing.assert_allclose(Po, Pi, rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(xo, xi, rtol=1e-9, atol=1e-12)
+        assert chi2 == pytest.approx(r @ np.linalg.solve(P[:3, :3] + R, r), rel=1e-10)
+
+
+def test_meas_cov_frames(oracle_mod):
+    # barrel: radial / phi / z resolutions along the hit's own axes
+    s = dict(kind=0, pos=10.0, half_or_rin=50, r_out=0, x_x0=0.02, sig_n=0.03, sig_rphi=0.01, sig_3=0.1)
+    a = 0.9
+    R = oracle_mod.meas_cov(s, np.array([10 * math.cos(a), 10 * math.sin(a), 1.0]))
+    er = np.array([math.cos(a), math.sin(a), 0])
+    ep = np.array([-math.sin(a), math.cos(a), 0])
+    assert er @ R @ er == pytest.approx(0.03 ** 2, rel=1e-12)
+    assert ep @ R @ ep == pytest.approx(0.01 ** 2, rel=1e-12)
+    assert R[2, 2] == pytest.approx(0.01, rel=1e-12)
+    assert abs(er @ R @ ep) < 1e-18
+    # disk: z is the normal, r the third axis
+    s = dict(kind=1, pos=50.0, half_or_rin=10, r_out=100, x_x0=0.02, sig_n=0.01, sig_rphi=0.02, sig_3=0.1)
+    R = oracle_mod.meas_cov(s, np.array([20 * math.cos(a), 20 * math.sin(a), 50.0]))
+    assert R[2, 2] == pytest.approx(1e-4, rel=1e-12)
+    assert er @ R @ er == pytest.approx(0.01, rel=1e-12)
+    assert ep @ R @ ep == pytest.approx(4e-4, rel=1e-12)
+
+
+def test_kf_equals_global_least_squares_linear_model(oracle_mod):
+    """Scattering off, propagation linearised about the true trajectory: the filter's
+    final state, covariance and summed chi2 equal the batch generalised least-squares
+    solution with the Gaussian seed prior (the Kalman/GLS identity)."""
+    g = synth.geometry("barrel17")
+    ref = synth.gen_tracks(g, 6, 21, ms_on=False, smear=False, keep_truth=True)
+    noisy = synth.gen_tracks(g, 6, 21, ms_on=False, smear=True, keep_truth=True)
+    assert np.array_equal(ref["offsets"], noisy["offsets"])
+    H = np.hstack([np.eye(3), np.zeros((3, 3))])
+    for t in range(ref["n"]):
+        o0, o1 = ref["offsets"][t], ref["offsets"][t + 1]
+        if o1 - o0 < 6:
+            continue
+        o1 = o0 + 6
+        q = int(ref["truth_q"][t])
+        trj = ref["truth"][o0:o1]
+        lay = ref["layer"][o0:o1]
+        hx, hy, hz = noisy["x"][o0:o1], noisy["y"][o0:o1], noisy["z"][o0:o1]
+        seed = trj[0] + np.array([0.02, -0.01, 0.05, 0.01, 0.002, -0.003])
+        P0 = 0.5
+        res = oracle_mod.fit_one(g, lay, hx, hy, hz, seed, q, seed_cov=P0, ms_on=False, lin_ref=trj)
+        assert res["status"] == 0
+        # batch model: x_k = ref_k + Phi_k (x_0 - ref_0)
+        Phi = [np.eye(6)]
+        for k in range(1, 6):
+            _, _, J = oracle_mod.propagate(trj[k - 1], q, g["bz"], g["surfaces"][lay[k]])
+            Phi.append(J @ Phi[-1])
+        Ainf = np.eye(6) / P0
+        b = (seed - trj[0]) / P0
+        for k in range(6):
+            m = np.array([hx[k], hy[k], hz[k]], float)
+            R = oracle_mod.meas_cov(g["surfaces"][lay[k]], m)
+            Ri = np.linalg.inv(R)
+            Hk = H @ Phi[k]
+            Ainf += Hk.T @ Ri @ Hk
+            b += Hk.T @ Ri @ (m - trj[k][:3])
+        cov0 = np.linalg.inv(Ainf)
+        d0 = cov0 @ b
+        xN = trj[5] + Phi[5] @ d0
+        PN = Phi[5] @ cov0 @ Phi[5].T
+        chi2 = (d0 - (seed - trj[0])) @ (d0 - (seed - trj[0])) / P0
+        for k in range(6):
+            m = np.array([hx[k], hy[k], hz[k]], float)
+            R = oracle_mod.meas_cov(g["surfaces"][lay[k]], m)
+            rk = m - trj[k][:3] - H @ Phi[k] @ d0
+            chi2 += rk @ np.linalg.solve(R, rk)
+        sig = np.sqrt(np.diag(PN))
+        assert np.max(np.abs(res["state"] - xN) / sig) < 1e-6
+        np.testing.assert_allclose(res["cov"], PN, rtol=1e-6, atol=1e-12 * np.abs(PN).max())
+        assert res["chi2"] == pytest.approx(chi2, rel=1e-7)
+
+
+# ---------------------------------------------------------------------- seed (Sec. 2)
+
+@pytest.mark.parametrize("q", [-1, 1])
+def test_seed_on_exact_helix(oracle_mod, q):
+    pt, phi0, th = 1.7, -2.9, 2.0
+    c = -q * KAPPA * BZ / pt
+    rho = 1 / abs(c)
+    hits = []
+    for R in (4.0, 8.0, 12.0):
+        s = 2 * rho * math.asin(R / (2 * rho))
+        hits.append(np.array([R * math.cos(phi0 + c * s / 2), R * math.sin(phi0 + c * s / 2), s / math.tan(th)]))
+    st, qs = oracle_mod.seed(hits[0], hits[1], hits[2], BZ)
+    s1 = 2 * rho * math.asin(4.0 / (2 * rho))
+    assert qs == q
+    np.testing.assert_allclose(st[:3], hits[0], atol=1e-14)
+    assert st[3] == pytest.approx(1 / pt, rel=1e-10)
+    d = (st[4] - (phi0 + c * s1) + math.pi) % (2 * math.pi) - math.pi
+    assert abs(d) < 1e-11
+    assert st[5] == pytest.approx(th, abs=1e-11)
+
+
+def test_seed_collinear(oracle_mod):
+    st, q = oracle_mod.seed(np.array([1.0, 1, 0]), np.array([2.0, 2, 1]), np.array([3.0, 3, 2]), BZ)
+    assert q == 1 and st[3] == 0.0
+    assert st[4] == pytest.approx(math.pi / 4, abs=1e-15)
+    assert st[5] == pytest.approx(math.atan2(2 * math.sqrt(2), 2), abs=1e-15)
+
+
+# ---------------------------------------------------------------------- full fit (Sec. 2)
+
+def test_noise_free_fit_recovers_truth(oracle_mod):
+    g = synth.geometry("barrel10")
+    tk = synth.gen_tracks(g, 200, 31, ms_on=False, smear=False, keep_truth=True)
+    r = oracle_mod.fit(g, tk, ms_on=False)
+    last = tk["offsets"][1:] - 1
+    tru = tk["truth"][last]
+    assert np.all(r["status"] == 0)
+    sig = np.sqrt(np.diagonal(r["cov"], axis1=1, axis2=2))
+    d = r["state"] - tru
+    d[:, 3] = r["q"] * r["state"][:, 3] - tk["truth_q"] * tru[:, 3]
+    # the only noise left is the float32 rounding of the hit coordinates (~4e-6 cm)
+    assert np.max(np.abs(d) / sig) < 0.01
+    assert np.max(r["chi2"]) < 1e-3
+
+
+def test_fit_straight_line_without_field(oracle_mod):
+    g = synth.geometry("barrel10", bz=0.0)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        phi0, th = rng.uniform(-3, 3), rng.uniform(0.8, 2.3)
+        d = np.array([math.sin(th) * math.cos(phi0), math.sin(th) * math.sin(phi0), math.cos(th)])
+        R = np.array([s["pos"] for s in g["surfaces"]])
+        pts = d[None, :] * (R / math.sin(th))[:, None]
+        lay = np.arange(10, dtype=np.uint8)
+        st, q = oracle_mod.seed(pts[0], pts[1], pts[2], 0.0)
+        res = oracle_mod.fit_one(g, lay, pts[:, 0], pts[:, 1], pts[:, 2], st, q, ms_on=False)
+        assert res["status"] == 0
+        np.testing.assert_allclose(res["state"][:3], pts[-1], atol=2e-5)
+        assert res["state"][4] == pytest.approx(phi0, abs=1e-6)
+        assert res["state"][5] == pytest.approx(th, abs=1e-6)
+
+
+def test_fit_statistics_on_simulated_tracks(oracle_mod):
+    """Pulls of the five surface parameters ~ N(0,1) and chi2 ~ chi2(2N-5) on 1e5 tracks."""
+    from scipy import stats
+    g = synth.geometry("barrel10")
+    tk = synth.gen_tracks(g, 100_000, synth.BASE_SEED + 1, keep_truth=True)
+    r = oracle_mod.fit(g, tk, threads=4)
+    assert np.all(r["status"] & ~np.uint32(oracle_mod.ST_GRAZING) == 0)
+    last = tk["offsets"][1:] - 1
+    tru = tk["truth"][last]
+    st = r["state"]
+    C = r["cov"]
+    # local barrel frame at the truth point: r-phi displacement, z
+    a = np.arctan2(tru[:, 1], tru[:, 0])
+    ep = np.stack([-np.sin(a), np.cos(a)], 1)
+    drphi = np.sum((st[:, :2] - tru[:, :2]) * ep, 1)
+    srphi = np.sqrt(np.einsum("ni,nij,nj->n", ep, C[:, :2, :2], ep))
+    pulls = {
+        "rphi": drphi / srphi,
+        "z": (st[:, 2] - tru[:, 2]) / np.sqrt(C[:, 2, 2]),
+        "q/pT": (r["q"] * st[:, 3] - tk["truth_q"] * tru[:, 3]) / np.sqrt(C[:, 3, 3]),
+        "phi": ((st[:, 4] - tru[:, 4] + np.pi) % (2 * np.pi) - np.pi) / np.sqrt(C[:, 4, 4]),
+        "theta": (st[:, 5] - tru[:, 5]) / np.sqrt(C[:, 5, 5]),
+    }
+    for k, p in pulls.items():
+        assert abs(p.mean()) < 0.02, (k, p.mean())
+        assert abs(p.std() - 1.0) < 0.03, (k, p.std())
+    assert np.all(r["ndof"] == 2 * 10 - 5)
+    assert abs(np.mean(r["chi2"] / r["ndof"]) - 1.0) < 0.02
+    pv = stats.chi2.sf(r["chi2"], r["ndof"])
+    assert stats.kstest(pv[:20000], "uniform").pvalue > 1e-3
+
+
+def test_output_covariances_psd_rank5_and_symmetric(oracle_mod):
+    """The fitted covariance is symmetric positive semi-definite with exactly one null
+    direction: the fitted point lies on the last surface, so the position variance along
+    the surface normal is zero (six parameters, five degrees of freedom)."""
+    g = synth.geometry("lids")
+    tk = synth.gen_tracks(g, 3000, 41, eta_max=2.5, keep_truth=False, min_hits=4)
+    r = oracle_mod.fit(g, tk)
+    ok = r["status"] & np.uint32(oracle_mod.ST_NO_INTERSECT | oracle_mod.ST_CHOL_FAIL) == 0
+    assert ok.mean() > 0.99
+    for t in np.nonzero(ok)[0]:
+        C = r["cov"][t]
+        assert np.max(np.abs(C - C.T)) <= 1e-12 * np.abs(C).max()
+        ev = np.linalg.eigvalsh(C)
+        assert ev[0] >= -1e-12 * ev[-1]
+        assert ev[1] > 1e-9 * ev[-1]
+        # the null vector is the normal of the last surface (position block only)
+        w, V = np.linalg.eigh(C)
+        v = V[:, 0]
+        assert np.linalg.norm(v[:3]) > 0.99, (t, v)
+
+
+def test_fp64_oracle_vs_high_precision_reference(oracle_mod):
+    """Bound the oracle's own rounding error: the same filter steps in 40-digit arithmetic
+    (mpmath) give the same final state to < 1e-4 sigma."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    g = synth.geometry("barrel17")
+    tk = synth.gen_tracks(g, 3, 7, keep_truth=True)
+    r = oracle_mod.fit(g, tk)
+    for t in range(tk["n"]):
+        o0, o1 = tk["offsets"][t], tk["offsets"][t + 1]
+        q = int(r["q"][t])
+        st = mp.matrix(r["seed"][t].tolist())
+        P = mp.eye(6) * mp.mpf(10000)
+        chi = mp.mpf(0)
+        for k in range(o1 - o0):
+            sf = g["surfaces"][tk["layer"][o0 + k]]
+            stf = np.array([float(v) for v in st])
+            if k > 0:
+                _, nx, J = oracle_mod.propagate(stf, q, g["bz"], sf)
+                Jm = mp.matrix(J.tolist())
+                P = Jm * P * Jm.T
+                st = mp.matrix(nx.tolist())
+                stf = nx
+            _, Q = oracle_mod.ms_noise(stf, g["mass"], sf, np.zeros((6, 6)))
+            P = P + mp.matrix(Q.tolist())
+            hit = np.array([tk["x"][o0 + k], tk["y"][o0 + k], tk["z"][o0 + k]], float)
+            R = mp.matrix(oracle_mod.meas_cov(sf, hit).tolist())
+            rr = mp.matrix([mp.mpf(float(hit[i])) - st[i] for i in range(3)])
+            S = P[0:3, 0:3] + R
+            Si = S ** -1
+            K = P[:, 0:3] * Si
+            st = st + K * rr
+            P = P - K * P[0:3, :]
+            chi += (rr.T * Si * rr)[0]
+        ref = np.array([float(v) for v in st])
+        sig = np.sqrt(np.array([float(P[i, i]) for i in range(6)]))
+        d = (r["state"][t] - ref) / sig
+        assert np.max(np.abs(d)) < 1e-4
+        assert r["chi2"][t] == pytest.approx(float(chi), rel=1e-5)
+
+
+# ---------------------------------------------------------------------- binning (Sec. 3.1)
+
+def test_bin_key_at_bin_centres(oracle_mod):
+    Lz = 40.0
+    for j in (0, 1, 511, 512, 1000, 1023):
+        for zb in (0, 17, 63):
+            phi = -math.pi + (j + 0.5) * 2 * math.pi / 1024
+            z = -Lz + (zb + 0.5) * 2 * Lz / 64
+            key = oracle_mod.bin_key(20 * math.cos(phi), 20 * math.sin(phi), z, Lz)
+            assert key == zb * 1024 + j
+    # clamping: z beyond the layer, phi exactly pi
+    assert oracle_mod.bin_key(-20.0, 0.0, 1e3, Lz) == 63 * 1024 + 1023
+    assert oracle_mod.bin_key(-20.0, -0.0, -1e3, Lz) == 0
+
+
+def test_bin_layer_is_stable_counting_sort(oracle_mod):
+    rng = np.random.default_rng(8)
+    n = 5000
+    Lz = 30 + 1.6 * 40
+    phi = rng.uniform(-math.pi, math.pi, n)
+    # crowd some hits into a few bins to exercise stability
+    phi[:600] = 0.1
+    x = (40 * np.cos(phi)).astype(np.float32)
+    y = (40 * np.sin(phi)).astype(np.float32)
+    z = rng.uniform(-Lz - 5, Lz + 5, n).astype(np.float32)
+    z[:300] = 1.0
+    perm, offsets = oracle_mod.bin_layer(x, y, z, Lz)
+    keys = [oracle_mod.bin_key(x[i], y[i], z[i], Lz) for i in range(n)]
+    expect = sorted(range(n), key=lambda i: (keys[i], i))
+    assert list(perm) == expect
+    counts = np.bincount(keys, minlength=65536)
+    assert offsets[0] == 0 and offsets[-1] == n
+    np.testing.assert_array_equal(np.diff(offsets), counts)
+    # empty layer
+    perm, offsets = oracle_mod.bin_layer(np.zeros(0, np.float32), np.zeros(0, np.float32),
+                                         np.zeros(0, np.float32), Lz)
+    assert len(perm) == 0 and np.all(offsets == 0)
+
+
+# ---------------------------------------------------------------------- best-hit building (Sec. 2)
+
+def _binned_event(oracle_mod, g, n, seed, noise=0.2):
+    ev = synth.gen_event(g, n, seed, noise_frac=noise)
+    for ly in ev["layers"]:
+        Lz = g["surfaces"][ly["surf"]]["half_or_rin"]
+        ly["perm"], ly["offsets"] = oracle_mod.bin_layer(ly["x"], ly["y"], ly["z"], Lz)
+    return ev
+
+
+def test_besthit_window_enumeration_brute_force(oracle_mod):
+    g = synth.geometry("barrel17")
+    ev = _binned_event(oracle_mod, g, 400, 5)
+    out = oracle_mod.build_besthit(g, ev, record=True)
+    rec = out["rec"]
+    checked = 0
+    for t in range(0, ev["n"], 7):
+        for L in range(3, 17):
+            r = rec[t, L]
+            if r["status"] != 0 or r["phi_n"] == 0:
+                continue
+            ly = ev["layers"][L]
+            Lz = g["surfaces"][L]["half_or_rin"]
+            zset = set(range(r["z_lo"], r["z_hi"] + 1))
+            pset = set((r["phi_lo"] + k) % 1024 for k in range(r["phi_n"]))
+            inwin = [i for i in range(len(ly["x"]))
+                     if (lambda kk: kk // 1024 in zset and kk % 1024 in pset)(
+                         oracle_mod.bin_key(ly["x"][i], ly["y"][i], ly["z"][i], Lz))]
+            assert r["n_cand"] == min(len(inwin), 32)
+            assert bool(r["capped"]) == (len(inwin) > 32)
+            if r["best"] >= 0:
+                assert r["best"] in inwin
+                assert r["chi2_best"] < 30.0
+            checked += 1
+    assert checked > 100
+
+
+def test_besthit_finds_true_hits(oracle_mod):
+    g = synth.geometry("barrel17")
+    ev = _binned_event(oracle_mod, g, 2000, 6)
+    out = oracle_mod.build_besthit(g, ev)
+    where = ev["truth_where"]
+    has = where[:, 3:] >= 0
+    found = out["idx"][:, 3:]
+    eff = np.mean(found[has] == where[:, 3:][has])
+    fake = np.mean((found >= 0) & (found != where[:, 3:]))
+    assert eff > 0.97, eff
+    assert fake < 0.03, fake
+    # seed layers carry the given seed hits
+    np.testing.assert_array_equal(out["idx"][:, :3], ev["seed_idx"])
