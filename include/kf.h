@@ -1,0 +1,266 @@
+/*
+ * kf.h -- C ABI of libkf.so: batched Kalman-filter track fitting and
+ * best-hit track building on one GB300 (sm_103a).
+ *
+ * The method (arXiv:1711.06571): Kalman-filter tracking in three stages,
+ * seeding, building and fitting (Sec. 2); state in hybrid coordinates, global
+ * Cartesian position plus polar momentum, in a uniform longitudinal field
+ * (Sec. 3); propagation to each detector layer and a KF update on the plane
+ * tangent to the hit radius (Sec. 4.1); multiple scattering folded into the
+ * trajectory estimate (Sec. 2); a binned hit structure for selecting hit
+ * candidates (Sec. 3.1); one track per GPU thread over a structure-of-arrays
+ * layout with coalesced loads, several events in flight (Sec. 4.2, 4.3).
+ *
+ * Conventions for every entry point
+ *   - Return value: KF_OK (0) or a negative KF_E* code; the context keeps a
+ *     message for the last error (kf_ctx_last_error).  Per-track problems never
+ *     fail a call: they are reported in the per-track status word (KF_ST_*).
+ *   - Arrays marked "device" must be device memory of the context's GPU
+ *     (cudaMalloc / torch CUDA tensors); a host pointer there is rejected with
+ *     KF_EINVAL.  Arrays marked "host" are host memory.
+ *   - The caller owns every array passed in or out.  The context owns its
+ *     scratch (workspace, autotune results, CUDA graphs) and frees it in
+ *     kf_ctx_destroy.
+ *   - Work is enqueued on the given CUDA stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream) and returns before it completes;
+ *     results are valid once the stream has been synchronised.
+ *   - Structure-of-arrays layouts: "[k][n]" means k planes of n values, plane
+ *     i at offset i*n.  Track state vectors are (x, y, z, 1/pT, phi, theta) in
+ *     cm, GeV^-1 and rad; the charge q = +-1 is carried separately and 1/pT may
+ *     change sign during a fit (the physical curvature is -q * kappa * Bz / pT).
+ *     Covariances are packed lower triangles, row-major, i >= j:
+ *     entry (i, j) at index i*(i+1)/2 + j, 21 values.
+ */
+#ifndef KF_H
+#define KF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define KF_OK 0
+#define KF_EINVAL (-1)   /* bad argument, size or pointer kind */
+#define KF_ENOMEM (-2)   /* workspace allocation failed */
+#define KF_ECUDA (-3)    /* a CUDA call or kernel launch failed */
+#define KF_ETIMEOUT (-4) /* a device-side wait ran out (reported, never trapped) */
+#define KF_EAGAIN (-5)   /* serving: result not ready yet */
+#define KF_EBUSY (-6)    /* serving: request exceeds the memory budget */
+
+/* per-track status bits */
+#define KF_ST_NO_INTERSECT 1u /* helix never reaches the next surface; later hits unused */
+#define KF_ST_CHOL_FAIL 2u    /* innovation covariance S not positive definite */
+#define KF_ST_NONFINITE 4u    /* non-finite state */
+#define KF_ST_CAND_CAPPED 8u  /* building: more window candidates than the cap */
+#define KF_ST_GRAZING 16u     /* scattering thickness used the |cos(alpha)| >= 0.05 guard */
+
+/* precision policies (kf_fit_params.precision) */
+#define KF_PREC_MIXED 0 /* FP32 propagation/transport/update; FP64 for the 3x3 S
+                           solve and for the first n_fp64_updates updates */
+#define KF_PREC_FP64 1  /* every step in FP64 (the plain reference path) */
+
+/* scheduling of kf_fit (kf_fit_params.schedule) */
+#define KF_SCHED_GRID 0       /* one thread per track, one launch */
+#define KF_SCHED_PERSISTENT 1 /* tracks bucketed by hit count, persistent kernel
+                                 with an atomic work queue, replayed as a CUDA graph */
+
+#define KF_MAX_SURFACES 64
+#define KF_NPHI 1024
+#define KF_NZ 64
+#define KF_NBINS (KF_NPHI * KF_NZ)
+
+typedef struct kf_ctx kf_ctx;
+
+/* One detector surface (Sec. 3 ideal barrel; Sec. 4.1 "cylinder with lids").
+ * kind 0: barrel cylinder r = pos, |z| <= half_or_rin.
+ * kind 1: disk z = pos, half_or_rin <= r <= r_out.
+ * x_x0: thickness in radiation lengths at normal incidence.
+ * sig_n: hit resolution along the surface normal; sig_rphi: along phi-hat;
+ * sig_3: along z (barrel) or r (disk), all in cm. */
+typedef struct {
+    int32_t kind;
+    int32_t pad_;
+    double pos;
+    double half_or_rin;
+    double r_out;
+    double x_x0;
+    double sig_n;
+    double sig_rphi;
+    double sig_3;
+} kf_surface;
+
+/* Detector and field.  surfaces: host array of n_surfaces (<= KF_MAX_SURFACES). */
+typedef struct {
+    double bz;   /* T, uniform along z (Sec. 3) */
+    double mass; /* GeV, particle mass for the velocity in the scattering angle */
+    int32_t n_surfaces;
+    int32_t pad_;
+    const kf_surface *surfaces;
+} kf_geometry;
+
+typedef struct {
+    int32_t precision;      /* KF_PREC_MIXED | KF_PREC_FP64 */
+    int32_t n_fp64_updates; /* MIXED: updates (from the seed) kept in FP64, 0..32; default 3 */
+    double seed_cov;        /* seed covariance = seed_cov * I6, default 1e4 */
+    int32_t ms_on;          /* 1: add multiple-scattering noise at every surface */
+    int32_t schedule;       /* KF_SCHED_GRID | KF_SCHED_PERSISTENT */
+} kf_fit_params;
+
+/* Seeds: device SoA. state [6][n] FP32 (x, y, z, 1/pT, phi, theta at the
+ * track's first hit); q [n] int8 (+1 / -1). */
+typedef struct {
+    const float *state;
+    const int8_t *q;
+} kf_seeds;
+
+/* Hits of n tracks in path order, device CSR: track t owns hits
+ * offsets[t] .. offsets[t+1]-1; layer[] is the surface index of each hit. */
+typedef struct {
+    const int32_t *offsets; /* [n+1], offsets[0] == 0, non-decreasing */
+    const uint8_t *layer;   /* [offsets[n]] */
+    const float *x;
+    const float *y;
+    const float *z;
+} kf_track_hits;
+
+/* Fitted tracks, device outputs.  state [6][n] and cov [21][n] in FP64 storage
+ * whatever the compute precision (the mixed path keeps the position and phi in
+ * float-float, which FP32 storage would round away); chi2 [n]; ndof [n] =
+ * 2 * (hits used) - 5; status [n] KF_ST_* bits.  Any pointer may be NULL. */
+typedef struct {
+    double *state;
+    double *cov;
+    double *chi2;
+    int32_t *ndof;
+    uint32_t *status;
+} kf_tracks_out;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device cuda_device.  device_mem_budget_bytes caps
+ * the context's own workspace (0 = no cap).  *out receives the context. */
+int kf_ctx_create(kf_ctx **out, int cuda_device, size_t device_mem_budget_bytes);
+/* Free the context and everything it owns.  NULL is accepted. */
+void kf_ctx_destroy(kf_ctx *ctx);
+/* Message for the last error of this context (owned by the context). */
+const char *kf_ctx_last_error(const kf_ctx *ctx);
+/* Library version string (static). */
+const char *kf_version(void);
+
+/* ---------------------------------------------------------------- seeding */
+
+/* Seed estimate (Sec. 2: "initial estimate of the track parameters based on a
+ * few hits in the innermost regions"; the estimate itself is a reading): for
+ * each track, hit 0 and the next two hits at least 2 cm apart in x-y (hits
+ * 0, 1, 2 on a barrel); signed curvature of the circle through them, 1/pT =
+ * |k| / (kappa |Bz|), q = -sign(k), phi = tangent at hit 0, theta from the
+ * arc length, position = hit 0.  FP32.  Tracks with fewer than 3 hits get a
+ * zero state and q = +1.
+ * hits: device CSR (n tracks); state_out: device [6][n]; q_out: device [n]. */
+int kf_make_seeds(kf_ctx *ctx, const kf_geometry *geom, int32_t n, const kf_track_hits *hits, float *state_out,
+                  int8_t *q_out, void *stream);
+
+/* ---------------------------------------------------------------- fitting */
+
+/* Kalman-filter fit of n tracks (Sec. 2: with the hit collection known, the
+ * KF is applied over it without branching; Sec. 4.1: propagate to each layer,
+ * update on the tangent plane).  For each hit in path order: propagate the
+ * state along the helix to the hit's surface with the surface-constrained
+ * 6x6 Jacobian (no propagation for hit 0, where the seed sits), transport
+ * P <- J P J^T, add Highland scattering noise to the phi and theta variances,
+ * then the 3-D update: r = m - x, S = H P H^T + R, chi2 = r^T S^-1 r via an
+ * LDL^T (square-root-free Cholesky) factorisation of S in FP64, K = P H^T S^-1,
+ * x += K r, P updated (Joseph form on the FP64 updates).  The output state is
+ * the one at the last used hit.
+ * params: host struct (NULL = defaults); seeds, hits: device; out: device. */
+int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n, const kf_seeds *seeds,
+           const kf_track_hits *hits, const kf_tracks_out *out, void *stream);
+
+/* Choose block size, tracks per thread and work-queue chunk of the persistent
+ * fit for this (n, hit count) by timing candidates on the given inputs (it
+ * runs the fit several times and overwrites out).  The choice is cached in the
+ * context and used by later kf_fit calls with schedule = KF_SCHED_PERSISTENT.
+ * report (host, may be NULL) receives "block,tpt,chunk,ms" of the winner. */
+int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
+                    const kf_seeds *seeds, const kf_track_hits *hits, const kf_tracks_out *out, void *stream,
+                    char *report, size_t report_len);
+
+/* ---------------------------------------------------------------- binning */
+
+/* Bin one layer's hits into the (phi, z) grid used to select hit candidates
+ * (Sec. 3.1), in FP64 from the FP32 coordinates:
+ *   phi_bin = clamp(floor(((atan2(y, x) + pi) * 1024) / (2 pi)), 0, 1023)
+ *   z_bin   = clamp(floor(((z + half_len) * 64) / (2 half_len)), 0, 63)
+ *   key     = z_bin * 1024 + phi_bin
+ * then a stable counting sort by key (ties keep the original order).
+ * x, y, z: device [n_hits].  perm_out: device [n_hits], original index of the
+ * i-th hit in binned order.  offsets_out: device [KF_NBINS + 1], hits of key k
+ * are binned positions offsets[k] .. offsets[k+1]-1.  packed_out: device
+ * [n_hits][4] floats (x, y, z, original index as int32 bits) in binned order,
+ * or NULL.  half_len > 0.  n_hits == 0 is allowed (offsets all zero). */
+int kf_bin_hits(kf_ctx *ctx, int32_t n_hits, const float *x, const float *y, const float *z, double half_len,
+                int32_t *perm_out, int32_t *offsets_out, float *packed_out, void *stream);
+
+/* ---------------------------------------------------------------- building */
+
+/* One binned layer of one event (device arrays made by kf_bin_hits). */
+typedef struct {
+    int32_t n_hits;
+    int32_t surface;         /* index into the geometry (a barrel) */
+    const float *packed;     /* [n_hits][4]: x, y, z, original index bits, binned order */
+    const int32_t *offsets;  /* [KF_NBINS + 1] */
+    const float *x;          /* [n_hits] original order (read by kf_gather_hits only; may be NULL otherwise) */
+    const float *y;
+    const float *z;
+} kf_binned_layer;
+
+typedef struct {
+    double nsigma;    /* window half width in sigmas (3) */
+    double chi2_cut;  /* accept the best hit only if chi2 < cut (30) */
+    int32_t max_cand; /* candidates scored per step, in enumeration order (32), 1..64 */
+    int32_t warp_coop;/* 1: score window candidates across the warp with a
+                         shuffle min-reduction; 0: one thread per track */
+} kf_build_params;
+
+/* Best-hit track building (Sec. 2: project the candidate outwards, use the KF
+ * to pick the most likely continuation on each layer; here one candidate per
+ * seed keeps the minimum-chi2 hit).  Tracks of several events run in one
+ * launch (Sec. 4.2 "multiple events at a time").  Per track: KF fit over its
+ * three seed hits (layers 0..2 of the event), then for every later layer:
+ * propagate, add scattering noise, open a window of +- nsigma in phi
+ * (position and hit resolution) and z, enumerate the window's bins (z
+ * ascending, phi ascending with wrap, binned order; at most max_cand hits),
+ * chi2 of each candidate with the FP64 S solve, keep the smallest below
+ * chi2_cut (ties: lower original index), update with it.
+ *   n_events, n_layers: events and layers per event (all events share the
+ *     layer list; n_layers <= KF_MAX_SURFACES).
+ *   layers: host [n_events * n_layers] descriptors, event-major.
+ *   event_offsets: host [n_events + 1], tracks of event e are
+ *     event_offsets[e] .. event_offsets[e+1]-1 of the n = event_offsets[n_events]
+ *     tracks.
+ *   seeds: device, from kf_make_seeds over the three seed hits.
+ *   seed_hits: device [9][n] FP32: x0, y0, z0, x1, y1, z1, x2, y2, z2.
+ *   hit_idx_out: device [n_layers][n] int32: chosen original hit index per
+ *     layer, -1 for none; the seed layers get -1 (the caller knows them).
+ *   out: device fitted tracks after the last layer.
+ * fit: host (precision, n_fp64_updates, seed_cov, ms_on are used). */
+int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit, const kf_build_params *bp,
+                     int32_t n_events, int32_t n_layers, const kf_binned_layer *layers, const int32_t *event_offsets,
+                     const kf_seeds *seeds, const float *seed_hits, int32_t *hit_idx_out, const kf_tracks_out *out,
+                     void *stream);
+
+/* Gather the hits a build chose into fit input (for the final fit, Sec. 2):
+ * for each track, its three seed hits then every layer with hit_idx >= 0, in
+ * layer order.  offsets_out: device [n+1]; layer_out, x_out, y_out, z_out:
+ * device, capacity n * n_layers.  Arguments as in kf_build_besthit. */
+int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_binned_layer *layers,
+                   const int32_t *event_offsets, const float *seed_hits, const int32_t *hit_idx, int32_t *offsets_out,
+                   uint8_t *layer_out, float *x_out, float *y_out, float *z_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KF_H */

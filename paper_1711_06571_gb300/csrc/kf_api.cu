@@ -1,0 +1,641 @@
+// kf_api.cu -- the extern "C" entry points of libkf.so (declared in include/kf.h):
+// argument checking, geometry upload by value, per-stream workspaces, the
+// graph-captured persistent fit and its autotuner.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kf_internal.h"
+
+using namespace kfd;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+struct Tuned {
+    int block = 128, grid = 0, chunk = 64;
+    float ms = 0.f;
+};
+
+struct GraphKey {
+    std::vector<uint8_t> bytes;
+    bool operator==(const GraphKey &o) const { return bytes == o.bytes; }
+};
+
+}  // namespace
+
+struct kf_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::string err;
+    std::mutex mu;
+    std::map<cudaStream_t, Buf> ws;  // one workspace per stream: calls on one stream are ordered
+    cudaStream_t cap_stream = nullptr;
+    // autotune results: key = (fp64, n bucket)
+    std::map<std::pair<int, int>, Tuned> tuned;
+    // one cached graph of the persistent fit
+    GraphKey gkey;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+int fail(kf_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(kf_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, KF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+#define NEED_DEV(ptr, name)                                                                 \
+    do {                                                                                    \
+        if (!is_device_ptr(ptr)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
+    } while (0)
+#define OPT_DEV(ptr, name)                                                                  \
+    do {                                                                                    \
+        if ((ptr) && !is_device_ptr(ptr)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
+    } while (0)
+
+int to_geom(kf_ctx *ctx, const kf_geometry *g, Geom &G)
+{
+    if (!g || !g->surfaces || g->n_surfaces <= 0 || g->n_surfaces > KF_MAX_SURFACES)
+        return fail(ctx, KF_EINVAL, "geometry: need 1..%d surfaces", KF_MAX_SURFACES);
+    memset(&G, 0, sizeof G);
+    G.n = g->n_surfaces;
+    G.kbd = KAPPA * g->bz;
+    G.kb = (float)G.kbd;
+    G.mass2d = g->mass * g->mass;
+    G.mass2 = (float)G.mass2d;
+    for (int i = 0; i < G.n; ++i) {
+        const kf_surface &s = g->surfaces[i];
+        if (s.kind != 0 && s.kind != 1) return fail(ctx, KF_EINVAL, "surface %d: kind must be 0 or 1", i);
+        if (!(s.sig_n > 0) || !(s.sig_rphi > 0) || !(s.sig_3 > 0) || !(s.x_x0 >= 0))
+            return fail(ctx, KF_EINVAL, "surface %d: resolutions must be > 0 and x/X0 >= 0", i);
+        if (s.kind == 0 && !(s.pos > 0 && s.half_or_rin > 0))
+            return fail(ctx, KF_EINVAL, "surface %d: barrel needs R > 0 and half length > 0", i);
+        Surf &d = G.s[i];
+        d.kind = s.kind;
+        d.posd = s.pos;
+        d.pos = (float)s.pos;
+        d.pos2 = (float)(s.pos * s.pos);
+        d.halfd = s.half_or_rin;
+        d.half = (float)s.half_or_rin;
+        d.rout = (float)s.r_out;
+        d.x_x0d = s.x_x0;
+        d.x_x0 = (float)s.x_x0;
+        double rad = s.kind == 0 ? s.sig_n : s.sig_3;
+        double zz = s.kind == 0 ? s.sig_3 : s.sig_n;
+        d.var_radd = rad * rad;
+        d.var_rphid = s.sig_rphi * s.sig_rphi;
+        d.var_zzd = zz * zz;
+        d.var_rad = (float)d.var_radd;
+        d.var_rphi = (float)d.var_rphid;
+        d.var_zz = (float)d.var_zzd;
+    }
+    return KF_OK;
+}
+
+// scratch of at least `bytes` for work on stream `st` (grows; never shrinks)
+int ws_get(kf_ctx *ctx, cudaStream_t st, size_t bytes, void **out)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Buf &b = ctx->ws[st];
+    if (b.n < bytes) {
+        size_t want = bytes + bytes / 4;
+        if (ctx->budget && ctx->used - b.n + want > ctx->budget)
+            return fail(ctx, KF_ENOMEM, "workspace of %zu bytes exceeds the budget", want);
+        if (b.p) {
+            cudaStreamSynchronize(st);
+            cudaFree(b.p);
+            ctx->used -= b.n;
+            b = Buf{};
+            // graphs captured against the old workspace are stale
+            if (ctx->gexec) {
+                cudaGraphExecDestroy(ctx->gexec);
+                ctx->gexec = nullptr;
+                ctx->gkey.bytes.clear();
+            }
+        }
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, KF_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+        }
+        b.n = want;
+        ctx->used += want;
+    }
+    *out = b.p;
+    return KF_OK;
+}
+
+int check_fit_params(kf_ctx *ctx, const kf_fit_params *p, kf_fit_params &q)
+{
+    q.precision = KF_PREC_MIXED;
+    q.n_fp64_updates = 3;
+    q.seed_cov = 1e4;
+    q.ms_on = 1;
+    q.schedule = KF_SCHED_GRID;
+    if (!p) return KF_OK;
+    q = *p;
+    if (q.precision != KF_PREC_MIXED && q.precision != KF_PREC_FP64)
+        return fail(ctx, KF_EINVAL, "precision must be KF_PREC_MIXED or KF_PREC_FP64");
+    if (q.n_fp64_updates < 0 || q.n_fp64_updates > 32) return fail(ctx, KF_EINVAL, "n_fp64_updates must be 0..32");
+    if (!(q.seed_cov > 0)) return fail(ctx, KF_EINVAL, "seed_cov must be > 0");
+    if (q.schedule != KF_SCHED_GRID && q.schedule != KF_SCHED_PERSISTENT)
+        return fail(ctx, KF_EINVAL, "schedule must be KF_SCHED_GRID or KF_SCHED_PERSISTENT");
+    return KF_OK;
+}
+
+int set_dev(kf_ctx *ctx)
+{
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return KF_OK;
+}
+
+int n_bucket(int n)
+{
+    int b = 0;
+    while ((1 << b) < n && b < 30) ++b;
+    return b;
+}
+
+template <class T>
+void key_put(std::vector<uint8_t> &k, const T &v)
+{
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(&v);
+    k.insert(k.end(), p, p + sizeof(T));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kf_version(void) { return "libkf 0.1 (sm_103a)"; }
+
+int kf_ctx_create(kf_ctx **out, int cuda_device, size_t budget)
+{
+    if (!out) return KF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev) {
+        cudaGetLastError();
+        return KF_EINVAL;
+    }
+    kf_ctx *c = new kf_ctx();
+    c->device = cuda_device;
+    c->budget = budget;
+    if (cudaSetDevice(cuda_device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return KF_ECUDA;
+    }
+    *out = c;
+    return KF_OK;
+}
+
+void kf_ctx_destroy(kf_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (auto &kv : c->ws)
+        if (kv.second.p) cudaFree(kv.second.p);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+const char *kf_ctx_last_error(const kf_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int kf_make_seeds(kf_ctx *ctx, const kf_geometry *geom, int32_t n, const kf_track_hits *hits, float *state_out,
+                  int8_t *q_out, void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (n < 0 || !hits) return fail(ctx, KF_EINVAL, "n must be >= 0 and hits given");
+    Geom G;
+    int rc = to_geom(ctx, geom, G);
+    if (rc) return rc;
+    if ((rc = set_dev(ctx))) return rc;
+    if (n == 0) return KF_OK;
+    NEED_DEV(hits->offsets, "hits.offsets");
+    NEED_DEV(hits->x, "hits.x");
+    NEED_DEV(hits->y, "hits.y");
+    NEED_DEV(hits->z, "hits.z");
+    NEED_DEV(state_out, "state_out");
+    NEED_DEV(q_out, "q_out");
+    cudaError_t e = launch_seeds(G, n, hits->offsets, hits->x, hits->y, hits->z, state_out, q_out,
+                                 (cudaStream_t)stream);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "seed kernel");
+}
+
+static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
+                    const kf_seeds *seeds, const kf_track_hits *hits, const kf_tracks_out *out, void *stream,
+                    const Tuned *force)
+{
+    if (!ctx) return KF_EINVAL;
+    if (n < 0 || !seeds || !hits || !out) return fail(ctx, KF_EINVAL, "n >= 0, seeds, hits and out are required");
+    kf_fit_params P;
+    int rc = check_fit_params(ctx, params, P);
+    if (rc) return rc;
+    Geom G;
+    if ((rc = to_geom(ctx, geom, G))) return rc;
+    if ((rc = set_dev(ctx))) return rc;
+    if (n == 0) return KF_OK;
+    NEED_DEV(seeds->state, "seeds.state");
+    NEED_DEV(seeds->q, "seeds.q");
+    NEED_DEV(hits->offsets, "hits.offsets");
+    NEED_DEV(hits->layer, "hits.layer");
+    NEED_DEV(hits->x, "hits.x");
+    NEED_DEV(hits->y, "hits.y");
+    NEED_DEV(hits->z, "hits.z");
+    OPT_DEV(out->state, "out.state");
+    OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->chi2, "out.chi2");
+    OPT_DEV(out->ndof, "out.ndof");
+    OPT_DEV(out->status, "out.status");
+    cudaStream_t st = (cudaStream_t)stream;
+    FitArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = n;
+    a.n64 = P.precision == KF_PREC_FP64 ? P.n_fp64_updates : P.n_fp64_updates;
+    a.seed_cov = P.seed_cov;
+    a.ms_on = P.ms_on;
+    a.seed_state = seeds->state;
+    a.q = seeds->q;
+    a.off = hits->offsets;
+    a.layer = hits->layer;
+    a.hx = hits->x;
+    a.hy = hits->y;
+    a.hz = hits->z;
+    a.o_state = out->state;
+    a.o_cov = out->cov;
+    a.o_chi2 = out->chi2;
+    a.o_ndof = out->ndof;
+    a.o_status = out->status;
+    const bool fp64 = P.precision == KF_PREC_FP64;
+    // processing order (both schedules): tracks bucketed by hit count and seed 1/pT
+    const size_t nhist = order_scratch_ints();
+    const size_t need = (nhist + 64) * sizeof(int32_t) + (size_t)n * sizeof(int32_t) + 256;
+    void *wsp = nullptr;
+    if ((rc = ws_get(ctx, st, need, &wsp))) return rc;
+    int32_t *hist = reinterpret_cast<int32_t *>(wsp);
+    int32_t *queue = hist + nhist;
+    int32_t *order = queue + 64;
+    a.order = order;
+    if (P.schedule == KF_SCHED_GRID && !force) {
+        cudaError_t e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hist, order, st);
+        if (e == cudaSuccess) e = launch_fit(G, a, fp64, 128, st);
+        return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "fit kernel");
+    }
+    // persistent: order by hit count + work queue, captured once as a CUDA graph
+    Tuned tu;
+    if (force) {
+        tu = *force;
+    } else {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        auto it = ctx->tuned.find({fp64 ? 1 : 0, n_bucket(n)});
+        if (it != ctx->tuned.end()) tu = it->second;
+    }
+    if (tu.grid <= 0) tu.grid = ctx->sm_count * std::max(1, persistent_blocks_per_sm(fp64, tu.block));
+    a.queue = queue;
+    a.chunk = tu.chunk;
+    if (force) {
+        cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+        if (e == cudaSuccess) e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hist, order, st);
+        if (e == cudaSuccess) e = launch_fit_persistent(G, a, fp64, tu.block, tu.grid, st);
+        return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "persistent fit");
+    }
+    GraphKey key;
+    key_put(key.bytes, a);
+    key_put(key.bytes, fp64);
+    key_put(key.bytes, tu);
+    key_put(key.bytes, G);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->gexec || !(key == ctx->gkey)) {
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaStream_t cs = ctx->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+        cudaError_t e1 = cudaMemsetAsync(queue, 0, sizeof(int32_t), cs);
+        if (e1 == cudaSuccess) e1 = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hist, order, cs);
+        if (e1 == cudaSuccess) e1 = launch_fit_persistent(G, a, fp64, tu.block, tu.grid, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e1 != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ctx, e1 != cudaSuccess ? e1 : e, "capturing the persistent fit");
+        }
+        e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
+        ctx->gkey = key;
+    }
+    cudaError_t e = cudaGraphLaunch(ctx->gexec, st);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "cudaGraphLaunch");
+}
+
+int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n, const kf_seeds *seeds,
+           const kf_track_hits *hits, const kf_tracks_out *out, void *stream)
+{
+    return fit_impl(ctx, geom, params, n, seeds, hits, out, stream, nullptr);
+}
+
+int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
+                    const kf_seeds *seeds, const kf_track_hits *hits, const kf_tracks_out *out, void *stream,
+                    char *report, size_t report_len)
+{
+    if (!ctx) return KF_EINVAL;
+    kf_fit_params P;
+    int rc = check_fit_params(ctx, params, P);
+    if (rc) return rc;
+    if ((rc = set_dev(ctx))) return rc;
+    if (n <= 0) return fail(ctx, KF_EINVAL, "autotune needs n > 0");
+    const bool fp64 = P.precision == KF_PREC_FP64;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Tuned best;
+    best.ms = 1e30f;
+    const int blocks[3] = {64, 128, 256};
+    const int chunks[3] = {32, 64, 128};
+    for (int bi = 0; bi < 3; ++bi) {
+        const int occ = persistent_blocks_per_sm(fp64, blocks[bi]);
+        if (occ <= 0) continue;
+        for (int ci = 0; ci < 3; ++ci) {
+            Tuned c;
+            c.block = blocks[bi];
+            c.chunk = chunks[ci];
+            c.grid = ctx->sm_count * occ;
+            // warm-up, then the best of three timed runs
+            rc = fit_impl(ctx, geom, &P, n, seeds, hits, out, stream, &c);
+            if (rc) break;
+            float bestc = 1e30f;
+            for (int r = 0; r < 3 && !rc; ++r) {
+                cudaEventRecord(e0, st);
+                rc = fit_impl(ctx, geom, &P, n, seeds, hits, out, stream, &c);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < bestc) bestc = ms;
+            }
+            if (rc) break;
+            c.ms = bestc;
+            if (c.ms < best.ms) best = c;
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tuned[{fp64 ? 1 : 0, n_bucket(n)}] = best;
+    }
+    if (report && report_len)
+        snprintf(report, report_len, "%d,%d,%d,%d,%.4f", best.block, 1, best.chunk, best.grid, best.ms);
+    return KF_OK;
+}
+
+int kf_bin_hits(kf_ctx *ctx, int32_t n_hits, const float *x, const float *y, const float *z, double half_len,
+                int32_t *perm_out, int32_t *offsets_out, float *packed_out, void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (n_hits < 0 || !(half_len > 0)) return fail(ctx, KF_EINVAL, "n_hits >= 0 and half_len > 0 required");
+    int rc = set_dev(ctx);
+    if (rc) return rc;
+    NEED_DEV(offsets_out, "offsets_out");
+    if (n_hits > 0) {
+        NEED_DEV(x, "x");
+        NEED_DEV(y, "y");
+        NEED_DEV(z, "z");
+        NEED_DEV(perm_out, "perm_out");
+        OPT_DEV(packed_out, "packed_out");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    void *wsp = nullptr;
+    if ((rc = ws_get(ctx, st, bin_scratch_bytes(n_hits), &wsp))) return rc;
+    cudaError_t e = launch_bin(n_hits, x, y, z, half_len, perm_out, offsets_out, packed_out, wsp, st);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "binning kernels");
+}
+
+// device copy of the layer table and event offsets, in the stream's workspace after `skip` bytes
+static int upload_layers(kf_ctx *ctx, cudaStream_t st, int n_events, int n_layers, const kf_binned_layer *layers,
+                         const int32_t *event_offsets, size_t extra, void **ws_out, LayerDev **dl, int32_t **deoff,
+                         bool need_xyz)
+{
+    const size_t nl = (size_t)n_events * n_layers;
+    std::vector<LayerDev> host(nl);
+    for (size_t i = 0; i < nl; ++i) {
+        const kf_binned_layer &L = layers[i];
+        if (L.n_hits < 0) return fail(ctx, KF_EINVAL, "layer %zu: n_hits < 0", i);
+        host[i].packed = reinterpret_cast<const float4 *>(L.packed);
+        host[i].offsets = L.offsets;
+        host[i].x = L.x;
+        host[i].y = L.y;
+        host[i].z = L.z;
+        host[i].n_hits = L.n_hits;
+        host[i].surface = L.surface;
+    }
+    const size_t tbl = nl * sizeof(LayerDev), eo = (size_t)(n_events + 1) * sizeof(int32_t);
+    const size_t tbl_al = (tbl + 255) & ~(size_t)255, eo_al = (eo + 255) & ~(size_t)255;
+    void *wsp = nullptr;
+    int rc = ws_get(ctx, st, tbl_al + eo_al + extra, &wsp);
+    if (rc) return rc;
+    // stage through a small pinned buffer so the copy is ordered on the stream
+    void *pin = nullptr;
+    if (cudaMallocHost(&pin, tbl + eo) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KF_ENOMEM, "pinned staging");
+    }
+    memcpy(pin, host.data(), tbl);
+    memcpy((char *)pin + tbl, event_offsets, eo);
+    cudaError_t e = cudaMemcpyAsync(wsp, pin, tbl, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char *)wsp + tbl_al, (char *)pin + tbl, eo, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeHost(pin);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading the layer table");
+    (void)need_xyz;
+    *ws_out = (char *)wsp + tbl_al + eo_al;
+    *dl = reinterpret_cast<LayerDev *>(wsp);
+    *deoff = reinterpret_cast<int32_t *>((char *)wsp + tbl_al);
+    return KF_OK;
+}
+
+static int check_events(kf_ctx *ctx, const kf_geometry *geom, int n_events, int n_layers,
+                        const kf_binned_layer *layers, const int32_t *event_offsets, bool need_xyz)
+{
+    if (n_events <= 0 || n_layers < 3 || n_layers > KF_MAX_SURFACES || !layers || !event_offsets)
+        return fail(ctx, KF_EINVAL, "need n_events > 0, 3 <= n_layers <= %d, layers and event_offsets",
+                    KF_MAX_SURFACES);
+    if (event_offsets[0] != 0) return fail(ctx, KF_EINVAL, "event_offsets[0] must be 0");
+    for (int e = 0; e < n_events; ++e)
+        if (event_offsets[e + 1] < event_offsets[e]) return fail(ctx, KF_EINVAL, "event_offsets must not decrease");
+    for (int i = 0; i < n_events * n_layers; ++i) {
+        const kf_binned_layer &L = layers[i];
+        if (L.surface < 0 || L.surface >= geom->n_surfaces)
+            return fail(ctx, KF_EINVAL, "layer %d: surface index out of range", i);
+        if (geom->surfaces[L.surface].kind != 0) return fail(ctx, KF_EINVAL, "layer %d: building needs barrels", i);
+        if (i % n_layers >= 3 && L.n_hits > 0) {
+            if (!is_device_ptr(L.packed) || !is_device_ptr(L.offsets))
+                return fail(ctx, KF_EINVAL, "layer %d: packed and offsets must be device memory", i);
+        } else if (i % n_layers >= 3 && !is_device_ptr(L.offsets)) {
+            return fail(ctx, KF_EINVAL, "layer %d: offsets must be device memory", i);
+        }
+        if (need_xyz && i % n_layers >= 3 && L.n_hits > 0 &&
+            (!is_device_ptr(L.x) || !is_device_ptr(L.y) || !is_device_ptr(L.z)))
+            return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory", i);
+    }
+    return KF_OK;
+}
+
+int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit, const kf_build_params *bp,
+                     int32_t n_events, int32_t n_layers, const kf_binned_layer *layers, const int32_t *event_offsets,
+                     const kf_seeds *seeds, const float *seed_hits, int32_t *hit_idx_out, const kf_tracks_out *out,
+                     void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    kf_fit_params P;
+    int rc = check_fit_params(ctx, fit, P);
+    if (rc) return rc;
+    Geom G;
+    if ((rc = to_geom(ctx, geom, G))) return rc;
+    if ((rc = set_dev(ctx))) return rc;
+    if ((rc = check_events(ctx, geom, n_events, n_layers, layers, event_offsets, false))) return rc;
+    kf_build_params B = {3.0, 30.0, 32, 0};
+    if (bp) B = *bp;
+    if (!(B.nsigma > 0) || !(B.chi2_cut > 0) || B.max_cand < 1 || B.max_cand > 64)
+        return fail(ctx, KF_EINVAL, "build params: nsigma > 0, chi2_cut > 0, 1 <= max_cand <= 64");
+    const int n = event_offsets[n_events];
+    if (n == 0) return KF_OK;
+    if (!seeds || !out) return fail(ctx, KF_EINVAL, "seeds and out are required");
+    NEED_DEV(seeds->state, "seeds.state");
+    NEED_DEV(seeds->q, "seeds.q");
+    NEED_DEV(seed_hits, "seed_hits");
+    NEED_DEV(hit_idx_out, "hit_idx_out");
+    OPT_DEV(out->state, "out.state");
+    OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->chi2, "out.chi2");
+    OPT_DEV(out->ndof, "out.ndof");
+    OPT_DEV(out->status, "out.status");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *rest = nullptr;
+    LayerDev *dl = nullptr;
+    int32_t *deoff = nullptr;
+    const size_t nhist = order_scratch_ints();
+    if ((rc = upload_layers(ctx, st, n_events, n_layers, layers, event_offsets,
+                            (nhist + (size_t)n) * sizeof(int32_t) + 256, &rest, &dl, &deoff, false)))
+        return rc;
+    int32_t *hist = reinterpret_cast<int32_t *>(rest);
+    int32_t *order = hist + nhist;
+    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, hist, order, st);
+    if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
+    BuildArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = n;
+    a.n_events = n_events;
+    a.n_layers = n_layers;
+    a.n64 = P.n_fp64_updates;
+    a.seed_cov = P.seed_cov;
+    a.ms_on = P.ms_on;
+    a.max_cand = B.max_cand;
+    a.nsigma = (float)B.nsigma;
+    a.chi2_cut = (float)B.chi2_cut;
+    a.layers = dl;
+    a.event_off = deoff;
+    a.seed_state = seeds->state;
+    a.q = seeds->q;
+    a.seed_hits = seed_hits;
+    a.hit_idx = hit_idx_out;
+    a.order = order;
+    a.o_state = out->state;
+    a.o_cov = out->cov;
+    a.o_chi2 = out->chi2;
+    a.o_ndof = out->ndof;
+    a.o_status = out->status;
+    cudaError_t e = launch_build(G, a, P.precision == KF_PREC_FP64, B.warp_coop != 0, st);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "build kernel");
+}
+
+int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_binned_layer *layers,
+                   const int32_t *event_offsets, const float *seed_hits, const int32_t *hit_idx, int32_t *offsets_out,
+                   uint8_t *layer_out, float *x_out, float *y_out, float *z_out, void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    int rc = set_dev(ctx);
+    if (rc) return rc;
+    if (n_events <= 0 || n_layers < 3 || n_layers > KF_MAX_SURFACES || !layers || !event_offsets)
+        return fail(ctx, KF_EINVAL, "need n_events > 0, 3 <= n_layers <= %d, layers and event_offsets",
+                    KF_MAX_SURFACES);
+    for (int i = 0; i < n_events * n_layers; ++i)
+        if (i % n_layers >= 3 && layers[i].n_hits > 0 &&
+            (!is_device_ptr(layers[i].x) || !is_device_ptr(layers[i].y) || !is_device_ptr(layers[i].z)))
+            return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory", i);
+    const int n = event_offsets[n_events];
+    NEED_DEV(offsets_out, "offsets_out");
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(offsets_out, 0, sizeof(int32_t), (cudaStream_t)stream);
+        return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "memset");
+    }
+    NEED_DEV(seed_hits, "seed_hits");
+    NEED_DEV(hit_idx, "hit_idx");
+    NEED_DEV(layer_out, "layer_out");
+    NEED_DEV(x_out, "x_out");
+    NEED_DEV(y_out, "y_out");
+    NEED_DEV(z_out, "z_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *rest = nullptr;
+    LayerDev *dl = nullptr;
+    int32_t *deoff = nullptr;
+    if ((rc = upload_layers(ctx, st, n_events, n_layers, layers, event_offsets, gather_scratch_bytes(n), &rest, &dl,
+                            &deoff, true)))
+        return rc;
+    cudaError_t e = launch_gather(n, n_events, n_layers, dl, deoff, seed_hits, hit_idx, offsets_out, layer_out, x_out,
+                                  y_out, z_out, rest, st);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "gather kernels");
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// kf_bin.cu -- per-layer hit binning into the (phi, z) grid used to select hit
+// candidates during building (Sec. 3.1: "data structures for selecting hit
+// candidates"), as a stable counting sort on the GPU.
+//
+//   1. key of every hit, in FP64 with explicit rounding (no contraction), and a
+//      histogram of keys (atomics into offsets[1..]);
+//   2. in-place inclusive scan of the histogram -> CSR offsets;
+//   3. scatter by atomic cursors (order inside a bin is arbitrary here);
+//   4. each hit counts the hits of its bin with a smaller original index and
+//      moves to that rank, which restores the stable order bit-exactly;
+//   5. optional packed copy (x, y, z, index) in binned order, one 16-byte load
+//      per candidate in the build kernel.
+// Scratch (from the caller): key[n], cursor[KF_NBINS], tmp[n] int32.
+#include "kf_internal.h"
+
+namespace kfd {
+
+constexpr double PI_D = 3.14159265358979323846;
+
+__device__ __forceinline__ int32_t bin_key(float x, float y, float z, double half_len)
+{
+    // ((atan2(y, x) + pi) * 1024) / (2 pi) and ((z + L) * 64) / (2 L), each op rounded
+    double u = __ddiv_rn(__dmul_rn(__dadd_rn(atan2((double)y, (double)x), PI_D), 1024.0), 2.0 * PI_D);
+    double v = __ddiv_rn(__dmul_rn(__dadd_rn((double)z, half_len), 64.0), __dmul_rn(2.0, half_len));
+    double fu = floor(u), fv = floor(v);
+    fu = fmin(fmax(fu, 0.0), (double)(KF_NPHI - 1));
+    fv = fmin(fmax(fv, 0.0), (double)(KF_NZ - 1));
+    return (int32_t)fv * KF_NPHI + (int32_t)fu;
+}
+
+__global__ void key_kernel(int n, const float *__restrict__ x, const float *__restrict__ y,
+                           const float *__restrict__ z, double half_len, int32_t *__restrict__ key,
+                           int32_t *__restrict__ counts /* offsets + 1 */)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t k = bin_key(x[i], y[i], z[i], half_len);
+    key[i] = k;
+    atomicAdd(&counts[k], 1);
+}
+
+// inclusive scan of KF_NBINS counts in place (one block of 1024 threads, 64 per thread)
+__global__ void __launch_bounds__(1024) scan_kernel(int32_t *__restrict__ counts, int32_t *__restrict__ cursor)
+{
+    __shared__ int32_t warp_tot[32];
+    const int tid = threadIdx.x;
+    constexpr int PER = KF_NBINS / 1024;
+    int32_t loc[PER];
+    int32_t s = 0;
+    const int base = tid * PER;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        s += counts[base + j];
+        loc[j] = s;
+    }
+    // exclusive scan of per-thread sums across the block
+    int32_t v = s;
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = warp_tot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int32_t o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    const int32_t excl = v - s + (wid > 0 ? warp_tot[wid - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        // counts[k] becomes offsets[k + 1]; the cursor of bin k starts at offsets[k]
+        int32_t incl = excl + loc[j];
+        int32_t cnt = j == 0 ? loc[0] : loc[j] - loc[j - 1];
+        counts[base + j] = incl;
+        cursor[base + j] = incl - cnt;
+    }
+}
+
+__global__ void scatter_hits_kernel(int n, const int32_t *__restrict__ key, int32_t *__restrict__ cursor,
+                                    int32_t *__restrict__ tmp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int pos = atomicAdd(&cursor[key[i]], 1);
+    tmp[pos] = i;
+}
+
+__global__ void rank_kernel(int n, const int32_t *__restrict__ key, const int32_t *__restrict__ offsets,
+                            const int32_t *__restrict__ tmp, int32_t *__restrict__ perm)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t i = tmp[p];
+    const int32_t k = key[i];
+    const int32_t b0 = offsets[k], b1 = offsets[k + 1];
+    int r = 0;
+    for (int j = b0; j < b1; ++j) r += tmp[j] < i;
+    perm[b0 + r] = i;
+}
+
+__global__ void pack_kernel(int n, const int32_t *__restrict__ perm, const float *__restrict__ x,
+                            const float *__restrict__ y, const float *__restrict__ z, float4 *__restrict__ packed)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int i = perm[p];
+    packed[p] = make_float4(x[i], y[i], z[i], __int_as_float(i));
+}
+
+size_t bin_scratch_bytes(int n_hits)
+{
+    size_t n = n_hits > 0 ? (size_t)n_hits : 1;
+    return (2 * n + KF_NBINS) * sizeof(int32_t) + 256;
+}
+
+cudaError_t launch_bin(int n, const float *x, const float *y, const float *z, double half_len, int32_t *perm,
+                       int32_t *offsets, float *packed, void *scratch, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(offsets, 0, (KF_NBINS + 1) * sizeof(int32_t), st);
+    if (e != cudaSuccess || n <= 0) return e;
+    int32_t *key = reinterpret_cast<int32_t *>(scratch);
+    int32_t *cursor = key + n;
+    int32_t *tmp = cursor + KF_NBINS;
+    const int b = 256, grid = (n + b - 1) / b;
+    key_kernel<<<grid, b, 0, st>>>(n, x, y, z, half_len, key, offsets + 1);
+    scan_kernel<<<1, 1024, 0, st>>>(offsets + 1, cursor);
+    scatter_hits_kernel<<<grid, b, 0, st>>>(n, key, cursor, tmp);
+    rank_kernel<<<grid, b, 0, st>>>(n, key, offsets, tmp, perm);
+    if (packed) pack_kernel<<<grid, b, 0, st>>>(n, perm, x, y, z, reinterpret_cast<float4 *>(packed));
+    return cudaGetLastError();
+}
+
+}  // namespace kfd

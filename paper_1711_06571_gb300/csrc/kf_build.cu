@@ -1,0 +1,644 @@
+// kf_build.cu -- best-hit track building (Sec. 2: track building projects the
+// candidate outwards and uses the KF to pick the most likely continuation on
+// each layer; this variant keeps one candidate per seed, the minimum-chi2 hit).
+//
+// Tracks of several events run in one launch (Sec. 4.2: several events at a
+// time fill the machine).  Per track: KF fit over its three seed hits (FP64,
+// Joseph form), then for every later layer propagate, add scattering noise,
+// open a +-nsigma window in (phi, z), score the window's hits, update with
+// the best one.  A window row (one z bin, a run of phi bins) is one or two
+// contiguous ranges of the layer's binned hits, read as 16-byte (x, y, z,
+// index) records.
+//
+// Two scoring schemes:
+//   per-thread: each thread walks its own window;
+//   warp-cooperative: the 32 tracks of a warp pool their candidates; every lane
+//     scores one (track, candidate) pair per round and a shuffle reduction
+//     picks each track's minimum, so a warp costs ceil(total/32) rounds
+//     instead of max-over-lanes candidates.
+#include "kf_internal.h"
+#include "kf_track.cuh"
+
+namespace kfd {
+
+__device__ __forceinline__ int find_event(const int32_t *__restrict__ eoff, int n_events, int t)
+{
+    int lo = 0, hi = n_events - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (eoff[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Window of a predicted state on a barrel layer (SURVEY reading: +- nsigma in the
+// azimuth of the predicted position, with its variance from P and the hit
+// resolution, and in z).
+struct Window {
+    int phi_lo;  // first phi bin, in [0, 1024)
+    int nphi;    // number of phi bins, <= 1024
+    int z_lo, z_hi;
+};
+
+template <class T, class P>
+__device__ __forceinline__ Window make_window(const Track<T, P> &st, const float p[21], const Surf &sf, float nsig)
+{
+    const float X = (float)lead(st.x), Y = (float)lead(st.y), Z = (float)lead(st.z);
+    const float r2 = X * X + Y * Y;
+    const float phip = atan2f(Y, X);
+    const float sphi2 = (Y * Y * p[pk(0, 0)] + X * X * p[pk(1, 1)] - 2.f * X * Y * p[pk(1, 0)]) / (r2 * r2);
+    const float R = sf.pos;
+    const float dphi = nsig * sqrtf(fmaxf(sphi2, 0.f) + sf.var_rphi / (R * R));
+    const float dz = nsig * sqrtf(fmaxf(p[pk(2, 2)], 0.f) + sf.var_zz);
+    const float kphi = 1024.f / (2.f * PI_F);
+    Window w;
+    if (!(dphi < PI_F) || !(fabsf(phip) <= 2.f * PI_F)) {
+        // the whole ring (also for a non-finite prediction)
+        w.nphi = KF_NPHI;
+        w.phi_lo = 0;
+    } else {
+        const int lo = (int)floorf((phip - dphi + PI_F) * kphi);  // within [-1024, 2048]
+        const int hi = (int)floorf((phip + dphi + PI_F) * kphi);
+        w.nphi = max(0, min(hi - lo + 1, KF_NPHI));
+        w.phi_lo = ((lo % KF_NPHI) + KF_NPHI) % KF_NPHI;
+    }
+    const float L = sf.half;
+    const float kz = 64.f / (2.f * L);
+    const float zl = fminf(fmaxf(floorf((Z - dz + L) * kz), 0.f), (float)(KF_NZ - 1));
+    const float zh = fminf(fmaxf(floorf((Z + dz + L) * kz), 0.f), (float)(KF_NZ - 1));
+    w.z_lo = zl == zl ? (int)zl : 0;  // NaN -> 0
+    w.z_hi = zh == zh ? (int)zh : KF_NZ - 1;
+    return w;
+}
+
+// chi2 of one candidate against the predicted state; S shared (f) when the hit
+// covariance does not depend on the hit azimuth, else built for this hit.
+template <class T, class P>
+__device__ __forceinline__ double cand_chi2(const Track<T, P> &st, const float p[21], const Surf &sf, bool shared,
+                                            const Ldl3 &f, float4 h)
+{
+    const auto r0 = resid(h.x, st.x), r1 = resid(h.y, st.y), r2 = resid(h.z, st.z);
+    if (shared) return ldl3_chi2(f, (double)r0, (double)r1, (double)r2);
+    float rxx, rxy, ryy, rzz;
+    meas_cov<float>(sf, h.x, h.y, rxx, rxy, ryy, rzz);
+    Ldl3 g;
+    if (!ldl3((double)(p[pk(0, 0)] + rxx), (double)(p[pk(1, 0)] + rxy), (double)(p[pk(1, 1)] + ryy),
+              (double)p[pk(2, 0)], (double)p[pk(2, 1)], (double)(p[pk(2, 2)] + rzz), g))
+        return -1.0;
+    return ldl3_chi2(g, (double)r0, (double)r1, (double)r2);
+}
+
+template <bool FP64> struct sel_t;
+template <> struct sel_t<true> { using T = double; using P = double; };
+template <> struct sel_t<false> { using T = float; using P = ff; };
+
+// Result of one layer step of one track.
+struct StepOut {
+    int chosen;     // original hit index or -1
+    bool capped;
+};
+
+// Per-thread scoring: walk the window's rows (z ascending, phi from the low edge
+// with wrap, binned order), at most max_cand candidates.
+template <class T, class P>
+__device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[21], const Surf &sf,
+                                          const LayerDev &ly, const Window &w, bool shared, const Ldl3 &fs,
+                                          int max_cand, int &best, double &bchi, float4 &bhit, bool &capped)
+{
+    int ncand = 0;
+    for (int zb = w.z_lo; zb <= w.z_hi && !capped; ++zb) {
+        const int row = zb * KF_NPHI;
+        const int first = w.phi_lo, last = w.phi_lo + w.nphi - 1;
+        for (int part = 0; part < 2 && !capped; ++part) {
+            int b0, b1;  // bin range [b0, b1] in this row
+            if (part == 0) {
+                b0 = first;
+                b1 = min(last, KF_NPHI - 1);
+            } else {
+                if (last < KF_NPHI) break;
+                b0 = 0;
+                b1 = last - KF_NPHI;
+            }
+            const int j0 = max(ly.offsets[row + b0], 0), j1 = min(ly.offsets[row + b1 + 1], ly.n_hits);
+            for (int j = j0; j < j1; ++j) {
+                if (ncand >= max_cand) {
+                    capped = true;
+                    break;
+                }
+                ++ncand;
+                const float4 h = ly.packed[j];
+                const double c2 = cand_chi2(st, pw, sf, shared, fs, h);
+                const int hi = __float_as_int(h.w);
+                if (c2 >= 0.0 && (best < 0 || c2 < bchi || (c2 == bchi && hi < best))) {
+                    best = hi;
+                    bchi = c2;
+                    bhit = h;
+                }
+            }
+        }
+    }
+}
+
+// shared S factor (hit covariance independent of the hit azimuth)
+template <class C>
+__device__ __forceinline__ bool shared_factor(const C pc[21], const Surf &sf, Ldl3 &fs)
+{
+    const C vr = sizeof(C) == 8 ? (C)sf.var_radd : (C)sf.var_rad;
+    const C vz = sizeof(C) == 8 ? (C)sf.var_zzd : (C)sf.var_zz;
+    return ldl3((double)(pc[pk(0, 0)] + vr), (double)pc[pk(1, 0)], (double)(pc[pk(1, 1)] + vr), (double)pc[pk(2, 0)],
+                (double)pc[pk(2, 1)], (double)(pc[pk(2, 2)] + vz), fs);
+}
+
+// One build layer for one track with per-thread scoring: propagate, transport,
+// scattering noise, window, candidates, update.  JOSEPH selects the covariance
+// update form (the FP64 steps).
+template <bool JOSEPH, class T, class P, class C>
+__device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], T alpha, T mass2, const BuildArgs &a,
+                                                     const Surf &sf, const LayerDev &ly, double &chi2,
+                                                     unsigned &status, bool &alive)
+{
+    StepOut o{-1, false};
+    Jac<T> J;
+    if (!propagate(st, alpha, sf, J)) {
+        status |= KF_ST_NO_INTERSECT;
+        alive = false;
+        return o;
+    }
+    transport<C>(pc, JacAs<C>::get(J));
+    if (a.ms_on) status |= ms_noise<T, C>(st, sf, J.cphi1, J.sphi1, mass2, pc);
+    float pw[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pw[i] = (float)pc[i];
+    const Window w = make_window(st, pw, sf, a.nsigma);
+    const bool shared = sf.var_rad == sf.var_rphi;
+    Ldl3 fs{0, 0, 0, 0, 0, 0};
+    if (shared && !shared_factor(pc, sf, fs)) {
+        status |= KF_ST_CHOL_FAIL;
+        alive = false;
+        return o;
+    }
+    int best = -1;
+    double bchi = 0.0;
+    float4 bhit = make_float4(0.f, 0.f, 0.f, 0.f);
+    score_own(st, pw, sf, ly, w, shared, fs, a.max_cand, best, bchi, bhit, o.capped);
+    if (best >= 0 && bchi < (double)a.chi2_cut) {
+        bool ok;
+        if constexpr (JOSEPH) ok = kf_update<true>(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
+        else ok = kf_update_mixed(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
+        if (ok) {
+            o.chosen = best;
+        } else {
+            status |= KF_ST_CHOL_FAIL;
+            alive = false;
+        }
+    }
+    return o;
+}
+
+// FP64 layer step for a mixed-path track at a near-tangent crossing
+__device__ __forceinline__ StepOut layer_step_fp64(Track<float, ff> &st, float pc[21], double alpha, double mass2,
+                                                   const BuildArgs &a, const Surf &sf, const LayerDev &ly,
+                                                   double &chi2, unsigned &status, bool &alive)
+{
+    Track<double, double> sd;
+    sd.x = to_d(st.x);
+    sd.y = to_d(st.y);
+    sd.z = to_d(st.z);
+    sd.phi = to_d(st.phi);
+    sd.th = to_d(st.th);
+    sd.ip = st.ip;
+    double pd[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pd[i] = pc[i];
+    const StepOut o = layer_step_thread<true>(sd, pd, alpha, mass2, a, sf, ly, chi2, status, alive);
+    if (alive) {
+        auto f = [](double d) {
+            float h = (float)d;
+            return ff{h, (float)(d - (double)h)};
+        };
+        st.x = f(sd.x);
+        st.y = f(sd.y);
+        st.z = f(sd.z);
+        st.phi = f(sd.phi);
+        st.th = f(sd.th);
+        st.ip = (float)sd.ip;
+#pragma unroll
+        for (int i = 0; i < 21; ++i) pc[i] = (float)pd[i];
+    }
+    return o;
+}
+
+// Warp-cooperative scoring of one layer: every lane of the warp calls it; lanes
+// with do_step == false contribute no candidates.  Lanes list their window's
+// candidates as consecutive items of one warp-wide list; each round every lane
+// scores one item for the item's owner (predicted position and S factor come by
+// shuffle) and each owner folds its items' chi2 into its best by shuffles.
+template <class T, class P>
+__device__ __forceinline__ void score_coop(const Track<T, P> &st, bool do_step, const Window &w, const Ldl3 &fs,
+                                           const LayerDev &ly, int max_cand, int &best, double &bchi, float4 &bhit,
+                                           bool &capped)
+{
+    const int lane = threadIdx.x & 31;
+    int my_total = 0;
+    if (do_step) {
+        for (int zb = w.z_lo; zb <= w.z_hi; ++zb) {
+            const int row = zb * KF_NPHI;
+            const int first = w.phi_lo, last = w.phi_lo + w.nphi - 1;
+            my_total += ly.offsets[row + min(last, KF_NPHI - 1) + 1] - ly.offsets[row + first];
+            if (last >= KF_NPHI) my_total += ly.offsets[row + (last - KF_NPHI) + 1] - ly.offsets[row];
+        }
+        my_total = max(my_total, 0);
+        if (my_total > max_cand) {
+            capped = true;
+            my_total = max_cand;
+        }
+    }
+    int pre = my_total;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int o = __shfl_up_sync(0xffffffffu, pre, d);
+        if (lane >= d) pre += o;
+    }
+    const int warp_total = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= my_total;
+    const float Xh = (float)lead(st.x), Yh = (float)lead(st.y), Zh = (float)lead(st.z);
+    const float Xl = (float)lo_part(st.x), Yl = (float)lo_part(st.y), Zl = (float)lo_part(st.z);
+    for (int r0 = 0; r0 < warp_total; r0 += 32) {
+        const int item = r0 + lane;
+        // owner: the last lane whose first item is <= item
+        int owner = 0;
+#pragma unroll
+        for (int d = 0; d < 32; ++d) {
+            const int pd_ = __shfl_sync(0xffffffffu, pre, d);
+            if (pd_ <= item) owner = d;
+        }
+        const int opre = __shfl_sync(0xffffffffu, pre, owner);
+        const int ozlo = __shfl_sync(0xffffffffu, w.z_lo, owner);
+        const int ozhi = __shfl_sync(0xffffffffu, w.z_hi, owner);
+        const int oplo = __shfl_sync(0xffffffffu, w.phi_lo, owner);
+        const int onph = __shfl_sync(0xffffffffu, w.nphi, owner);
+        // the owner's layer: lanes of one warp can belong to different events
+        const int32_t *ooff = reinterpret_cast<const int32_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ly.offsets), owner));
+        const float4 *opk = reinterpret_cast<const float4 *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(ly.packed), owner));
+        const int onh = __shfl_sync(0xffffffffu, ly.n_hits, owner);
+        const float oXh = __shfl_sync(0xffffffffu, Xh, owner), oYh = __shfl_sync(0xffffffffu, Yh, owner),
+                    oZh = __shfl_sync(0xffffffffu, Zh, owner);
+        const float oXl = __shfl_sync(0xffffffffu, Xl, owner), oYl = __shfl_sync(0xffffffffu, Yl, owner),
+                    oZl = __shfl_sync(0xffffffffu, Zl, owner);
+        Ldl3 of;
+        of.l21 = __shfl_sync(0xffffffffu, fs.l21, owner);
+        of.l31 = __shfl_sync(0xffffffffu, fs.l31, owner);
+        of.l32 = __shfl_sync(0xffffffffu, fs.l32, owner);
+        of.i1 = __shfl_sync(0xffffffffu, fs.i1, owner);
+        of.i2 = __shfl_sync(0xffffffffu, fs.i2, owner);
+        of.i3 = __shfl_sync(0xffffffffu, fs.i3, owner);
+        double c2 = -1.0;
+        int hidx = 0x7fffffff;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (item < warp_total) {
+            int rem = item - opre;
+            int j = -1;
+            const int last = oplo + onph - 1;
+            for (int zb = ozlo; zb <= ozhi && j < 0; ++zb) {
+                const int row = zb * KF_NPHI;
+                const int a0 = ooff[row + oplo], a1 = ooff[row + min(last, KF_NPHI - 1) + 1];
+                if (rem < a1 - a0) {
+                    j = a0 + rem;
+                    break;
+                }
+                rem -= a1 - a0;
+                if (last >= KF_NPHI) {
+                    const int b0 = ooff[row], b1 = ooff[row + (last - KF_NPHI) + 1];
+                    if (rem < b1 - b0) {
+                        j = b0 + rem;
+                        break;
+                    }
+                    rem -= b1 - b0;
+                }
+            }
+            if (j >= 0 && j < onh) {
+                h = opk[j];
+                hidx = __float_as_int(h.w);
+                const float rx = __fsub_rn(__fsub_rn(h.x, oXh), oXl);
+                const float ry = __fsub_rn(__fsub_rn(h.y, oYh), oYl);
+                const float rz = __fsub_rn(__fsub_rn(h.z, oZh), oZl);
+                c2 = ldl3_chi2(of, (double)rx, (double)ry, (double)rz);
+            }
+        }
+        // each owner folds the round's items that belong to it
+#pragma unroll 1
+        for (int d = 0; d < 32; ++d) {
+            const double dc = __shfl_sync(0xffffffffu, c2, d);
+            const int di = __shfl_sync(0xffffffffu, hidx, d);
+            const int down = __shfl_sync(0xffffffffu, owner, d);
+            const float dhx = __shfl_sync(0xffffffffu, h.x, d), dhy = __shfl_sync(0xffffffffu, h.y, d),
+                        dhz = __shfl_sync(0xffffffffu, h.z, d);
+            if (down == lane && r0 + d < warp_total && dc >= 0.0 &&
+                (best < 0 || dc < bchi || (dc == bchi && di < best))) {
+                best = di;
+                bchi = dc;
+                bhit = make_float4(dhx, dhy, dhz, __int_as_float(di));
+            }
+        }
+    }
+}
+
+// The build keeps the covariance in FP32 on the mixed path after the seed fit
+// (whose updates are the FP64 ones) and in FP64 on the all-FP64 path; a mixed
+// step at a near-tangent crossing runs in FP64.
+template <bool FP64, bool COOP>
+__global__ void __launch_bounds__(128) build_kernel(const Geom g, const BuildArgs a)
+{
+    using T = typename sel_t<FP64>::T;
+    using P = typename sel_t<FP64>::P;
+    using C = T;  // covariance type of the build layers
+    __shared__ Surf s_surf[MAX_SURF];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
+    __syncthreads();
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i0 < a.n;
+    const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real track but write nothing
+    const int t = a.order ? a.order[i] : i;
+    const int n = a.n;
+    const int e = find_event(a.event_off, a.n_events, t);
+    const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
+    Track<T, P> st;
+    st.x = from_f<P>(a.seed_state[0 * n + t]);
+    st.y = from_f<P>(a.seed_state[1 * n + t]);
+    st.z = from_f<P>(a.seed_state[2 * n + t]);
+    st.ip = (T)a.seed_state[3 * n + t];
+    st.phi = from_f<P>(a.seed_state[4 * n + t]);
+    st.th = from_f<P>(a.seed_state[5 * n + t]);
+    const int q = a.q[t];
+    const T alpha = FP64 ? T(-q * g.kbd) : T(-q) * T(g.kb);
+    const T mass2 = FP64 ? T(g.mass2d) : T(g.mass2);
+    const double alphad = -q * g.kbd;
+    unsigned status = 0u;
+    double chi2 = 0.0;
+    int used = 0;
+    bool alive = active;
+    // seed fit over the three seed hits; the first n64 updates with an FP64 covariance
+    double pd[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pd[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
+    C pc[21];
+    const int n1 = min(a.n64, 3);
+    int k = 0;
+    for (; k < n1 && alive; ++k) {
+        const Surf &sf = s_surf[lays[k].surface];
+        const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
+                    hz = a.seed_hits[(3 * k + 2) * n + t];
+        T cphi, sphi;
+        if (k > 0) {
+            Jac<T> J;
+            if (!propagate(st, alpha, sf, J)) {
+                status |= KF_ST_NO_INTERSECT;
+                alive = false;
+                break;
+            }
+            transport<double>(pd, JacAs<double>::get(J));
+            cphi = J.cphi1;
+            sphi = J.sphi1;
+        } else {
+            sincos_pos(st.phi, sphi, cphi);
+        }
+        if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
+        if (!kf_update<true>(st, pd, hx, hy, hz, sf, chi2)) {
+            status |= KF_ST_CHOL_FAIL;
+            alive = false;
+            break;
+        }
+        ++used;
+    }
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pc[i] = (C)pd[i];
+    for (; k < 3 && alive; ++k) {
+        const Surf &sf = s_surf[lays[k].surface];
+        const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
+                    hz = a.seed_hits[(3 * k + 2) * n + t];
+        T cphi, sphi;
+        if (k > 0) {
+            Jac<T> J;
+            if (!propagate(st, alpha, sf, J)) {
+                status |= KF_ST_NO_INTERSECT;
+                alive = false;
+                break;
+            }
+            transport<C>(pc, JacAs<C>::get(J));
+            cphi = J.cphi1;
+            sphi = J.sphi1;
+        } else {
+            sincos_pos(st.phi, sphi, cphi);
+        }
+        if (a.ms_on) status |= ms_noise<T, C>(st, sf, cphi, sphi, mass2, pc);
+        if (!kf_update_mixed(st, pc, hx, hy, hz, sf, chi2)) {
+            status |= KF_ST_CHOL_FAIL;
+            alive = false;
+            break;
+        }
+        ++used;
+    }
+    if (active)
+        for (int L = 0; L < 3; ++L) a.hit_idx[(size_t)L * n + t] = -1;
+    // build layers
+    for (int L = 3; L < a.n_layers; ++L) {
+        const LayerDev ly = lays[L];
+        const Surf &sf = s_surf[ly.surface];
+        StepOut so{-1, false};
+        bool near_tangent = false;
+        if constexpr (!FP64) near_tangent = alive && crossing_sine(st, alpha, sf) > 0.8f;
+        if (near_tangent) {
+            if constexpr (!FP64) so = layer_step_fp64(st, pc, alphad, g.mass2d, a, sf, ly, chi2, status, alive);
+        }
+        // the cooperative path needs the S factor shared by a layer's candidates; the
+        // condition is the same for every lane (all events share the geometry)
+        const bool coop = COOP && sf.var_rad == sf.var_rphi;
+        if (!coop) {
+            if (alive && !near_tangent)
+                so = layer_step_thread<false>(st, pc, alpha, mass2, a, sf, ly, chi2, status, alive);
+        } else {
+            // every lane of the warp takes part in the shuffles, stepping or not
+            bool do_step = alive && !near_tangent;
+            if (do_step) {
+                Jac<T> J;
+                if (!propagate(st, alpha, sf, J)) {
+                    status |= KF_ST_NO_INTERSECT;
+                    alive = false;
+                    do_step = false;
+                } else {
+                    transport<C>(pc, JacAs<C>::get(J));
+                    if (a.ms_on) status |= ms_noise<T, C>(st, sf, J.cphi1, J.sphi1, mass2, pc);
+                }
+            }
+            float pw[21];
+#pragma unroll
+            for (int i = 0; i < 21; ++i) pw[i] = (float)pc[i];
+            Window w{0, 0, 0, -1};
+            Ldl3 fs{0, 0, 0, 0, 0, 0};
+            if (do_step) {
+                w = make_window(st, pw, sf, a.nsigma);
+                if (!shared_factor(pc, sf, fs)) {
+                    status |= KF_ST_CHOL_FAIL;
+                    alive = false;
+                    do_step = false;
+                }
+            }
+            int best = -1;
+            double bchi = 0.0;
+            float4 bhit = make_float4(0.f, 0.f, 0.f, 0.f);
+            score_coop(st, do_step, w, fs, ly, a.max_cand, best, bchi, bhit, so.capped);
+            if (do_step && best >= 0 && bchi < (double)a.chi2_cut) {
+                if (kf_update_mixed(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2)) {
+                    so.chosen = best;
+                } else {
+                    status |= KF_ST_CHOL_FAIL;
+                    alive = false;
+                }
+            }
+        }
+        if (so.capped) status |= KF_ST_CAND_CAPPED;
+        if (so.chosen >= 0) ++used;
+        if (active) a.hit_idx[(size_t)L * n + t] = so.chosen;
+    }
+    if (!active) return;
+    double sv[6] = {to_d(st.x), to_d(st.y), to_d(st.z), (double)st.ip, to_d(st.phi), to_d(st.th)};
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(sv[i])) status |= KF_ST_NONFINITE;
+    if (a.o_state)
+        for (int i = 0; i < 6; ++i) a.o_state[(size_t)i * n + t] = sv[i];
+    if (a.o_cov)
+        for (int i = 0; i < 21; ++i) a.o_cov[(size_t)i * n + t] = (double)pc[i];
+    if (a.o_chi2) a.o_chi2[t] = chi2;
+    if (a.o_ndof) a.o_ndof[t] = 2 * used - 5;
+    if (a.o_status) a.o_status[t] = status;
+}
+
+cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp_coop, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    const int b = 128, grid = (a.n + b - 1) / b;
+    if (fp64) {
+        if (warp_coop) build_kernel<true, true><<<grid, b, 0, st>>>(g, a);
+        else build_kernel<true, false><<<grid, b, 0, st>>>(g, a);
+    } else {
+        if (warp_coop) build_kernel<false, true><<<grid, b, 0, st>>>(g, a);
+        else build_kernel<false, false><<<grid, b, 0, st>>>(g, a);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gather for the final fit
+
+__global__ void gather_count_kernel(int n, int n_layers, const int32_t *__restrict__ hit_idx, int32_t *cnt)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int c = 3;
+    for (int L = 3; L < n_layers; ++L) c += hit_idx[(size_t)L * n + t] >= 0;
+    cnt[t] = c;
+}
+
+// exclusive scan of n counts into off[0..n] (off[n] = total); one block per 1024 entries,
+// then a single-block pass over block sums, then a fix-up (n <= 1024 * 1024 * 64)
+__global__ void __launch_bounds__(1024) block_scan_kernel(int n, const int32_t *__restrict__ in,
+                                                          int32_t *__restrict__ out, int32_t *__restrict__ bsum)
+{
+    __shared__ int32_t wt[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t v = i < n ? in[i] : 0, x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int32_t o = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += o;
+    }
+    if (lane == 31) wt[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t y = wt[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int32_t o = __shfl_up_sync(0xffffffffu, y, d);
+            if (lane >= d) y += o;
+        }
+        wt[lane] = y;
+    }
+    __syncthreads();
+    const int32_t incl = x + (wid > 0 ? wt[wid - 1] : 0);
+    if (i < n) out[i] = incl - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = incl;
+}
+__global__ void bsum_scan_kernel(int nb, int32_t *bsum)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int32_t acc = 0;
+        for (int i = 0; i < nb; ++i) {
+            int32_t v = bsum[i];
+            bsum[i] = acc;
+            acc += v;
+        }
+        bsum[nb] = acc;
+    }
+}
+__global__ void add_bsum_kernel(int n, int32_t *out, const int32_t *__restrict__ bsum, int nb)
+{
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += bsum[blockIdx.x];
+    if (i == 0) out[n] = bsum[nb];
+}
+
+__global__ void gather_fill_kernel(int n, int n_events, int n_layers, const LayerDev *__restrict__ layers,
+                                   const int32_t *__restrict__ eoff, const float *__restrict__ seed_hits,
+                                   const int32_t *__restrict__ hit_idx, const int32_t *__restrict__ off,
+                                   uint8_t *lay_out, float *xo, float *yo, float *zo)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int e = find_event(eoff, n_events, t);
+    const LayerDev *lays = layers + (size_t)e * n_layers;
+    int o = off[t];
+    for (int k = 0; k < 3; ++k) {
+        lay_out[o] = (uint8_t)lays[k].surface;
+        xo[o] = seed_hits[(3 * k + 0) * n + t];
+        yo[o] = seed_hits[(3 * k + 1) * n + t];
+        zo[o] = seed_hits[(3 * k + 2) * n + t];
+        ++o;
+    }
+    for (int L = 3; L < n_layers; ++L) {
+        const int h = hit_idx[(size_t)L * n + t];
+        if (h < 0) continue;
+        const LayerDev ly = lays[L];
+        lay_out[o] = (uint8_t)ly.surface;
+        xo[o] = ly.x[h];
+        yo[o] = ly.y[h];
+        zo[o] = ly.z[h];
+        ++o;
+    }
+}
+
+size_t gather_scratch_bytes(int n) { return ((size_t)n + (size_t)(n / 1024 + 2)) * sizeof(int32_t) + 256; }
+
+cudaError_t launch_gather(int n, int n_events, int n_layers, const LayerDev *layers, const int32_t *event_off,
+                          const float *seed_hits, const int32_t *hit_idx, int32_t *off_out, uint8_t *layer_out,
+                          float *x_out, float *y_out, float *z_out, void *scratch, cudaStream_t st)
+{
+    if (n <= 0) return cudaMemsetAsync(off_out, 0, sizeof(int32_t), st);
+    int32_t *cnt = reinterpret_cast<int32_t *>(scratch);
+    const int nb = (n + 1023) / 1024;
+    int32_t *bsum = cnt + n;
+    gather_count_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, n_layers, hit_idx, cnt);
+    block_scan_kernel<<<nb, 1024, 0, st>>>(n, cnt, off_out, bsum);
+    bsum_scan_kernel<<<1, 32, 0, st>>>(nb, bsum);
+    add_bsum_kernel<<<nb, 1024, 0, st>>>(n, off_out, bsum, nb);
+    gather_fill_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, n_events, n_layers, layers, event_off, seed_hits,
+                                                        hit_idx, off_out, layer_out, x_out, y_out, z_out);
+    return cudaGetLastError();
+}
+
+}  // namespace kfd

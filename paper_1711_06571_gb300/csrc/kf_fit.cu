@@ -1,0 +1,470 @@
+// kf_fit.cu -- seed estimate and Kalman-filter track fit kernels.
+//
+// One thread fits one track: the state and the packed covariance stay in
+// registers across the whole layer loop (Sec. 2: fitting applies the KF over
+// a known hit list with no branching between tracks; Sec. 4.3: one track per
+// thread, structure-of-arrays inputs and outputs so neighbouring threads touch
+// neighbouring addresses).
+#include "kf_internal.h"
+#include "kf_track.cuh"
+
+namespace kfd {
+
+template <bool B, class X, class Y> struct sel { using type = X; };
+template <class X, class Y> struct sel<false, X, Y> { using type = Y; };
+
+__device__ __forceinline__ void load_geom(const Geom &g, Surf *s_surf)
+{
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ seeds
+
+// Seed hits: hit 0, then the first hit >= 2 cm (transverse) from it, then the
+// first later hit >= 2 cm from that one (hits 1, 2 if none).  The distance test
+// is done in FP64 with explicit rounding so it decides exactly as an FP64
+// reference would on the same FP32 inputs.
+__device__ __forceinline__ bool far_enough(float xa, float ya, float xb, float yb)
+{
+    double dx = (double)xb - (double)xa, dy = (double)yb - (double)ya;
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) >= 4.0;
+}
+
+// index of the third seed hit of a track (the rule above)
+__device__ __forceinline__ int seed_hit_last(const float *__restrict__ hx, const float *__restrict__ hy, int nh)
+{
+    int a = -1, b = -1;
+    for (int j = 1; j < nh; ++j)
+        if (far_enough(hx[0], hy[0], hx[j], hy[j])) {
+            a = j;
+            break;
+        }
+    if (a > 0)
+        for (int j = a + 1; j < nh; ++j)
+            if (far_enough(hx[a], hy[a], hx[j], hy[j])) {
+                b = j;
+                break;
+            }
+    return (a < 0 || b < 0) ? 2 : b;
+}
+
+__global__ void __launch_bounds__(128) seed_kernel(int n, const int32_t *__restrict__ off,
+                                                   const float *__restrict__ hx, const float *__restrict__ hy,
+                                                   const float *__restrict__ hz, float kb_abs,
+                                                   float *__restrict__ state, int8_t *__restrict__ qo)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int o = off[t], nh = off[t + 1] - o;
+    if (nh < 3) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) state[i * n + t] = 0.f;
+        qo[t] = 1;
+        return;
+    }
+    int a = -1, b = -1;
+    const float x0 = hx[o], y0 = hy[o];
+    for (int j = 1; j < nh; ++j)
+        if (far_enough(x0, y0, hx[o + j], hy[o + j])) {
+            a = j;
+            break;
+        }
+    if (a > 0)
+        for (int j = a + 1; j < nh; ++j)
+            if (far_enough(hx[o + a], hy[o + a], hx[o + j], hy[o + j])) {
+                b = j;
+                break;
+            }
+    if (a < 0 || b < 0) {
+        a = 1;
+        b = 2;
+    }
+    // circle through three points: signed curvature k = 2 (a x b) / (|a| |b| |b - a|)
+    const float ax = hx[o + a] - x0, ay = hy[o + a] - y0;
+    const float bx = hx[o + b] - x0, by = hy[o + b] - y0;
+    const float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by);
+    const float lab = sqrtf((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+    const float cr = ax * by - ay * bx;
+    const float k = 2.f * cr / (la * lb * lab);
+    const float ak = fabsf(k);
+    const float sg = k > 0.f ? 1.f : (k < 0.f ? -1.f : 0.f);
+    const float arc = ak > 0.f ? 2.f * asinf(fminf(1.f, 0.5f * lb * ak)) / ak : lb;
+    float phi = atan2f(ay, ax) - sg * asinf(fminf(1.f, 0.5f * la * ak));
+    if (phi > PI_F) phi -= 2.f * PI_F;
+    if (phi <= -PI_F) phi += 2.f * PI_F;
+    state[0 * n + t] = x0;
+    state[1 * n + t] = y0;
+    state[2 * n + t] = hz[o];
+    state[3 * n + t] = kb_abs > 0.f ? ak / kb_abs : 0.f;
+    state[4 * n + t] = phi;
+    state[5 * n + t] = atan2f(arc, hz[o + b] - hz[o]);
+    qo[t] = k > 0.f ? (int8_t)-1 : (int8_t)1;
+}
+
+cudaError_t launch_seeds(const Geom &g, int n, const int32_t *off, const float *hx, const float *hy,
+                         const float *hz, float *state, int8_t *q, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    seed_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, off, hx, hy, hz, fabsf(g.kb), state, q);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ fit
+
+template <bool FP64>
+struct FitTypes {
+    using T = typename sel<FP64, double, float>::type;
+    using P = typename sel<FP64, double, ff>::type;
+};
+
+// one surface crossing + update; returns false when the track ends here
+template <bool JOSEPH, class C, class T, class P>
+__device__ __forceinline__ bool fit_step(Track<T, P> &st, C p[21], int k, T alpha, T mass2, int ms_on,
+                                         const Surf &sf, float hx, float hy, float hz, double &chi2,
+                                         unsigned &status)
+{
+    T cphi, sphi;
+    if (k > 0) {
+        Jac<T> J;
+        if (!propagate(st, alpha, sf, J)) {
+            status |= KF_ST_NO_INTERSECT;
+            return false;
+        }
+        transport<C>(p, JacAs<C>::get(J));
+        cphi = J.cphi1;
+        sphi = J.sphi1;
+    } else {
+        sincos_pos(st.phi, sphi, cphi);
+    }
+    if (ms_on) status |= ms_noise<T, C>(st, sf, cphi, sphi, mass2, p);
+    bool ok;
+    if constexpr (JOSEPH) ok = kf_update<true>(st, p, hx, hy, hz, sf, chi2);
+    else ok = kf_update_mixed(st, p, hx, hy, hz, sf, chi2);
+    if (!ok) {
+        status |= KF_ST_CHOL_FAIL;
+        return false;
+    }
+    return true;
+}
+
+// Sine of the crossing angle above which a mixed-path step runs in FP64:
+// cos(alpha) < 0.6 (about 2% of steps on the 17-layer barrel: low-pT tracks
+// meeting a layer close to their apex).
+constexpr float NEAR_TANGENT_SINE = 0.8f;
+
+// A crossing where FP32 cannot carry the transport: barrel, the helix meets the
+// cylinder close to its apex; disk, the direction is close to the disk plane
+// (the incidence cosine is cos(theta)).  Both: cos(alpha) < 0.6.
+__device__ __forceinline__ bool grazing_crossing(const Track<float, ff> &st, float alpha, const Surf &sf)
+{
+    if (sf.kind == 0) return crossing_sine(st, alpha, sf) > NEAR_TANGENT_SINE;
+    float sth, cth;
+    sincos_pos(st.th, sth, cth);
+    return fabsf(cth) < 0.6f;
+}
+
+__device__ __forceinline__ ff ff_from_d(double d)
+{
+    float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+
+// one full step in FP64 for a mixed-path track (state float-float, P float)
+__device__ __forceinline__ bool fp64_step(Track<float, ff> &st, float pf[21], int k, double alpha, double mass2,
+                                       int ms_on, const Surf &sf, float hx, float hy, float hz, double &chi2,
+                                       unsigned &status)
+{
+    Track<double, double> sd;
+    sd.x = to_d(st.x);
+    sd.y = to_d(st.y);
+    sd.z = to_d(st.z);
+    sd.phi = to_d(st.phi);
+    sd.ip = st.ip;
+    sd.th = to_d(st.th);
+    double pd[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pd[i] = pf[i];
+    if (!fit_step<true, double>(sd, pd, k, alpha, mass2, ms_on, sf, hx, hy, hz, chi2, status)) return false;
+    st.x = ff_from_d(sd.x);
+    st.y = ff_from_d(sd.y);
+    st.z = ff_from_d(sd.z);
+    st.phi = ff_from_d(sd.phi);
+    st.ip = (float)sd.ip;
+    st.th = ff_from_d(sd.th);
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pf[i] = (float)pd[i];
+    return true;
+}
+
+template <class C>
+__device__ __forceinline__ void store_cov(double *o_cov, int n, int t, const C p[21])
+{
+    if (!o_cov) return;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) o_cov[(size_t)i * n + t] = (double)p[i];
+}
+
+template <bool FP64>
+__device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *surf, float kb, float mass2f,
+                                          double kbd, double mass2d)
+{
+    using T = typename FitTypes<FP64>::T;
+    using P = typename FitTypes<FP64>::P;
+    const int n = a.n;
+    const int o0 = a.off[t], nh = a.off[t + 1] - o0;
+    Track<T, P> st;
+    st.x = from_f<P>(a.seed_state[0 * n + t]);
+    st.y = from_f<P>(a.seed_state[1 * n + t]);
+    st.z = from_f<P>(a.seed_state[2 * n + t]);
+    st.ip = (T)a.seed_state[3 * n + t];
+    st.phi = from_f<P>(a.seed_state[4 * n + t]);
+    st.th = from_f<P>(a.seed_state[5 * n + t]);
+    const int q = a.q[t];
+    const T alpha = FP64 ? T(-q * kbd) : T(-q) * T(kb);
+    const T mass2 = FP64 ? T(mass2d) : T(mass2f);
+    unsigned status = 0u;
+    double chi2 = 0.0;
+    int used = 0, k = 0;
+    bool alive = true;
+    double pd[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pd[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
+    // phase 1: the first n64 updates with an FP64 covariance, Joseph form, and
+    // at least until the third seed hit (the seed-hit rule) has been used: a
+    // disk/barrel overlap can put two of the first hits a fraction of a mm
+    // apart, and the curvature is only pinned by the third distinct point
+    int n1 = a.n64;
+    if (a.n64 > 0 && nh >= 3) {
+        const int s2 = seed_hit_last(a.hx + o0, a.hy + o0, nh);
+        n1 = max(n1, s2 + 1);
+    }
+    n1 = min(n1, nh);
+    for (; k < n1; ++k) {
+        const int h = o0 + k;
+        if (!fit_step<true, double>(st, pd, k, alpha, mass2, a.ms_on, surf[a.layer[h]], a.hx[h], a.hy[h], a.hz[h],
+                                    chi2, status)) {
+            alive = false;
+            break;
+        }
+        ++used;
+    }
+    if (alive && k < nh) {
+        // phase 2: the rest in T (FP32 on the mixed path), standard form
+        T pf[21];
+#pragma unroll
+        for (int i = 0; i < 21; ++i) pf[i] = (T)pd[i];
+        for (; k < nh; ++k) {
+            const int h = o0 + k;
+            const Surf &sf = surf[a.layer[h]];
+            bool near_tangent = false;
+            if constexpr (!FP64) near_tangent = grazing_crossing(st, alpha, sf);
+            if (near_tangent) {
+                // near-tangent crossing: the whole step in FP64 (Joseph form)
+                if constexpr (!FP64) {
+                    if (!fp64_step(st, pf, k, kbd * (double)(-q), mass2d, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h],
+                                   chi2, status))
+                        break;
+                }
+            } else if (!fit_step<false, T>(st, pf, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
+                                           status)) {
+                break;
+            }
+            ++used;
+        }
+        store_cov(a.o_cov, n, t, pf);
+    } else {
+        store_cov(a.o_cov, n, t, pd);
+    }
+    double sv[6] = {to_d(st.x), to_d(st.y), to_d(st.z), (double)st.ip, to_d(st.phi), to_d(st.th)};
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(sv[i])) status |= KF_ST_NONFINITE;
+    if (a.o_state) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) a.o_state[(size_t)i * n + t] = sv[i];
+    }
+    if (a.o_chi2) a.o_chi2[t] = chi2;
+    if (a.o_ndof) a.o_ndof[t] = 2 * used - 5;
+    if (a.o_status) a.o_status[t] = status;
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(128) fit_kernel(const Geom g, const FitArgs a)
+{
+    __shared__ Surf s_surf[MAX_SURF];
+    load_geom(g, s_surf);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int t = a.order ? a.order[i] : i;
+    fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
+}
+
+// Persistent form: a grid sized to the machine; each warp takes chunks of
+// a.chunk consecutive entries of a.order (tracks sorted by descending hit
+// count, so a warp's 32 tracks cross nearly the same number of layers) from
+// an atomic work counter until the queue is empty (dynamic load balancing in
+// place of the work stealing of Sec. 3.2).
+template <bool FP64, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const Geom g, const FitArgs a)
+{
+    __shared__ Surf s_surf[MAX_SURF];
+    load_geom(g, s_surf);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, a.chunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= a.n) break;
+        const int end = min(base + a.chunk, a.n);
+        for (int i = base + lane; i < end; i += 32) {
+            const int t = a.order ? a.order[i] : i;
+            fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
+        }
+    }
+}
+
+cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    (void)block;
+    const int b = 128;
+    const int grid = (a.n + b - 1) / b;
+    if (fp64)
+        fit_kernel<true><<<grid, b, 0, st>>>(g, a);
+    else
+        fit_kernel<false><<<grid, b, 0, st>>>(g, a);
+    return cudaGetLastError();
+}
+
+template <bool FP64>
+static cudaError_t launch_pers(const Geom &g, const FitArgs &a, int block, int grid, cudaStream_t st)
+{
+    switch (block) {
+    case 64: fit_persistent_kernel<FP64, 64><<<grid, 64, 0, st>>>(g, a); break;
+    case 128: fit_persistent_kernel<FP64, 128><<<grid, 128, 0, st>>>(g, a); break;
+    case 256: fit_persistent_kernel<FP64, 256><<<grid, 256, 0, st>>>(g, a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, int block, int grid, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    return fp64 ? launch_pers<true>(g, a, block, grid, st) : launch_pers<false>(g, a, block, grid, st);
+}
+
+// resident blocks per SM of the persistent kernel at this block size
+int persistent_blocks_per_sm(bool fp64, int block)
+{
+    int nb = 0;
+    cudaError_t e = cudaSuccess;
+    switch (block) {
+    case 64:
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<true, 64>, 64, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<false, 64>, 64, 0);
+        break;
+    case 128:
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<true, 128>, 128, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<false, 128>, 128, 0);
+        break;
+    case 256:
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<true, 256>, 256, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<false, 256>, 256, 0);
+        break;
+    default: return 0;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+// ------------------------------------------------------------------ processing order
+
+// Counting sort of the tracks into buckets of (hit count, descending) x (seed
+// |1/pT|, 64 bins of 1/32 GeV^-1, clamped): a warp then takes 32 tracks that
+// cross nearly the same layers and bend alike, so the layer loop and the
+// near-tangent FP64 steps (low-pT tracks at their apex) diverge little.  The
+// order inside a bucket is that of the atomics, which does not change any
+// track's result.
+constexpr int ORDER_BUCKETS = 65 * 64;
+
+__device__ __forceinline__ int order_key(const int32_t *__restrict__ off, const float *__restrict__ ip, int t)
+{
+    const int nh = off ? min(off[t + 1] - off[t], 64) : 0;
+    const int b = min((int)(fabsf(ip[t]) * 32.f), 63);
+    return (64 - nh) * 64 + b;
+}
+__global__ void order_hist_kernel(int n, const int32_t *__restrict__ off, const float *__restrict__ ip,
+                                  int32_t *hist)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    atomicAdd(&hist[order_key(off, ip, t)], 1);
+}
+__global__ void __launch_bounds__(1024) order_scan_kernel(int32_t *hist)
+{
+    // exclusive scan of ORDER_BUCKETS counts, one block
+    __shared__ int32_t wt[32];
+    constexpr int PER = (ORDER_BUCKETS + 1023) / 1024;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int32_t loc[PER];
+    int32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int i = tid * PER + j;
+        loc[j] = i < ORDER_BUCKETS ? hist[i] : 0;
+        sum += loc[j];
+    }
+    int32_t v = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) wt[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = wt[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int32_t o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        wt[lane] = w;
+    }
+    __syncthreads();
+    int32_t acc = v - sum + (wid > 0 ? wt[wid - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int i = tid * PER + j;
+        if (i < ORDER_BUCKETS) hist[i] = acc;
+        acc += loc[j];
+    }
+}
+__global__ void order_scatter_kernel(int n, const int32_t *__restrict__ off, const float *__restrict__ ip,
+                                     int32_t *hist, int32_t *order)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int pos = atomicAdd(&hist[order_key(off, ip, t)], 1);
+    order[pos] = t;
+}
+
+size_t order_scratch_ints() { return ORDER_BUCKETS; }
+
+cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, int32_t *hist, int32_t *order,
+                         cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(hist, 0, ORDER_BUCKETS * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    const int b = 256, grid = (n + b - 1) / b;
+    order_hist_kernel<<<grid, b, 0, st>>>(n, off, seed_ip, hist);
+    order_scan_kernel<<<1, 1024, 0, st>>>(hist);
+    order_scatter_kernel<<<grid, b, 0, st>>>(n, off, seed_ip, hist, order);
+    return cudaGetLastError();
+}
+
+}  // namespace kfd

@@ -1,0 +1,84 @@
+// kf_internal.h -- host-side declarations shared by the translation units of libkf.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kf_common.cuh"
+
+namespace kfd {
+
+struct FitArgs {
+    int n;
+    int n64;          // updates carried in FP64 (Joseph form) from the seed
+    double seed_cov;
+    int ms_on;
+    int pad_;
+    const float *seed_state;  // [6][n]
+    const int8_t *q;          // [n]
+    const int32_t *off;       // [n+1]
+    const uint8_t *layer;
+    const float *hx, *hy, *hz;
+    double *o_state;   // [6][n]
+    double *o_cov;     // [21][n]
+    double *o_chi2;
+    int32_t *o_ndof;
+    uint32_t *o_status;
+    // persistent schedule
+    const int32_t *order;  // processing order (tracks sorted by hit count), or null
+    int32_t *queue;        // work counter, zeroed before the launch
+    int chunk;             // tracks taken per queue grab (multiple of 32)
+    int pad2_;
+};
+
+// kf_fit.cu
+cudaError_t launch_seeds(const Geom &g, int n, const int32_t *off, const float *hx, const float *hy,
+                         const float *hz, float *state, int8_t *q, cudaStream_t st);
+cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cudaStream_t st);
+cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, int block, int grid, cudaStream_t st);
+int persistent_blocks_per_sm(bool fp64, int block);
+size_t order_scratch_ints();
+cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, int32_t *hist, int32_t *order,
+                         cudaStream_t st);
+
+// kf_bin.cu
+size_t bin_scratch_bytes(int n_hits);
+cudaError_t launch_bin(int n_hits, const float *x, const float *y, const float *z, double half_len, int32_t *perm,
+                       int32_t *offsets, float *packed, void *scratch, cudaStream_t st);
+
+// kf_build.cu
+struct LayerDev {
+    const float4 *packed;
+    const int32_t *offsets;
+    const float *x, *y, *z;  // original order
+    int n_hits;
+    int surface;
+};
+struct BuildArgs {
+    int n;
+    int n_events;
+    int n_layers;
+    int n64;
+    double seed_cov;
+    int ms_on;
+    int max_cand;
+    float nsigma;
+    float chi2_cut;
+    const LayerDev *layers;       // device [n_events][n_layers]
+    const int32_t *event_off;     // device [n_events + 1]
+    const float *seed_state;      // [6][n]
+    const int8_t *q;
+    const float *seed_hits;       // [9][n]
+    int32_t *hit_idx;             // [n_layers][n]
+    const int32_t *order;         // processing order (by seed 1/pT), or null
+    double *o_state, *o_cov, *o_chi2;
+    int32_t *o_ndof;
+    uint32_t *o_status;
+};
+cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp_coop, cudaStream_t st);
+size_t gather_scratch_bytes(int n);
+cudaError_t launch_gather(int n, int n_events, int n_layers, const LayerDev *layers, const int32_t *event_off,
+                          const float *seed_hits, const int32_t *hit_idx, int32_t *off_out, uint8_t *layer_out,
+                          float *x_out, float *y_out, float *z_out, void *scratch, cudaStream_t st);
+
+}  // namespace kfd

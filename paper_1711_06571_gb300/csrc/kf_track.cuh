@@ -1,0 +1,431 @@
+// kf_track.cuh -- per-track Kalman-filter steps, held in registers.
+//
+// One thread owns one track: state (x, y, z, 1/pT, phi, theta) and the packed
+// 21-entry covariance live in registers for the whole layer loop.  Two type
+// parameters select the precision:
+//   T: arithmetic of propagation, Jacobian, transport and update
+//      (float on the mixed path, double on the all-FP64 path)
+//   P: storage of x, y, z, phi and theta (float-float on the mixed path, double):
+//      FP32 storage alone would round these by ~1e-4 of their fitted sigma at
+//      every update (100 cm, pi), which adds up over a 17-layer fit
+// The 3x3 innovation-covariance solve is always FP64 (kf_common.cuh).
+#pragma once
+
+#include "kf_common.cuh"
+
+namespace kfd {
+
+// packed lower-triangle index, i >= j
+__host__ __device__ constexpr int pk(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+template <class T, class P>
+struct Track {
+    P x, y, z, phi, th;  // extended precision (float-float on the mixed path)
+    T ip;
+};
+
+// Pieces of the surface-constrained propagation Jacobian J = A + u w^T:
+//   A = I + {ax3, ax4 (row x), ay3, ay4 (row y), az5 (row z), ap3 (row phi)},
+//   u = d(state)/ds on rows x, y, z, phi, w = ds/d(state).
+template <class T>
+struct Jac {
+    T ax3, ax4, ay3, ay4, az5, ap3;
+    T u0, u1, u2, u4;
+    T w[6];
+    T cphi1, sphi1;  // cos, sin of the new phi
+};
+
+template <class T> __device__ __forceinline__ T tsqrt(T v);
+template <> __device__ __forceinline__ float tsqrt<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double tsqrt<double>(double v) { return sqrt(v); }
+__device__ __forceinline__ void tsincos(float a, float &s, float &c) { sincosf(a, &s, &c); }
+__device__ __forceinline__ void tsincos(double a, double &s, double &c) { sincos(a, &s, &c); }
+__device__ __forceinline__ float tlog(float v) { return logf(v); }
+__device__ __forceinline__ double tlog(double v) { return log(v); }
+
+template <class T> __device__ __forceinline__ T spos(const Surf &s);
+template <> __device__ __forceinline__ float spos<float>(const Surf &s) { return s.pos; }
+template <> __device__ __forceinline__ double spos<double>(const Surf &s) { return s.posd; }
+template <class T> __device__ __forceinline__ T sxx0(const Surf &s);
+template <> __device__ __forceinline__ float sxx0<float>(const Surf &s) { return s.x_x0; }
+template <> __device__ __forceinline__ double sxx0<double>(const Surf &s) { return s.x_x0d; }
+
+__device__ __forceinline__ float lo_part(ff a) { return a.lo; }
+__device__ __forceinline__ double lo_part(double) { return 0.0; }
+__device__ __forceinline__ float sub_lead(float Z, ff z) { return __fsub_rn(__fsub_rn(Z, z.hi), z.lo); }
+__device__ __forceinline__ double sub_lead(double Z, double z) { return Z - z; }
+__device__ __forceinline__ ff set_exact(float Z, ff) { return {Z, 0.f}; }
+__device__ __forceinline__ double set_exact(double Z, double) { return Z; }
+
+constexpr float MAX_PATH = 1.0e6f;  // longer transverse paths count as no intersection
+
+// Propagate st along its helix to surface sf (Sec. 3 uniform field, Sec. 4.1
+// propagation to the layer).  Barrel from inside: first crossing s > 0, found
+// by Newton steps on |pos(s)|^2 - R^2 (to working precision, at most 12) from
+// the second-order (parabolic) estimate; from outside: the crossing nearest s = 0.  Disk: s = (Z - z) tan(theta).
+// alpha = -q * kappa * Bz (c = alpha / pT).  Returns false (state untouched)
+// when the surface is not reached.
+template <class T, class P>
+__device__ __forceinline__ bool propagate(Track<T, P> &st, T alpha, const Surf &sf, Jac<T> &J)
+{
+    T c = alpha * st.ip;
+    T sphi, cphi;
+    sincos_pos(st.phi, sphi, cphi);
+    T sth, cth;
+    sincos_pos(st.th, sth, cth);
+    T cot = cth / sth;
+    T s;
+    const T X = lead(st.x), Y = lead(st.y);
+    if (sf.kind == 0) {
+        const T R = spos<T>(sf);
+        const T g0 = radial_excess(st.x, st.y, R * R);
+        const T pt = X * cphi + Y * sphi, pn = -X * sphi + Y * cphi;
+        const bool inside = g0 < T(0);
+        if (inside) {
+            // the helix circle reaches radius R iff |c| (R^2 - r^2) - 2 sgn(c) (p.n) <= 2 R
+            T sg = c > T(0) ? T(1) : (c < T(0) ? T(-1) : T(0));
+            if (fabs(c) * (-g0) - T(2) * sg * pn > T(2) * R) return false;
+        }
+        // second-order model |pos(s)|^2 - R^2 ~ A s^2 + 2 pt s + g0, A = 1 + c (p.n);
+        // A < 0 near the apex of a curling track
+        const T A = T(1) + c * pn;
+        const T disc = pt * pt - A * g0;
+        if (disc >= T(0)) {
+            T sq = tsqrt<T>(disc);
+            T den = inside ? (pt + sq) : (pt + copysign(sq, pt));
+            s = -g0 / den;  // root nearest s = 0 in the direction of motion
+        } else {
+            s = -pt / A;  // the model's apex; Newton on the exact helix takes it from there
+        }
+        const T xl = lo_part(st.x), yl = lo_part(st.y);
+        // Newton on the exact helix until the step is below the working precision
+        const T tol = sizeof(T) == 8 ? T(1e-13) : T(2e-7);
+        for (int it = 0; it < 12; ++it) {
+            T sinc, ch, sh, f1;
+            helix_factors(T(0.5) * c * s, sinc, ch, sh, f1);
+            T cm = cphi * ch - sphi * sh, sm = sphi * ch + cphi * sh;
+            T dx = s * sinc * cm, dy = s * sinc * sm;
+            T g = g0 + T(2) * ((X + xl) * dx + (Y + yl) * dy) + dx * dx + dy * dy;
+            T c1 = cm * ch - sm * sh, s1 = sm * ch + cm * sh;
+            T gp = T(2) * ((X + dx) * c1 + (Y + dy) * s1);
+            T ds = g / gp;
+            s = s - ds;
+            if (!(fabs(ds) > tol * (fabs(s) + T(1)))) break;
+        }
+        if (!isfinite(s) || (inside && !(s > T(0)))) return false;
+    } else {
+        if (cot == T(0)) return false;
+        s = sub_lead(spos<T>(sf), st.z) / cot;
+        if (!(fabs(s) <= T(MAX_PATH))) return false;
+    }
+    T sinc, ch, sh, f1;
+    helix_factors(T(0.5) * c * s, sinc, ch, sh, f1);
+    T cm = cphi * ch - sphi * sh, sm = sphi * ch + cphi * sh;  // direction of the chord
+    T dx = s * sinc * cm, dy = s * sinc * sm;
+    T c1 = cm * ch - sm * sh, s1 = sm * ch + cm * sh;  // new direction
+    T s2 = s * s;
+    J.ax4 = -dy;
+    J.ay4 = dx;
+    J.ax3 = alpha * s2 * (cm * f1 - sm * T(0.5) * sinc);
+    J.ay3 = alpha * s2 * (sm * f1 + cm * T(0.5) * sinc);
+    J.az5 = -s / (sth * sth);
+    J.ap3 = alpha * s;
+    J.u0 = c1;
+    J.u1 = s1;
+    J.u2 = cot;
+    J.u4 = c;
+    J.cphi1 = c1;
+    J.sphi1 = s1;
+    const P nx = inc(st.x, dx), ny = inc(st.y, dy);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) J.w[j] = T(0);
+    if (sf.kind == 0) {
+        const T xp = lead(nx), yp = lead(ny);
+        T D = xp * c1 + yp * s1;  // (1/2) d|pos|^2/ds
+        if (D == T(0)) return false;
+        T iD = T(1) / D;
+        J.w[0] = -xp * iD;
+        J.w[1] = -yp * iD;
+        J.w[3] = -(xp * J.ax3 + yp * J.ay3) * iD;
+        J.w[4] = -(xp * J.ax4 + yp * J.ay4) * iD;
+        st.z = inc(st.z, s * cot);
+    } else {
+        T ic = T(1) / cot;
+        J.w[2] = -ic;
+        J.w[5] = -J.az5 * ic;
+        st.z = set_exact(spos<T>(sf), st.z);
+    }
+    st.x = nx;
+    st.y = ny;
+    st.phi = wrap(inc(st.phi, c * s));
+    return true;
+}
+
+// Sine of the angle between track and radial direction where the helix meets
+// the cylinder R, from the state before propagation: for the helix circle
+// (radius 1/|c|, centre C) and the cylinder, the triangle origin-C-crossing
+// gives u = (|c| (R^2 - r^2) - 2 sgn(c) (p.n)) / (2 R), n = (-sin phi, cos phi).
+// u > 1: the cylinder is out of reach; u -> 1: the crossing is tangent, where
+// the surface-constrained Jacobian grows like 1 / cos(alpha) and FP32 loses
+// the covariance transport.
+template <class T, class P>
+__device__ __forceinline__ T crossing_sine(const Track<T, P> &st, T alpha, const Surf &sf)
+{
+    T c = alpha * st.ip;
+    T sphi, cphi;
+    sincos_pos(st.phi, sphi, cphi);
+    const T X = lead(st.x), Y = lead(st.y);
+    const T R = spos<T>(sf);
+    const T g0 = radial_excess(st.x, st.y, R * R);
+    const T pn = -X * sphi + Y * cphi;
+    T sg = c > T(0) ? T(1) : (c < T(0) ? T(-1) : T(0));
+    return (fabs(c) * (-g0) - T(2) * sg * pn) / (T(2) * R);
+}
+
+// P <- J P J^T with J = A + u w^T, as A P A^T + a u^T + u a^T + gamma u u^T,
+// y = P w, a = A y, gamma = w.y; A has six off-diagonal entries and u two
+// structural zeros, so the product costs ~150 FMA instead of ~430 dense.
+template <class T>
+__device__ __forceinline__ void transport(T p[21], const Jac<T> &J)
+{
+    T y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T v = T(0);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) v += p[pk(i, j)] * J.w[j];
+        y[i] = v;
+    }
+    T gam = T(0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gam += J.w[i] * y[i];
+    T a[6];
+    a[0] = y[0] + J.ax3 * y[3] + J.ax4 * y[4];
+    a[1] = y[1] + J.ay3 * y[3] + J.ay4 * y[4];
+    a[2] = y[2] + J.az5 * y[5];
+    a[3] = y[3];
+    a[4] = y[4] + J.ap3 * y[3];
+    a[5] = y[5];
+    // B = A P
+    T B[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        T p3 = p[pk(3, j)], p4 = p[pk(4, j)], p5 = p[pk(5, j)];
+        B[0][j] = p[pk(0, j)] + J.ax3 * p3 + J.ax4 * p4;
+        B[1][j] = p[pk(1, j)] + J.ay3 * p3 + J.ay4 * p4;
+        B[2][j] = p[pk(2, j)] + J.az5 * p5;
+        B[3][j] = p3;
+        B[4][j] = p4 + J.ap3 * p3;
+        B[5][j] = p5;
+    }
+    const T u[6] = {J.u0, J.u1, J.u2, T(0), J.u4, T(0)};
+    // C = B A^T (lower triangle) plus the rank-2 terms
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            T v;
+            if (j == 0) v = B[i][0] + J.ax3 * B[i][3] + J.ax4 * B[i][4];
+            else if (j == 1) v = B[i][1] + J.ay3 * B[i][3] + J.ay4 * B[i][4];
+            else if (j == 2) v = B[i][2] + J.az5 * B[i][5];
+            else if (j == 4) v = B[i][4] + J.ap3 * B[i][3];
+            else v = B[i][j];
+            if (i != 3 && i != 5) v += u[i] * a[j];
+            if (j != 3 && j != 5) v += a[i] * u[j];
+            if (i != 3 && i != 5 && j != 3 && j != 5) v += gam * u[i] * u[j];
+            p[pk(i, j)] = v;
+        }
+    }
+}
+
+// Widen a float Jacobian for an FP64 transport.
+__device__ __forceinline__ Jac<double> widen(const Jac<float> &J)
+{
+    Jac<double> D;
+    D.ax3 = J.ax3; D.ax4 = J.ax4; D.ay3 = J.ay3; D.ay4 = J.ay4; D.az5 = J.az5; D.ap3 = J.ap3;
+    D.u0 = J.u0; D.u1 = J.u1; D.u2 = J.u2; D.u4 = J.u4;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) D.w[j] = J.w[j];
+    D.cphi1 = J.cphi1;
+    D.sphi1 = J.sphi1;
+    return D;
+}
+__device__ __forceinline__ const Jac<double> &widen(const Jac<double> &J) { return J; }
+
+// the Jacobian in the covariance's type C
+template <class C> struct JacAs;
+template <> struct JacAs<float> {
+    __device__ static const Jac<float> &get(const Jac<float> &J) { return J; }
+};
+template <> struct JacAs<double> {
+    __device__ static Jac<double> get(const Jac<float> &J) { return widen(J); }
+    __device__ static const Jac<double> &get(const Jac<double> &J) { return J; }
+};
+
+// Multiple scattering (Sec. 2), Highland angle with p = pT / sin(theta) and
+// thickness t = (x/X0) / max(|cos alpha|, 0.05):
+//   theta0 = 0.0136 (1/p) sqrt(1 + m^2/p^2) sqrt(t) (1 + 0.038 ln(t (1 + m^2/p^2)))
+// (the PDG form with 1/beta = sqrt(1 + m^2/p^2)); P_theta += theta0^2,
+// P_phi += theta0^2 / sin^2(theta).  Returns KF_ST_GRAZING if the guard was used.
+template <class T, class C, class Pp>
+__device__ __forceinline__ unsigned ms_noise(const Track<T, Pp> &st, const Surf &sf, T cphi, T sphi, T mass2, C p[21])
+{
+    T xx0 = sxx0<T>(sf);
+    if (!(xx0 > T(0))) return 0u;
+    T sth, cth;
+    sincos_pos(st.th, sth, cth);
+    T ca;
+    if (sf.kind == 0) {
+        T X = lead(st.x), Y = lead(st.y);
+        ca = sth * (X * cphi + Y * sphi) / tsqrt<T>(X * X + Y * Y);
+    } else {
+        ca = cth;
+    }
+    ca = fabs(ca);
+    unsigned flag = 0u;
+    if (ca < T(0.05)) {
+        ca = T(0.05);
+        flag = KF_ST_GRAZING;
+    }
+    T t = xx0 / ca;
+    T invp = fabs(st.ip) * sth;
+    if (invp > T(0)) {
+        T ib2 = T(1) + mass2 * invp * invp;
+        T th0 = T(0.0136) * invp * tsqrt<T>(ib2) * tsqrt<T>(t) * (T(1) + T(0.038) * tlog(t * ib2));
+        T th02 = th0 * th0;
+        p[pk(5, 5)] += C(th02);
+        p[pk(4, 4)] += C(th02 / (sth * sth));
+    }
+    return flag;
+}
+
+// Hit covariance R at the hit azimuth (Sec. 4.1 tangent plane):
+// variance var_rad along r-hat, var_rphi along phi-hat, var_zz along z.
+template <class T>
+__device__ __forceinline__ void meas_cov(const Surf &sf, float hx, float hy, T &rxx, T &rxy, T &ryy, T &rzz)
+{
+    const bool d = sizeof(T) == 8;
+    T a = d ? T(sf.var_radd) : T(sf.var_rad), b = d ? T(sf.var_rphid) : T(sf.var_rphi);
+    rzz = d ? T(sf.var_zzd) : T(sf.var_zz);
+    if (a == b) {
+        rxx = a;
+        ryy = a;
+        rxy = T(0);
+        return;
+    }
+    T r2 = T(hx) * T(hx) + T(hy) * T(hy);
+    T cs = T(hx), sn = T(hy);
+    T ir2 = T(1) / r2;
+    rxx = (a * cs * cs + b * sn * sn) * ir2;
+    rxy = (a - b) * cs * sn * ir2;
+    ryy = (a * sn * sn + b * cs * cs) * ir2;
+}
+
+__device__ __forceinline__ void add_inc(ff &a, double d)
+{
+    float h = (float)d;
+    a = ff_add(a, h);
+    a = ff_add(a, (float)(d - (double)h));
+}
+__device__ __forceinline__ void add_inc(double &a, double d) { a += d; }
+__device__ __forceinline__ void add_inc(ff &a, float d) { a = ff_add(a, d); }
+__device__ __forceinline__ void add_inc(float &a, double d) { a = (float)((double)a + d); }
+__device__ __forceinline__ void add_inc(float &a, float d) { a += d; }
+
+// Kalman update with the 3-D hit, H = [I3 | 0] (Sec. 4.1):
+//   r = m - x, S = P_pos + R, chi2 = r^T S^-1 r (FP64 LDL^T),
+//   K = P H^T S^-1, x += K r,
+//   JOSEPH = false: P -= K (H P)                          (standard form)
+//   JOSEPH = true:  P = (I - K H) P (I - K H)^T + K R K^T  (Joseph form, written
+//                   as P - K G^T + (K S - G) K^T with G = P H^T; stays positive
+//                   definite under the 1e4 seed covariance)
+// C is the covariance type; returns false if S is not positive definite.
+template <bool JOSEPH, class C, class T, class Pp>
+__device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, float hy, float hz, const Surf &sf,
+                                          double &chi2)
+{
+    const auto r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);  // float or double
+    C rxx, rxy, ryy, rzz;
+    meas_cov<C>(sf, hx, hy, rxx, rxy, ryy, rzz);
+    C s11 = p[pk(0, 0)] + rxx, s21 = p[pk(1, 0)] + rxy, s22 = p[pk(1, 1)] + ryy;
+    C s31 = p[pk(2, 0)], s32 = p[pk(2, 1)], s33 = p[pk(2, 2)] + rzz;
+    Ldl3 f;
+    if (!ldl3((double)s11, (double)s21, (double)s22, (double)s31, (double)s32, (double)s33, f)) return false;
+    chi2 += ldl3_chi2(f, (double)r0, (double)r1, (double)r2);
+    C a11, a21, a22, a31, a32, a33;
+    ldl3_inverse<C>(f, a11, a21, a22, a31, a32, a33);
+    C G[6][3], K[6][3];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        G[i][0] = p[pk(i, 0)];
+        G[i][1] = p[pk(i, 1)];
+        G[i][2] = p[pk(i, 2)];
+        K[i][0] = G[i][0] * a11 + G[i][1] * a21 + G[i][2] * a31;
+        K[i][1] = G[i][0] * a21 + G[i][1] * a22 + G[i][2] * a32;
+        K[i][2] = G[i][0] * a31 + G[i][1] * a32 + G[i][2] * a33;
+    }
+    C d[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d[i] = K[i][0] * C(r0) + K[i][1] * C(r1) + K[i][2] * C(r2);
+    add_inc(st.x, d[0]);
+    add_inc(st.y, d[1]);
+    add_inc(st.z, d[2]);
+    add_inc(st.ip, d[3]);
+    add_inc(st.phi, d[4]);
+    st.phi = wrap(st.phi);
+    add_inc(st.th, d[5]);  // float-float or double
+    if (JOSEPH) {
+        C W[6][3];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            W[i][0] = K[i][0] * s11 + K[i][1] * s21 + K[i][2] * s31 - G[i][0];
+            W[i][1] = K[i][0] * s21 + K[i][1] * s22 + K[i][2] * s32 - G[i][1];
+            W[i][2] = K[i][0] * s31 + K[i][1] * s32 + K[i][2] * s33 - G[i][2];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j)
+                p[pk(i, j)] = p[pk(i, j)] - (K[i][0] * G[j][0] + K[i][1] * G[j][1] + K[i][2] * G[j][2]) +
+                              (W[i][0] * K[j][0] + W[i][1] * K[j][1] + W[i][2] * K[j][2]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j)
+                p[pk(i, j)] -= K[i][0] * G[j][0] + K[i][1] * G[j][1] + K[i][2] * G[j][2];
+    }
+    return true;
+}
+
+// Update on the mixed path (FP32 covariance).  When the prior position variance
+// exceeds the smallest hit variance by more than 1e3 (after a run of layers
+// without an accepted hit, or a long extrapolation) the standard form cancels
+// more digits than FP32 holds, so that update runs in FP64, Joseph form.
+constexpr float UPDATE_FP64_RATIO = 1e3f;
+
+template <class Pp>
+__device__ __forceinline__ bool kf_update_mixed(Track<float, Pp> &st, float p[21], float hx, float hy, float hz,
+                                                const Surf &sf, double &chi2)
+{
+    const float pmax = fmaxf(p[pk(0, 0)], fmaxf(p[pk(1, 1)], p[pk(2, 2)]));
+    const float rmin = fminf(sf.var_rad, fminf(sf.var_rphi, sf.var_zz));
+    if (pmax > UPDATE_FP64_RATIO * rmin) {
+        double pd[21];
+#pragma unroll
+        for (int i = 0; i < 21; ++i) pd[i] = p[i];
+        const bool ok = kf_update<true>(st, pd, hx, hy, hz, sf, chi2);
+#pragma unroll
+        for (int i = 0; i < 21; ++i) p[i] = (float)pd[i];
+        return ok;
+    }
+    return kf_update<false>(st, p, hx, hy, hz, sf, chi2);
+}
+template <class Pp>
+__device__ __forceinline__ bool kf_update_mixed(Track<double, Pp> &st, double p[21], float hx, float hy, float hz,
+                                                const Surf &sf, double &chi2)
+{
+    return kf_update<false>(st, p, hx, hy, hz, sf, chi2);
+}
+
+}  // namespace kfd

@@ -1,0 +1,279 @@
+"""Thin Python binding of libkf.so (include/kf.h): ctypes structures with the
+same layout and functions with the same names, taking torch CUDA tensors.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Importing works without a GPU; any call raises if the library has
+not been built (no fallback of any kind).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libkf.so")
+
+KF_OK = 0
+KF_EINVAL = -1
+KF_ENOMEM = -2
+KF_ECUDA = -3
+KF_ETIMEOUT = -4
+KF_EAGAIN = -5
+KF_EBUSY = -6
+
+KF_ST_NO_INTERSECT = 1
+KF_ST_CHOL_FAIL = 2
+KF_ST_NONFINITE = 4
+KF_ST_CAND_CAPPED = 8
+KF_ST_GRAZING = 16
+
+KF_PREC_MIXED = 0
+KF_PREC_FP64 = 1
+KF_SCHED_GRID = 0
+KF_SCHED_PERSISTENT = 1
+KF_MAX_SURFACES = 64
+KF_NPHI = 1024
+KF_NZ = 64
+KF_NBINS = KF_NPHI * KF_NZ
+
+
+class KfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libkf error {code}: {msg}")
+        self.code = code
+
+
+class kf_surface(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("pos", C.c_double), ("half_or_rin", C.c_double),
+                ("r_out", C.c_double), ("x_x0", C.c_double), ("sig_n", C.c_double), ("sig_rphi", C.c_double),
+                ("sig_3", C.c_double)]
+
+
+class kf_geometry(C.Structure):
+    _fields_ = [("bz", C.c_double), ("mass", C.c_double), ("n_surfaces", C.c_int32), ("pad_", C.c_int32),
+                ("surfaces", C.POINTER(kf_surface))]
+
+
+class kf_fit_params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("n_fp64_updates", C.c_int32), ("seed_cov", C.c_double),
+                ("ms_on", C.c_int32), ("schedule", C.c_int32)]
+
+
+class kf_seeds(C.Structure):
+    _fields_ = [("state", C.c_void_p), ("q", C.c_void_p)]
+
+
+class kf_track_hits(C.Structure):
+    _fields_ = [("offsets", C.c_void_p), ("layer", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p),
+                ("z", C.c_void_p)]
+
+
+class kf_tracks_out(C.Structure):
+    _fields_ = [("state", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p), ("ndof", C.c_void_p),
+                ("status", C.c_void_p)]
+
+
+class kf_binned_layer(C.Structure):
+    _fields_ = [("n_hits", C.c_int32), ("surface", C.c_int32), ("packed", C.c_void_p), ("offsets", C.c_void_p),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p)]
+
+
+class kf_build_params(C.Structure):
+    _fields_ = [("nsigma", C.c_double), ("chi2_cut", C.c_double), ("max_cand", C.c_int32),
+                ("warp_coop", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes); every symbol of include/kf.h
+_SIGS = {
+    "kf_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_size_t]),
+    "kf_ctx_destroy": (None, [C.c_void_p]),
+    "kf_ctx_last_error": (C.c_char_p, [C.c_void_p]),
+    "kf_version": (C.c_char_p, []),
+    "kf_make_seeds": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.c_int32, C.POINTER(kf_track_hits),
+                                C.c_void_p, C.c_void_p, C.c_void_p]),
+    "kf_fit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
+                         C.POINTER(kf_seeds), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out), C.c_void_p]),
+    "kf_autotune_fit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
+                                  C.POINTER(kf_seeds), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out),
+                                  C.c_void_p, C.c_char_p, C.c_size_t]),
+    "kf_bin_hits": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p]),
+    "kf_build_besthit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params),
+                                   C.POINTER(kf_build_params), C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
+                                   C.POINTER(C.c_int32), C.POINTER(kf_seeds), C.c_void_p, C.c_void_p,
+                                   C.POINTER(kf_tracks_out), C.c_void_p]),
+    "kf_gather_hits": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
+                                 C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libkf.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libkf.so not found at {path}: build it with "
+                                   "paper_1711_06571_gb300.build.build() (there is no CPU fallback)")
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(ctx, rc):
+    if rc != KF_OK:
+        msg = load().kf_ctx_last_error(ctx)
+        raise KfError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def make_geometry(geom: dict):
+    """kf_geometry from a geometry dict (synth.geometry); keeps the surface array alive."""
+    surfs = geom["surfaces"]
+    arr = (kf_surface * len(surfs))()
+    for i, s in enumerate(surfs):
+        arr[i].kind = int(s["kind"])
+        arr[i].pos = float(s["pos"])
+        arr[i].half_or_rin = float(s["half_or_rin"])
+        arr[i].r_out = float(s.get("r_out", 0.0))
+        arr[i].x_x0 = float(s["x_x0"])
+        arr[i].sig_n = float(s["sig_n"])
+        arr[i].sig_rphi = float(s["sig_rphi"])
+        arr[i].sig_3 = float(s["sig_3"])
+    g = kf_geometry(bz=float(geom["bz"]), mass=float(geom["mass"]), n_surfaces=len(surfs),
+                    surfaces=C.cast(arr, C.POINTER(kf_surface)))
+    g._keep = arr
+    return g
+
+
+def fit_params(precision=KF_PREC_MIXED, n_fp64_updates=3, seed_cov=1e4, ms_on=True, schedule=KF_SCHED_GRID):
+    return kf_fit_params(precision=int(precision), n_fp64_updates=int(n_fp64_updates), seed_cov=float(seed_cov),
+                         ms_on=int(bool(ms_on)), schedule=int(schedule))
+
+
+# ---------------------------------------------------------------- entry points (same names as kf.h)
+
+def kf_version() -> str:
+    return load().kf_version().decode()
+
+
+def kf_ctx_create(device: int = 0, budget: int = 0):
+    h = C.c_void_p()
+    rc = load().kf_ctx_create(C.byref(h), int(device), C.c_size_t(int(budget)))
+    if rc != KF_OK:
+        raise KfError(rc, "kf_ctx_create failed")
+    return h
+
+
+def kf_ctx_destroy(ctx):
+    load().kf_ctx_destroy(ctx)
+
+
+def kf_ctx_last_error(ctx) -> str:
+    m = load().kf_ctx_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def kf_make_seeds(ctx, geom, n, offsets, x, y, z, state_out, q_out, stream=None):
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    h = kf_track_hits(_ptr(offsets), None, _ptr(x), _ptr(y), _ptr(z))
+    _check(ctx, load().kf_make_seeds(ctx, C.byref(g), int(n), C.byref(h), _ptr(state_out), _ptr(q_out),
+                                     _stream(stream)))
+
+
+def kf_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, out_state=None, out_cov=None,
+           out_chi2=None, out_ndof=None, out_status=None, stream=None):
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    p = params if params is not None else fit_params()
+    s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
+    h = kf_track_hits(_ptr(offsets), _ptr(layer), _ptr(x), _ptr(y), _ptr(z))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    _check(ctx, load().kf_fit(ctx, C.byref(g), C.byref(p), int(n), C.byref(s), C.byref(h), C.byref(o),
+                              _stream(stream)))
+
+
+def kf_autotune_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, out_state=None,
+                    out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None) -> str:
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    p = params if params is not None else fit_params()
+    s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
+    h = kf_track_hits(_ptr(offsets), _ptr(layer), _ptr(x), _ptr(y), _ptr(z))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    buf = C.create_string_buffer(128)
+    _check(ctx, load().kf_autotune_fit(ctx, C.byref(g), C.byref(p), int(n), C.byref(s), C.byref(h), C.byref(o),
+                                       _stream(stream), buf, 128))
+    return buf.value.decode()
+
+
+def kf_bin_hits(ctx, n_hits, x, y, z, half_len, perm_out, offsets_out, packed_out=None, stream=None):
+    _check(ctx, load().kf_bin_hits(ctx, int(n_hits), _ptr(x), _ptr(y), _ptr(z), float(half_len), _ptr(perm_out),
+                                   _ptr(offsets_out), _ptr(packed_out), _stream(stream)))
+
+
+def binned_layers(layer_dicts):
+    """kf_binned_layer array from dicts with n_hits, surface and tensors packed, offsets (and x, y, z)."""
+    arr = (kf_binned_layer * len(layer_dicts))()
+    for i, d in enumerate(layer_dicts):
+        arr[i].n_hits = int(d["n_hits"])
+        arr[i].surface = int(d["surface"])
+        arr[i].packed = _ptr(d.get("packed"))
+        arr[i].offsets = _ptr(d.get("offsets"))
+        arr[i].x = _ptr(d.get("x"))
+        arr[i].y = _ptr(d.get("y"))
+        arr[i].z = _ptr(d.get("z"))
+    return arr
+
+
+def build_params(nsigma=3.0, chi2_cut=30.0, max_cand=32, warp_coop=False):
+    return kf_build_params(nsigma=float(nsigma), chi2_cut=float(chi2_cut), max_cand=int(max_cand),
+                           warp_coop=int(bool(warp_coop)))
+
+
+def kf_build_besthit(ctx, geom, fit, bp, n_events, n_layers, layers, event_offsets, seed_state, seed_q, seed_hits,
+                     hit_idx_out, out_state=None, out_cov=None, out_chi2=None, out_ndof=None, out_status=None,
+                     stream=None):
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    f = fit if fit is not None else fit_params()
+    b = bp if bp is not None else build_params()
+    eo = (C.c_int32 * (n_events + 1))(*[int(v) for v in event_offsets])
+    s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    _check(ctx, load().kf_build_besthit(ctx, C.byref(g), C.byref(f), C.byref(b), int(n_events), int(n_layers),
+                                        layers, eo, C.byref(s), _ptr(seed_hits), _ptr(hit_idx_out), C.byref(o),
+                                        _stream(stream)))
+
+
+def kf_gather_hits(ctx, n_events, n_layers, layers, event_offsets, seed_hits, hit_idx, offsets_out, layer_out,
+                   x_out, y_out, z_out, stream=None):
+    eo = (C.c_int32 * (n_events + 1))(*[int(v) for v in event_offsets])
+    _check(ctx, load().kf_gather_hits(ctx, int(n_events), int(n_layers), layers, eo, _ptr(seed_hits),
+                                      _ptr(hit_idx), _ptr(offsets_out), _ptr(layer_out), _ptr(x_out), _ptr(y_out),
+                                      _ptr(z_out), _stream(stream)))

@@ -87,6 +87,7 @@ class _Tracks:
         self.x = torch.zeros(n, dtype=torch.float64, device=dev)
         self.y = torch.zeros_like(self.x)
         self.z = torch.zeros_like(self.x)
+        self.turn = torch.zeros_like(self.x)  # accumulated |c| s
 
     def curv(self, bz):
         return -self.q * KAPPA * bz / self.pt
@@ -162,7 +163,7 @@ def gen_tracks(geom: dict, n: int, seed: int, eta_max: float = 1.0, pt_min: floa
     recorded (smeared along the surface: r-phi by sig_rphi, z by sig_z on barrels, r by sig_r on
     disks) and then the direction is kicked by the Highland angle (theta += N(0, th0),
     phi += N(0, th0 / sin theta)); pT is held fixed.  Only outward crossings count and a track ends at
-    its apex (once it heads inwards).  Tracks with fewer than min_hits hits are dropped.  Returns numpy arrays: offsets (n+1), layer (uint8), x, y, z (float32) and, with
+    its apex (once it heads inwards, or after half a turn of transverse path).  Tracks with fewer than min_hits hits are dropped.  Returns numpy arrays: offsets (n+1), layer (uint8), x, y, z (float32) and, with
     keep_truth, truth (per hit: state (x, y, z, 1/pT, phi, theta) after the kick) and truth_q.
     """
     dev = torch.device(device)
@@ -236,8 +237,23 @@ def gen_tracks(geom: dict, n: int, seed: int, eta_max: float = 1.0, pt_min: floa
         if ih.numel() == 0:
             alive = alive_next
             break
-        _move(tr, ih, c[hit], s[hit])
-        sid = surf_id[hit]
+        # a track ends at its first apex: no crossing beyond half a turn of
+        # transverse path (loopers spiralling along z are not in these workloads)
+        turn = tr.turn[ih] + (c[hit] * s[hit]).abs()
+        past = turn > math.pi
+        if past.any():
+            alive_next[ih[past]] = False
+            keep = ~past
+            ih, s_h, c_h, sid_h = ih[keep], s[hit][keep], c[hit][keep], surf_id[hit][keep]
+            turn = turn[keep]
+        else:
+            s_h, c_h, sid_h = s[hit], c[hit], surf_id[hit]
+        if ih.numel() == 0:
+            alive = alive_next
+            continue
+        tr.turn[ih] = turn
+        _move(tr, ih, c_h, s_h)
+        sid = sid_h
         if not barrel_only:
             is_disk = torch.tensor([surfs[int(k)]["kind"] == 1 for k in range(len(surfs))],
                                    device=dev)[sid]
