@@ -1,0 +1,351 @@
+"""Benchmark of the batched Kalman-filter track fit on GB300.
+
+Workload (one step): seed estimate + KF fit of 1,000,000 synthetic tracks over
+17 barrel layers (R = 4..100 cm, Bz = 3.8 T, x/X0 = 0.02, seeds from three hits,
+seed covariance 1e4), mixed precision (FP32 + FP64 S solve and seed phase).
+Metric: track-layer updates per second (one update = propagation, transport,
+scattering noise and KF update of one track at one layer).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KF track-layer updates/sec, FP32 vs FP64 on one GB300 at stated err; p99 event ms"
+UNIT = "updates/s"
+N_TRACKS = 1_000_000
+WORKLOAD = ("KF fit of 1,000,000 tracks x 17 barrel layers (R 4-100 cm), Bz 3.8 T, x/X0 0.02, "
+            "pT log-uniform 0.5-10 GeV, |eta|<1, seeds from 3 hits, seed cov 1e4")
+
+# Algorithmic work per unit, counted from the formulas the fit kernel evaluates (the
+# derivation is written out in the design doc): FP64 FLOP of the seed phase (3 Joseph
+# updates + 2 covariance transports) per track and of the FP64 S solve per later
+# update; FP32 FLOP per later update.
+FP64_FLOP_SEED_PHASE = 2323.0
+FP64_FLOP_PER_FP32_UPDATE = 44.0
+FP32_FLOP_PER_FP32_UPDATE = 900.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tracks", type=int, default=N_TRACKS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the timed device-resident fit steps (the command the profiles capture)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        rows = [l.split(",") for l in open(self.path).read().splitlines() if l.strip()]
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    samples=len(rows), reasons=reasons)
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_baseline(geom, tk, n_sample, threads):
+    """FP64 oracle fit of the first n_sample tracks on `threads` host threads."""
+    import oracle
+    oracle.build_lib()
+    off = tk["offsets"]
+    sub = dict(offsets=off[:n_sample + 1], layer=tk["layer"], x=tk["x"], y=tk["y"], z=tk["z"])
+    t0 = time.perf_counter()
+    r = oracle.fit(geom, sub, t1=n_sample, threads=threads)
+    dt = time.perf_counter() - t0
+    upd = int(np.sum((r["ndof"][:n_sample] + 5) // 2))
+    return upd / dt, upd, dt
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 oracle, as it stands, on the host cores."""
+    from paper_1711_06571_gb300 import synth
+    if rank != 0:
+        return
+    geom = synth.geometry("barrel17")
+    threads = os.cpu_count() or 1
+    n_sample = 40_000
+    tk = synth.gen_tracks(geom, n_sample, synth.BASE_SEED + 2)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, upd, dt = oracle_baseline(geom, tk, n_sample, threads)
+        if i >= args.warmup:
+            vals.append((upd, dt))
+    tot_upd = sum(u for u, _ in vals)
+    tot_t = sum(d for _, d in vals)
+    value = tot_upd / tot_t
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=0, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * tot_t / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD + f" (per step a sample of {n_sample} tracks)", tracks=n_sample),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=threads, kind="oracle",
+                                  sample=f"{n_sample} tracks x up to 17 layers per step"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_1711_06571_gb300 import build as kbuild, kf, run, synth
+    kbuild.build()
+    torch.cuda.set_device(local)
+    ctx = run.context(local)
+    geom = synth.geometry("barrel17")
+    g = kf.make_geometry(geom)
+    n = args.tracks
+    # each rank fits its own tracks (independent units, no exchange step)
+    tk = synth.gen_tracks(geom, n, synth.BASE_SEED + 2 + 1000 * rank)
+    n = tk["n"]
+    dh = run.hits_to_device(tk)
+    seeds = run.make_seeds(ctx, g, dh)
+    out = run.alloc_fit_out(n)
+    stream = torch.cuda.current_stream()
+    params = kf.fit_params(precision=kf.KF_PREC_MIXED)
+
+    def step():
+        kf.kf_make_seeds(ctx, g, n, dh["offsets"], dh["x"], dh["y"], dh["z"], seeds[0], seeds[1])
+        kf.kf_fit(ctx, g, params, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                  out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    updates_per_step = int(((out["ndof"] + 5) // 2).clamp(min=0).sum().item())
+    # per-launch timing of the fit kernel (events on the launching stream)
+    fit_ms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0.record(stream)
+    for k in range(args.steps):
+        kf.kf_make_seeds(ctx, g, n, dh["offsets"], dh["x"], dh["y"], dh["z"], seeds[0], seeds[1])
+        ev[k][0].record(stream)
+        kf.kf_fit(ctx, g, params, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                  out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+        ev[k][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    fit_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = max_over_ranks(ms_local, world)
+    total_updates = sum_over_ranks(updates_per_step, world)
+    value = total_updates / (ms * 1e-3)
+
+    # roofline of the fit kernel: FP64 pipe (dominant), FP32 pipe, HBM
+    nh = len(tk["x"])
+    fp32_updates = updates_per_step - 3 * n
+    fp64_flop = FP64_FLOP_SEED_PHASE * n + FP64_FLOP_PER_FP32_UPDATE * fp32_updates
+    fp32_flop = FP32_FLOP_PER_FP32_UPDATE * fp32_updates
+    bytes_alg = 4 * (n + 1) + 13 * nh + 25 * n + (48 + 168 + 8 + 4 + 4) * n
+    fit_avg = float(np.mean(fit_ms))
+    peak64 = kf.kf_measure_peak(ctx, 0)
+    peak32 = kf.kf_measure_peak(ctx, 1)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ach64 = fp64_flop / (fit_avg * 1e-3) / 1e12
+    roofline = dict(bound="alu", pipe="fp64", achieved=ach64, peak=peak64 / 1e12, unit="TFLOP/s",
+                    frac=ach64 / (peak64 / 1e12), traffic=None,
+                    peak_source="kf_measure_peak FP64 FMA chains (measured in this run)",
+                    fp32=dict(achieved=fp32_flop / (fit_avg * 1e-3) / 1e12, peak=peak32 / 1e12, unit="TFLOP/s",
+                              frac=fp32_flop / (fit_avg * 1e-3) / peak32),
+                    hbm=dict(achieved=bytes_alg / (fit_avg * 1e-3) / 1e9, peak=hbm, unit="GB/s",
+                             frac=bytes_alg / (fit_avg * 1e-3) / 1e9 / hbm, peak_source="MEASURED_PEAKS.json"),
+                    fit_ms_per_launch=fit_avg, fp64_flop_per_launch=fp64_flop, fp32_flop_per_launch=fp32_flop,
+                    bytes_per_launch=bytes_alg)
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps(dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                                  warmup=args.warmup, ms_per_step=ms, fit_ms_per_launch=fit_avg,
+                                  higher_is_better=True, roofline=roofline, clocks=clk)), flush=True)
+        return
+
+    # all-FP64 GPU path on the same inputs, for comparison
+    p64 = kf.fit_params(precision=kf.KF_PREC_FP64)
+    out64 = run.alloc_fit_out(n)
+    for _ in range(2):
+        kf.kf_fit(ctx, g, p64, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                  out64["state"], out64["cov"], out64["chi2"], out64["ndof"], out64["status"])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    reps = max(3, args.steps // 4)
+    for _ in range(reps):
+        kf.kf_fit(ctx, g, p64, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                  out64["state"], out64["cov"], out64["chi2"], out64["ndof"], out64["status"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b) / reps
+
+    # end to end through the C ABI with host buffers (page-locked), copies inside
+    hh = dict(offsets=torch.from_numpy(tk["offsets"]).pin_memory(), layer=torch.from_numpy(tk["layer"]).pin_memory(),
+              x=torch.from_numpy(tk["x"]).pin_memory(), y=torch.from_numpy(tk["y"]).pin_memory(),
+              z=torch.from_numpy(tk["z"]).pin_memory())
+    ho = dict(state=torch.empty((6, n), dtype=torch.float64).pin_memory(),
+              cov=torch.empty((21, n), dtype=torch.float64).pin_memory(),
+              chi2=torch.empty(n, dtype=torch.float64).pin_memory(),
+              ndof=torch.empty(n, dtype=torch.int32).pin_memory(),
+              status=torch.empty(n, dtype=torch.int32).pin_memory())
+
+    def e2e_step():
+        kf.kf_fit_host(ctx, g, params, n, hh["offsets"], hh["layer"], hh["x"], hh["y"], hh["z"], ho["state"],
+                       ho["cov"], ho["chi2"], ho["ndof"], ho["status"])
+
+    for _ in range(max(2, args.warmup // 2)):
+        e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_reps = max(3, args.steps // 2)
+    for _ in range(e2e_reps):
+        e2e_step()
+    t_e2e = (time.perf_counter() - t0) / e2e_reps
+    t_e2e = max_over_ranks(t_e2e, world)
+    h2d = 4 * (n + 1) + 13 * nh
+    d2h = (48 + 168 + 8 + 4 + 4) * n
+    # the host results equal the device-resident run
+    same = np.array_equal(ho["chi2"].numpy(), out["chi2"].cpu().numpy())
+
+    # parity on a sample against the FP64 oracle
+    import oracle
+    parity = None
+    cpu_baseline = None
+    if rank == 0:
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        import parity as par
+        m = 2000
+        sub = dict(offsets=tk["offsets"][:m + 1], layer=tk["layer"], x=tk["x"], y=tk["y"], z=tk["z"], n=m)
+        orc = oracle.fit(geom, sub, t1=m, threads=os.cpu_count() or 1)
+        gsub = dict(state=out["state"][:, :m].t().cpu().numpy(), cov=run.unpack_cov(out["cov"][:, :m].cpu().numpy()),
+                    chi2=out["chi2"][:m].cpu().numpy(), q=seeds[1][:m].cpu().numpy())
+        orc = {k: (v[:m] if hasattr(v, "__len__") and len(v) >= m else v) for k, v in orc.items()}
+        ok = (orc["status"] & 7) == 0
+        res = par.compare_fits(gsub, orc, np.zeros(m, int), ok)
+        parity = dict(tracks=int(ok.sum()), max_param_over_sigma=float(res["max_pull"].max()),
+                      max_chi2_rel=float(res["chi2rel"].max()), max_cov_norm=float(res["dcov"].max()),
+                      tolerance=dict(param_over_sigma=1e-3, chi2_rel=1e-3))
+        if not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            n_sample = min(n, 150_000)
+            v, upd, dt = oracle_baseline(geom, tk, n_sample, threads)
+            cpu_baseline = dict(value=v, unit=UNIT, cores=threads, kind="oracle",
+                                sample=f"first {n_sample} tracks of the workload ({upd} updates, {dt:.1f} s)")
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
+                data="synthetic",
+                config=dict(workload=WORKLOAD, tracks_per_gpu=n, layers=17, updates_per_step=updates_per_step,
+                            precision="mixed: FP32 + FP64 S solve, FP64 seed phase",
+                            l2="inputs larger than L2 (hits 221 MB + outputs 232 MB per step)",
+                            parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+                roofline=roofline, cpu_baseline=cpu_baseline,
+                e2e=dict(value=total_updates / t_e2e, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                         ms_per_step=t_e2e * 1e3, api="kf_fit_host", host_matches_device=bool(same)),
+                fp64_path=dict(value=updates_per_step * world / (ms64 * 1e-3), unit=UNIT, fit_ms=ms64,
+                               speedup_of_mixed=ms64 / fit_avg),
+                gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,19 @@ int kf_make_seeds(kf_ctx *ctx, const kf_geometry *geom, int32_t n, const kf_trac
 int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n, const kf_seeds *seeds,
            const kf_track_hits *hits, const kf_tracks_out *out, void *stream);
 
+/* End-to-end fit from host memory: copies the hits to the device, estimates
+ * the seeds (kf_make_seeds), fits (kf_fit) and copies the results back.  The
+ * tracks are split into n_chunks ranges processed alternately on two internal
+ * streams, so the copies of one range overlap the kernels of the other (Sec.
+ * 4.3: copies overlapped with processing).  Blocks until the results are in
+ * host memory.  hits: host CSR as in kf_track_hits; out: host arrays with the
+ * layouts of kf_tracks_out (any may be NULL).  Page-locked host memory makes
+ * the copies asynchronous; pageable memory works but serialises them.
+ * n_chunks: 1..64, 0 = automatic.  Device buffers are owned by the context and
+ * kept for later calls of the same or smaller size. */
+int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
+                const kf_track_hits *hits, const kf_tracks_out *out, int32_t n_chunks);
+
 /* Choose block size, tracks per thread and work-queue chunk of the persistent
  * fit for this (n, hit count) by timing candidates on the given inputs (it
  * runs the fit several times and overwrites out).  The choice is cached in the
@@ -259,6 +272,15 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
 int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_binned_layer *layers,
                    const int32_t *event_offsets, const float *seed_hits, const int32_t *hit_idx, int32_t *offsets_out,
                    uint8_t *layer_out, float *x_out, float *y_out, float *z_out, void *stream);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Peak arithmetic rate of this GPU, measured (no counterpart in the paper; it
+ * gives the roofline denominators of the fit): a grid of several blocks per SM
+ * runs eight independent fused multiply-add chains per thread in FP64
+ * (which = 0) or FP32 (which = 1); *flops_per_s receives 2 * FMAs / elapsed.
+ * Synchronous; uses the context's device and a scratch buffer of the context. */
+int kf_measure_peak(kf_ctx *ctx, int which, double *flops_per_s);
 
 #ifdef __cplusplus
 }

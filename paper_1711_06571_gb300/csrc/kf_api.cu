@@ -46,6 +46,9 @@ struct kf_ctx {
     // one cached graph of the persistent fit
     GraphKey gkey;
     cudaGraphExec_t gexec = nullptr;
+    // end-to-end host path: device buffers and two streams
+    Buf host_ws;
+    cudaStream_t hs[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -237,6 +240,9 @@ void kf_ctx_destroy(kf_ctx *c)
     for (auto &kv : c->ws)
         if (kv.second.p) cudaFree(kv.second.p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->host_ws.p) cudaFree(c->host_ws.p);
+    for (int i = 0; i < 2; ++i)
+        if (c->hs[i]) cudaStreamDestroy(c->hs[i]);
     delete c;
 }
 
@@ -258,7 +264,7 @@ int kf_make_seeds(kf_ctx *ctx, const kf_geometry *geom, int32_t n, const kf_trac
     NEED_DEV(hits->z, "hits.z");
     NEED_DEV(state_out, "state_out");
     NEED_DEV(q_out, "q_out");
-    cudaError_t e = launch_seeds(G, n, hits->offsets, hits->x, hits->y, hits->z, state_out, q_out,
+    cudaError_t e = launch_seeds(G, n, n, 0, hits->offsets, hits->x, hits->y, hits->z, state_out, q_out,
                                  (cudaStream_t)stream);
     return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "seed kernel");
 }
@@ -292,7 +298,9 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     FitArgs a;
     memset(&a, 0, sizeof a);
     a.n = n;
-    a.n64 = P.precision == KF_PREC_FP64 ? P.n_fp64_updates : P.n_fp64_updates;
+    a.t_begin = 0;
+    a.count = n;
+    a.n64 = P.n_fp64_updates;
     a.seed_cov = P.seed_cov;
     a.ms_on = P.ms_on;
     a.seed_state = seeds->state;
@@ -381,6 +389,147 @@ int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, in
     return fit_impl(ctx, geom, params, n, seeds, hits, out, stream, nullptr);
 }
 
+static bool is_host_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;  // unknown to CUDA: pageable host memory
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
+                const kf_track_hits *hits, const kf_tracks_out *out, int32_t n_chunks)
+{
+    if (!ctx) return KF_EINVAL;
+    if (n < 0 || !hits || !out) return fail(ctx, KF_EINVAL, "n >= 0, hits and out are required");
+    kf_fit_params P;
+    int rc = check_fit_params(ctx, params, P);
+    if (rc) return rc;
+    Geom G;
+    if ((rc = to_geom(ctx, geom, G))) return rc;
+    if ((rc = set_dev(ctx))) return rc;
+    if (n == 0) return KF_OK;
+    if (!is_host_ptr(hits->offsets) || !is_host_ptr(hits->layer) || !is_host_ptr(hits->x) ||
+        !is_host_ptr(hits->y) || !is_host_ptr(hits->z))
+        return fail(ctx, KF_EINVAL, "kf_fit_host: hits must be host memory");
+    const void *outs[5] = {out->state, out->cov, out->chi2, out->ndof, out->status};
+    for (const void *o : outs)
+        if (o && !is_host_ptr(o)) return fail(ctx, KF_EINVAL, "kf_fit_host: outputs must be host memory");
+    if (n_chunks < 0 || n_chunks > 64) return fail(ctx, KF_EINVAL, "n_chunks must be 0..64");
+    if (hits->offsets[0] != 0) return fail(ctx, KF_EINVAL, "offsets[0] must be 0");
+    const int64_t nh = hits->offsets[n];
+    if (nh < 0) return fail(ctx, KF_EINVAL, "offsets[n] < 0");
+    int C = n_chunks ? n_chunks : (n >= 65536 ? 8 : 1);
+    if (C > n) C = n;
+    // device layout
+    const size_t nhist = order_scratch_ints();
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t o_off = 0, o_lay = o_off + al((size_t)(n + 1) * 4), o_x = o_lay + al((size_t)nh), o_y = o_x + al(nh * 4),
+           o_z = o_y + al(nh * 4), o_seed = o_z + al(nh * 4), o_q = o_seed + al((size_t)6 * n * 4),
+           o_st = o_q + al((size_t)n), o_cov = o_st + al((size_t)6 * n * 8), o_chi = o_cov + al((size_t)21 * n * 8),
+           o_nd = o_chi + al((size_t)n * 8), o_sts = o_nd + al((size_t)n * 4), o_ord = o_sts + al((size_t)n * 4),
+           total = o_ord + 2 * al((nhist + (size_t)n) * 4);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (int i = 0; i < 2; ++i)
+            if (!ctx->hs[i] && cudaStreamCreateWithFlags(&ctx->hs[i], cudaStreamNonBlocking) != cudaSuccess)
+                return cuda_fail(ctx, cudaGetLastError(), "stream create");
+        Buf &b = ctx->host_ws;
+        if (b.n < total) {
+            if (ctx->budget && ctx->used - b.n + total > ctx->budget)
+                return fail(ctx, KF_ENOMEM, "kf_fit_host buffers of %zu bytes exceed the budget", total);
+            if (b.p) {
+                cudaFree(b.p);
+                ctx->used -= b.n;
+                b = Buf{};
+            }
+            if (cudaMalloc(&b.p, total) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, KF_ENOMEM, "cudaMalloc(%zu) for kf_fit_host", total);
+            }
+            b.n = total;
+            ctx->used += total;
+        }
+    }
+    char *base = static_cast<char *>(ctx->host_ws.p);
+    int32_t *d_off = reinterpret_cast<int32_t *>(base + o_off);
+    uint8_t *d_lay = reinterpret_cast<uint8_t *>(base + o_lay);
+    float *d_x = reinterpret_cast<float *>(base + o_x);
+    float *d_y = reinterpret_cast<float *>(base + o_y);
+    float *d_z = reinterpret_cast<float *>(base + o_z);
+    float *d_seed = reinterpret_cast<float *>(base + o_seed);
+    int8_t *d_q = reinterpret_cast<int8_t *>(base + o_q);
+    double *d_st = reinterpret_cast<double *>(base + o_st);
+    double *d_cov = reinterpret_cast<double *>(base + o_cov);
+    double *d_chi = reinterpret_cast<double *>(base + o_chi);
+    int32_t *d_nd = reinterpret_cast<int32_t *>(base + o_nd);
+    uint32_t *d_sts = reinterpret_cast<uint32_t *>(base + o_sts);
+    const bool fp64 = P.precision == KF_PREC_FP64;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < C && e == cudaSuccess; ++c) {
+        const int t0 = (int)((int64_t)n * c / C), t1 = (int)((int64_t)n * (c + 1) / C);
+        const int cnt = t1 - t0;
+        if (cnt <= 0) continue;
+        cudaStream_t st = ctx->hs[c & 1];
+        int32_t *hist = reinterpret_cast<int32_t *>(base + o_ord + (c & 1) * al((nhist + (size_t)n) * 4));
+        int32_t *order = hist + nhist;
+        const int64_t h0 = hits->offsets[t0], h1 = hits->offsets[t1];
+        e = cudaMemcpyAsync(d_off + t0, hits->offsets + t0, (size_t)(cnt + 1) * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && h1 > h0) {
+            e = cudaMemcpyAsync(d_lay + h0, hits->layer + h0, (size_t)(h1 - h0), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_x + h0, hits->x + h0, (size_t)(h1 - h0) * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_y + h0, hits->y + h0, (size_t)(h1 - h0) * 4, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_z + h0, hits->z + h0, (size_t)(h1 - h0) * 4, cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess) e = launch_seeds(G, cnt, n, t0, d_off, d_x, d_y, d_z, d_seed, d_q, st);
+        if (e == cudaSuccess) e = launch_order(cnt, d_off + t0, d_seed + 3 * (size_t)n + t0, hist, order, st);
+        if (e == cudaSuccess) {
+            FitArgs a;
+            memset(&a, 0, sizeof a);
+            a.n = n;
+            a.t_begin = t0;
+            a.count = cnt;
+            a.n64 = P.n_fp64_updates;
+            a.seed_cov = P.seed_cov;
+            a.ms_on = P.ms_on;
+            a.seed_state = d_seed;
+            a.q = d_q;
+            a.off = d_off;
+            a.layer = d_lay;
+            a.hx = d_x;
+            a.hy = d_y;
+            a.hz = d_z;
+            a.o_state = d_st;
+            a.o_cov = out->cov ? d_cov : nullptr;
+            a.o_chi2 = d_chi;
+            a.o_ndof = d_nd;
+            a.o_status = d_sts;
+            a.order = order;
+            e = launch_fit(G, a, fp64, 128, st);
+        }
+        // results of this range back to the host
+        for (int i = 0; i < 6 && e == cudaSuccess && out->state; ++i)
+            e = cudaMemcpyAsync(out->state + (size_t)i * n + t0, d_st + (size_t)i * n + t0, (size_t)cnt * 8,
+                                cudaMemcpyDeviceToHost, st);
+        for (int i = 0; i < 21 && e == cudaSuccess && out->cov; ++i)
+            e = cudaMemcpyAsync(out->cov + (size_t)i * n + t0, d_cov + (size_t)i * n + t0, (size_t)cnt * 8,
+                                cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->chi2)
+            e = cudaMemcpyAsync(out->chi2 + t0, d_chi + t0, (size_t)cnt * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->ndof)
+            e = cudaMemcpyAsync(out->ndof + t0, d_nd + t0, (size_t)cnt * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->status)
+            e = cudaMemcpyAsync(out->status + t0, d_sts + t0, (size_t)cnt * 4, cudaMemcpyDeviceToHost, st);
+    }
+    cudaError_t e0 = cudaStreamSynchronize(ctx->hs[0]);
+    cudaError_t e1 = cudaStreamSynchronize(ctx->hs[1]);
+    if (e == cudaSuccess) e = e0 != cudaSuccess ? e0 : e1;
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "kf_fit_host");
+}
+
 int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
                     const kf_seeds *seeds, const kf_track_hits *hits, const kf_tracks_out *out, void *stream,
                     char *report, size_t report_len)
@@ -437,6 +586,18 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     if (report && report_len)
         snprintf(report, report_len, "%d,%d,%d,%d,%.4f", best.block, 1, best.chunk, best.grid, best.ms);
     return KF_OK;
+}
+
+int kf_measure_peak(kf_ctx *ctx, int which, double *flops_per_s)
+{
+    if (!ctx) return KF_EINVAL;
+    if ((which != 0 && which != 1) || !flops_per_s) return fail(ctx, KF_EINVAL, "which must be 0 or 1");
+    int rc = set_dev(ctx);
+    if (rc) return rc;
+    void *wsp = nullptr;
+    if ((rc = ws_get(ctx, nullptr, (size_t)ctx->sm_count * 8 * sizeof(double) + 256, &wsp))) return rc;
+    cudaError_t e = measure_peak(which, ctx->sm_count, wsp, flops_per_s);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "peak kernel");
 }
 
 int kf_bin_hits(kf_ctx *ctx, int32_t n_hits, const float *x, const float *y, const float *z, double half_len,

@@ -164,6 +164,34 @@ __device__ __forceinline__ void helix_factors(double h, double &sinc, double &ch
     }
 }
 
+// ------------------------------------------------------------ conversions on the integer pipe
+// On this GPU the FP64 pipe also executes F2F conversions and it is the fit's
+// bottleneck, so float <-> double goes through bit operations on the (idle)
+// integer pipe instead.  Float -> double is exact for normal numbers, zero,
+// infinity and NaN (subnormal floats flush to zero); double -> float rounds
+// the 29 dropped mantissa bits to nearest (ties away from zero) and flushes
+// results below the float normal range to zero.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    const unsigned ed = e == 0xffu ? 0x7ffu : (e == 0u ? 0u : e + 896u);
+    const unsigned mm = e == 0u ? 0u : m;
+    return __hiloint2double((int)(sign | (ed << 20) | (mm >> 3)), (int)(mm << 29));
+}
+
+__device__ __forceinline__ float d2f(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // float exponent field
+    unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    unsigned r = (sign | ((unsigned)e << 23)) + m + ((lo >> 28) & 1u);  // carry may bump the exponent
+    if (e <= 0) r = sign;                                              // below the normal range: signed zero
+    if (e >= 255) r = sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);  // overflow, inf, NaN
+    return __uint_as_float(r);
+}
+
 // ------------------------------------------------------------ FP64 3x3 solve
 // Reciprocal in FP64 for the positive pivots of S: the hardware approximation
 // rcp.approx.ftz.f64 (about 20 correct bits) refined by one Newton-Raphson step
@@ -209,10 +237,15 @@ __device__ __forceinline__ double ldl3_chi2(const Ldl3 &f, double r1, double r2,
 }
 
 // S^-1 = L^-T D^-1 L^-1 (symmetric, six entries), in type T
+__device__ __forceinline__ float to_t(double v, float) { return d2f(v); }
+__device__ __forceinline__ double to_t(double v, double) { return v; }
+
 template <class T>
 __device__ __forceinline__ void ldl3_inverse(const Ldl3 &f, T &a11, T &a21, T &a22, T &a31, T &a32, T &a33)
 {
-    T l21 = (T)f.l21, l31 = (T)f.l31, l32 = (T)f.l32, i1 = (T)f.i1, i2 = (T)f.i2, i3 = (T)f.i3;
+    const T z = T(0);
+    T l21 = to_t(f.l21, z), l31 = to_t(f.l31, z), l32 = to_t(f.l32, z), i1 = to_t(f.i1, z), i2 = to_t(f.i2, z),
+      i3 = to_t(f.i3, z);
     T m21 = -l21, m32 = -l32, m31 = l21 * l32 - l31;  // L^-1
     a33 = i3;
     a32 = m32 * i3;

@@ -49,13 +49,14 @@ __device__ __forceinline__ int seed_hit_last(const float *__restrict__ hx, const
     return (a < 0 || b < 0) ? 2 : b;
 }
 
-__global__ void __launch_bounds__(128) seed_kernel(int n, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(128) seed_kernel(int count, int n, int t_begin, const int32_t *__restrict__ off,
                                                    const float *__restrict__ hx, const float *__restrict__ hy,
                                                    const float *__restrict__ hz, float kb_abs,
                                                    float *__restrict__ state, int8_t *__restrict__ qo)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int t = t_begin + i;
     const int o = off[t], nh = off[t + 1] - o;
     if (nh < 3) {
 #pragma unroll
@@ -102,11 +103,11 @@ __global__ void __launch_bounds__(128) seed_kernel(int n, const int32_t *__restr
     qo[t] = k > 0.f ? (int8_t)-1 : (int8_t)1;
 }
 
-cudaError_t launch_seeds(const Geom &g, int n, const int32_t *off, const float *hx, const float *hy,
-                         const float *hz, float *state, int8_t *q, cudaStream_t st)
+cudaError_t launch_seeds(const Geom &g, int count, int stride, int t_begin, const int32_t *off, const float *hx,
+                         const float *hy, const float *hz, float *state, int8_t *q, cudaStream_t st)
 {
-    if (n <= 0) return cudaSuccess;
-    seed_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, off, hx, hy, hz, fabsf(g.kb), state, q);
+    if (count <= 0) return cudaSuccess;
+    seed_kernel<<<(count + 127) / 128, 128, 0, st>>>(count, stride, t_begin, off, hx, hy, hz, fabsf(g.kb), state, q);
     return cudaGetLastError();
 }
 
@@ -184,7 +185,7 @@ __device__ __forceinline__ bool fp64_step(Track<float, ff> &st, float pf[21], in
     sd.th = to_d(st.th);
     double pd[21];
 #pragma unroll
-    for (int i = 0; i < 21; ++i) pd[i] = pf[i];
+    for (int i = 0; i < 21; ++i) pd[i] = f2d(pf[i]);
     if (!fit_step<true, double>(sd, pd, k, alpha, mass2, ms_on, sf, hx, hy, hz, chi2, status)) return false;
     st.x = ff_from_d(sd.x);
     st.y = ff_from_d(sd.y);
@@ -193,7 +194,7 @@ __device__ __forceinline__ bool fp64_step(Track<float, ff> &st, float pf[21], in
     st.ip = (float)sd.ip;
     st.th = ff_from_d(sd.th);
 #pragma unroll
-    for (int i = 0; i < 21; ++i) pf[i] = (float)pd[i];
+    for (int i = 0; i < 21; ++i) pf[i] = d2f(pd[i]);
     return true;
 }
 
@@ -242,7 +243,21 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         n1 = max(n1, s2 + 1);
     }
     n1 = min(n1, nh);
-    for (; k < n1; ++k) {
+    if (n1 > 0) {
+        // the seed hit: no propagation, the structured first update
+        const Surf &sf = surf[a.layer[o0]];
+        T cphi, sphi;
+        sincos_pos(st.phi, sphi, cphi);
+        if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
+        if (kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)) {
+            ++used;
+            k = 1;
+        } else {
+            status |= KF_ST_CHOL_FAIL;
+            alive = false;
+        }
+    }
+    for (; alive && k < n1; ++k) {
         const int h = o0 + k;
         if (!fit_step<true, double>(st, pd, k, alpha, mass2, a.ms_on, surf[a.layer[h]], a.hx[h], a.hy[h], a.hz[h],
                                     chi2, status)) {
@@ -255,7 +270,7 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         // phase 2: the rest in T (FP32 on the mixed path), standard form
         T pf[21];
 #pragma unroll
-        for (int i = 0; i < 21; ++i) pf[i] = (T)pd[i];
+        for (int i = 0; i < 21; ++i) pf[i] = to_t(pd[i], T(0));
         for (; k < nh; ++k) {
             const int h = o0 + k;
             const Surf &sf = surf[a.layer[h]];
@@ -297,8 +312,8 @@ __global__ void __launch_bounds__(128) fit_kernel(const Geom g, const FitArgs a)
     __shared__ Surf s_surf[MAX_SURF];
     load_geom(g, s_surf);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const int t = a.order ? a.order[i] : i;
+    if (i >= a.count) return;
+    const int t = a.t_begin + (a.order ? a.order[i] : i);
     fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
 }
 
@@ -317,10 +332,10 @@ __global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const Geom g, con
         int base = 0;
         if (lane == 0) base = atomicAdd(a.queue, a.chunk);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= a.n) break;
-        const int end = min(base + a.chunk, a.n);
+        if (base >= a.count) break;
+        const int end = min(base + a.chunk, a.count);
         for (int i = base + lane; i < end; i += 32) {
-            const int t = a.order ? a.order[i] : i;
+            const int t = a.t_begin + (a.order ? a.order[i] : i);
             fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
         }
     }
@@ -328,10 +343,10 @@ __global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const Geom g, con
 
 cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cudaStream_t st)
 {
-    if (a.n <= 0) return cudaSuccess;
+    if (a.count <= 0) return cudaSuccess;
     (void)block;
     const int b = 128;
-    const int grid = (a.n + b - 1) / b;
+    const int grid = (a.count + b - 1) / b;
     if (fp64)
         fit_kernel<true><<<grid, b, 0, st>>>(g, a);
     else
@@ -353,7 +368,7 @@ static cudaError_t launch_pers(const Geom &g, const FitArgs &a, int block, int g
 
 cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, int block, int grid, cudaStream_t st)
 {
-    if (a.n <= 0) return cudaSuccess;
+    if (a.count <= 0) return cudaSuccess;
     return fp64 ? launch_pers<true>(g, a, block, grid, st) : launch_pers<false>(g, a, block, grid, st);
 }
 
@@ -396,12 +411,20 @@ __device__ __forceinline__ int order_key(const int32_t *__restrict__ off, const 
     const int b = min((int)(fabsf(ip[t]) * 32.f), 63);
     return (64 - nh) * 64 + b;
 }
-__global__ void order_hist_kernel(int n, const int32_t *__restrict__ off, const float *__restrict__ ip,
-                                  int32_t *hist)
+// Histogram and scatter count in shared memory per block and touch global
+// memory once per non-empty bucket and block: the keys of neighbouring tracks
+// repeat a lot, and per-track global atomics on them serialise.
+__global__ void __launch_bounds__(1024) order_hist_kernel(int n, const int32_t *__restrict__ off,
+                                                          const float *__restrict__ ip, int32_t *hist)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    atomicAdd(&hist[order_key(off, ip, t)], 1);
+    __shared__ int32_t cnt[ORDER_BUCKETS];
+    for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) atomicAdd(&cnt[order_key(off, ip, t)], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x)
+        if (cnt[b]) atomicAdd(&hist[b], cnt[b]);
 }
 __global__ void __launch_bounds__(1024) order_scan_kernel(int32_t *hist)
 {
@@ -443,13 +466,23 @@ __global__ void __launch_bounds__(1024) order_scan_kernel(int32_t *hist)
         acc += loc[j];
     }
 }
-__global__ void order_scatter_kernel(int n, const int32_t *__restrict__ off, const float *__restrict__ ip,
-                                     int32_t *hist, int32_t *order)
+__global__ void __launch_bounds__(1024) order_scatter_kernel(int n, const int32_t *__restrict__ off,
+                                                             const float *__restrict__ ip, int32_t *cursor,
+                                                             int32_t *order)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int pos = atomicAdd(&hist[order_key(off, ip, t)], 1);
-    order[pos] = t;
+    __shared__ int32_t cnt[ORDER_BUCKETS];
+    for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int key = t < n ? order_key(off, ip, t) : 0;
+    int local = 0;
+    if (t < n) local = atomicAdd(&cnt[key], 1);
+    __syncthreads();
+    // reserve this block's range in every bucket it uses
+    for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x)
+        if (cnt[b]) cnt[b] = atomicAdd(&cursor[b], cnt[b]);
+    __syncthreads();
+    if (t < n) order[cnt[key] + local] = t;
 }
 
 size_t order_scratch_ints() { return ORDER_BUCKETS; }
@@ -460,7 +493,7 @@ cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, int32_
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(hist, 0, ORDER_BUCKETS * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    const int b = 256, grid = (n + b - 1) / b;
+    const int b = 1024, grid = (n + b - 1) / b;
     order_hist_kernel<<<grid, b, 0, st>>>(n, off, seed_ip, hist);
     order_scan_kernel<<<1, 1024, 0, st>>>(hist);
     order_scatter_kernel<<<grid, b, 0, st>>>(n, off, seed_ip, hist, order);

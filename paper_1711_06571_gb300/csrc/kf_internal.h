@@ -9,7 +9,9 @@
 namespace kfd {
 
 struct FitArgs {
-    int n;
+    int n;            // plane stride of seeds and outputs ([k][n] arrays)
+    int t_begin;      // first track of this launch
+    int count;        // tracks in this launch (t_begin .. t_begin + count - 1)
     int n64;          // updates carried in FP64 (Joseph form) from the seed
     double seed_cov;
     int ms_on;
@@ -32,8 +34,8 @@ struct FitArgs {
 };
 
 // kf_fit.cu
-cudaError_t launch_seeds(const Geom &g, int n, const int32_t *off, const float *hx, const float *hy,
-                         const float *hz, float *state, int8_t *q, cudaStream_t st);
+cudaError_t launch_seeds(const Geom &g, int count, int stride, int t_begin, const int32_t *off, const float *hx,
+                         const float *hy, const float *hz, float *state, int8_t *q, cudaStream_t st);
 cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cudaStream_t st);
 cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, int block, int grid, cudaStream_t st);
 int persistent_blocks_per_sm(bool fp64, int block);
@@ -80,5 +82,8 @@ size_t gather_scratch_bytes(int n);
 cudaError_t launch_gather(int n, int n_events, int n_layers, const LayerDev *layers, const int32_t *event_off,
                           const float *seed_hits, const int32_t *hit_idx, int32_t *off_out, uint8_t *layer_out,
                           float *x_out, float *y_out, float *z_out, void *scratch, cudaStream_t st);
+
+// kf_peak.cu
+cudaError_t measure_peak(int which, int sm_count, void *scratch, double *flops_per_s);
 
 }  // namespace kfd

@@ -35,6 +35,9 @@ struct Jac {
     T cphi1, sphi1;  // cos, sin of the new phi
 };
 
+__device__ __forceinline__ double wide(float v) { return f2d(v); }
+__device__ __forceinline__ double wide(double v) { return v; }
+
 template <class T> __device__ __forceinline__ T tsqrt(T v);
 template <> __device__ __forceinline__ float tsqrt<float>(float v) { return sqrtf(v); }
 template <> __device__ __forceinline__ double tsqrt<double>(double v) { return sqrt(v); }
@@ -242,12 +245,13 @@ __device__ __forceinline__ void transport(T p[21], const Jac<T> &J)
 __device__ __forceinline__ Jac<double> widen(const Jac<float> &J)
 {
     Jac<double> D;
-    D.ax3 = J.ax3; D.ax4 = J.ax4; D.ay3 = J.ay3; D.ay4 = J.ay4; D.az5 = J.az5; D.ap3 = J.ap3;
-    D.u0 = J.u0; D.u1 = J.u1; D.u2 = J.u2; D.u4 = J.u4;
+    D.ax3 = f2d(J.ax3); D.ax4 = f2d(J.ax4); D.ay3 = f2d(J.ay3); D.ay4 = f2d(J.ay4); D.az5 = f2d(J.az5);
+    D.ap3 = f2d(J.ap3);
+    D.u0 = f2d(J.u0); D.u1 = f2d(J.u1); D.u2 = f2d(J.u2); D.u4 = f2d(J.u4);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) D.w[j] = J.w[j];
-    D.cphi1 = J.cphi1;
-    D.sphi1 = J.sphi1;
+    for (int j = 0; j < 6; ++j) D.w[j] = f2d(J.w[j]);
+    D.cphi1 = f2d(J.cphi1);
+    D.sphi1 = f2d(J.sphi1);
     return D;
 }
 __device__ __forceinline__ const Jac<double> &widen(const Jac<double> &J) { return J; }
@@ -350,8 +354,8 @@ __device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, f
     C s11 = p[pk(0, 0)] + rxx, s21 = p[pk(1, 0)] + rxy, s22 = p[pk(1, 1)] + ryy;
     C s31 = p[pk(2, 0)], s32 = p[pk(2, 1)], s33 = p[pk(2, 2)] + rzz;
     Ldl3 f;
-    if (!ldl3((double)s11, (double)s21, (double)s22, (double)s31, (double)s32, (double)s33, f)) return false;
-    chi2 += ldl3_chi2(f, (double)r0, (double)r1, (double)r2);
+    if (!ldl3(wide(s11), wide(s21), wide(s22), wide(s31), wide(s32), wide(s33), f)) return false;
+    chi2 += ldl3_chi2(f, wide(r0), wide(r1), wide(r2));
     C a11, a21, a22, a31, a32, a33;
     ldl3_inverse<C>(f, a11, a21, a22, a31, a32, a33);
     C G[6][3], K[6][3];
@@ -398,25 +402,28 @@ __device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, f
     return true;
 }
 
-// Update on the mixed path (FP32 covariance).  When the prior position variance
-// exceeds the smallest hit variance by more than 1e3 (after a run of layers
-// without an accepted hit, or a long extrapolation) the standard form cancels
-// more digits than FP32 holds, so that update runs in FP64, Joseph form.
-constexpr float UPDATE_FP64_RATIO = 1e3f;
+// Update on the mixed path (FP32 covariance).  The standard form loses about
+// log10(prior / hit variance) digits to cancellation; where the prior position
+// variance exceeds the hit variance along x, y or z by more than
+// UPDATE_FP64_RATIO (after layers without an accepted hit, a long extrapolation,
+// a seed phase) the update runs in FP64, Joseph form.
+constexpr float UPDATE_FP64_RATIO = 100.f;
 
 template <class Pp>
 __device__ __forceinline__ bool kf_update_mixed(Track<float, Pp> &st, float p[21], float hx, float hy, float hz,
                                                 const Surf &sf, double &chi2)
 {
-    const float pmax = fmaxf(p[pk(0, 0)], fmaxf(p[pk(1, 1)], p[pk(2, 2)]));
-    const float rmin = fminf(sf.var_rad, fminf(sf.var_rphi, sf.var_zz));
-    if (pmax > UPDATE_FP64_RATIO * rmin) {
+    float rxx, rxy, ryy, rzz;
+    meas_cov<float>(sf, hx, hy, rxx, rxy, ryy, rzz);
+    const bool informative = p[pk(0, 0)] > UPDATE_FP64_RATIO * rxx || p[pk(1, 1)] > UPDATE_FP64_RATIO * ryy ||
+                             p[pk(2, 2)] > UPDATE_FP64_RATIO * rzz;
+    if (informative) {
         double pd[21];
 #pragma unroll
-        for (int i = 0; i < 21; ++i) pd[i] = p[i];
+        for (int i = 0; i < 21; ++i) pd[i] = f2d(p[i]);
         const bool ok = kf_update<true>(st, pd, hx, hy, hz, sf, chi2);
 #pragma unroll
-        for (int i = 0; i < 21; ++i) p[i] = (float)pd[i];
+        for (int i = 0; i < 21; ++i) p[i] = d2f(pd[i]);
         return ok;
     }
     return kf_update<false>(st, p, hx, hy, hz, sf, chi2);
@@ -426,6 +433,49 @@ __device__ __forceinline__ bool kf_update_mixed(Track<double, Pp> &st, double p[
                                                 const Surf &sf, double &chi2)
 {
     return kf_update<false>(st, p, hx, hy, hz, sf, chi2);
+}
+
+// The first update, at the seed: the prior is seed_cov * I plus scattering
+// noise on phi and theta only, so the position block is seed_cov * I and the
+// position-angle blocks are zero.  The Joseph update then leaves the angle rows
+// untouched (K = 0 there) and acts on the 3x3 position block alone; this
+// evaluates exactly the nonzero part of kf_update<true>'s arithmetic.
+template <class T, class Pp>
+__device__ __forceinline__ bool kf_seed_update(Track<T, Pp> &st, double p[21], float hx, float hy, float hz,
+                                               const Surf &sf, double &chi2)
+{
+    const auto r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);
+    double rxx, rxy, ryy, rzz;
+    meas_cov<double>(sf, hx, hy, rxx, rxy, ryy, rzz);
+    const double c = p[pk(0, 0)];  // == p(1,1) == p(2,2); off-diagonal position and cross terms are 0
+    const double s11 = c + rxx, s21 = rxy, s22 = c + ryy, s33 = c + rzz;
+    Ldl3 f;
+    if (!ldl3(s11, s21, s22, 0.0, 0.0, s33, f)) return false;
+    chi2 += ldl3_chi2(f, wide(r0), wide(r1), wide(r2));
+    double a11, a21, a22, a31, a32, a33;
+    ldl3_inverse<double>(f, a11, a21, a22, a31, a32, a33);
+    // K = c S^-1 on the position rows
+    const double K[3][3] = {{c * a11, c * a21, c * a31}, {c * a21, c * a22, c * a32}, {c * a31, c * a32, c * a33}};
+    const double rr[3] = {wide(r0), wide(r1), wide(r2)};
+    double d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = K[i][0] * rr[0] + K[i][1] * rr[1] + K[i][2] * rr[2];
+    add_inc(st.x, d[0]);
+    add_inc(st.y, d[1]);
+    add_inc(st.z, d[2]);
+    // Joseph: P = P - K G^T + (K S - G) K^T with G = c I on the position block
+    const double S[3][3] = {{s11, s21, 0.0}, {s21, s22, 0.0}, {0.0, 0.0, s33}};
+    double W[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) W[i][j] = K[i][0] * S[0][j] + K[i][1] * S[1][j] + K[i][2] * S[2][j] - (i == j ? c : 0.0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j)
+            p[pk(i, j)] = p[pk(i, j)] - K[i][j] * c + (W[i][0] * K[j][0] + W[i][1] * K[j][1] + W[i][2] * K[j][2]);
+    return true;
 }
 
 }  // namespace kfd

@@ -99,6 +99,8 @@ _SIGS = {
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "kf_fit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
                          C.POINTER(kf_seeds), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out), C.c_void_p]),
+    "kf_fit_host": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
+                              C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out), C.c_int32]),
     "kf_autotune_fit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
                                   C.POINTER(kf_seeds), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out),
                                   C.c_void_p, C.c_char_p, C.c_size_t]),
@@ -108,6 +110,7 @@ _SIGS = {
                                    C.POINTER(kf_build_params), C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
                                    C.POINTER(C.c_int32), C.POINTER(kf_seeds), C.c_void_p, C.c_void_p,
                                    C.POINTER(kf_tracks_out), C.c_void_p]),
+    "kf_measure_peak": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "kf_gather_hits": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
                                  C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -220,6 +223,27 @@ def kf_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, ou
                               _stream(stream)))
 
 
+def _hptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if t.is_cuda:
+            raise ValueError("kf_fit_host takes host tensors")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(t.ctypes.data)  # numpy
+
+
+def kf_fit_host(ctx, geom, params, n, offsets, layer, x, y, z, out_state=None, out_cov=None, out_chi2=None,
+                out_ndof=None, out_status=None, n_chunks=0):
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    p = params if params is not None else fit_params()
+    h = kf_track_hits(_hptr(offsets), _hptr(layer), _hptr(x), _hptr(y), _hptr(z))
+    o = kf_tracks_out(_hptr(out_state), _hptr(out_cov), _hptr(out_chi2), _hptr(out_ndof), _hptr(out_status))
+    _check(ctx, load().kf_fit_host(ctx, C.byref(g), C.byref(p), int(n), C.byref(h), C.byref(o), int(n_chunks)))
+
+
 def kf_autotune_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, out_state=None,
                     out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None) -> str:
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
@@ -277,3 +301,10 @@ def kf_gather_hits(ctx, n_events, n_layers, layers, event_offsets, seed_hits, hi
     _check(ctx, load().kf_gather_hits(ctx, int(n_events), int(n_layers), layers, eo, _ptr(seed_hits),
                                       _ptr(hit_idx), _ptr(offsets_out), _ptr(layer_out), _ptr(x_out), _ptr(y_out),
                                       _ptr(z_out), _stream(stream)))
+
+
+def kf_measure_peak(ctx, which: int) -> float:
+    """Measured FMA throughput (FLOP/s): which = 0 FP64, 1 FP32."""
+    v = C.c_double(0.0)
+    _check(ctx, load().kf_measure_peak(ctx, int(which), C.byref(v)))
+    return v.value
