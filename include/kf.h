@@ -49,6 +49,7 @@ extern "C" {
 #define KF_ETIMEOUT (-4) /* a device-side wait ran out (reported, never trapped) */
 #define KF_EAGAIN (-5)   /* serving: result not ready yet */
 #define KF_EBUSY (-6)    /* serving: request exceeds the memory budget */
+#define KF_ESIZE (-7)    /* size beyond a fixed maximum (kf_bin_hits_static) */
 
 /* per-track status bits */
 #define KF_ST_NO_INTERSECT 1u /* helix never reaches the next surface; later hits unused */
@@ -216,6 +217,29 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
  * or NULL.  half_len > 0.  n_hits == 0 is allowed (offsets all zero). */
 int kf_bin_hits(kf_ctx *ctx, int32_t n_hits, const float *x, const float *y, const float *z, double half_len,
                 int32_t *perm_out, int32_t *offsets_out, float *packed_out, void *stream);
+
+/* Binning without any allocation.  The paper has no counterpart: this is the
+ * binning of kf_bin_hits for callers that cannot call cudaMalloc, such as a
+ * host framework that owns all device memory and hands it out itself, or a
+ * real-time (trigger) process whose memory footprint is fixed at start-up.
+ * It needs no context: its scratch is a fixed array in device memory,
+ * 4 * (2 * KF_STATIC_MAX_HITS + KF_NBINS) bytes (about 2.4 MB), which every
+ * GPU that loads the library holds until the process exits.
+ *   - Arguments, layouts and results are those of kf_bin_hits; n_hits may be
+ *     at most KF_STATIC_MAX_HITS, larger sizes return KF_ESIZE and do nothing.
+ *     Host pointers or a bad half_len return KF_EINVAL.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the array and it keeps the last call's
+ *     contents (nothing in it needs clearing: each call writes every scratch
+ *     word it reads).  Calls whose work overlaps on the GPU, from different
+ *     streams or threads, race on it; serialise them.
+ *   - It calls no allocation routine of any kind. */
+#define KF_STATIC_MAX_HITS 262144
+#define KF_MAX_DEVICES 64
+int kf_bin_hits_static(int32_t n_hits, const float *x, const float *y, const float *z, double half_len,
+                       int32_t *perm_out, int32_t *offsets_out, float *packed_out, void *stream);
 
 /* ---------------------------------------------------------------- building */
 

@@ -23,6 +23,8 @@ KF_ECUDA = -3
 KF_ETIMEOUT = -4
 KF_EAGAIN = -5
 KF_EBUSY = -6
+KF_ESIZE = -7
+KF_STATIC_MAX_HITS = 262144
 
 KF_ST_NO_INTERSECT = 1
 KF_ST_CHOL_FAIL = 2
@@ -110,6 +112,8 @@ _SIGS = {
                                    C.POINTER(kf_build_params), C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
                                    C.POINTER(C.c_int32), C.POINTER(kf_seeds), C.c_void_p, C.c_void_p,
                                    C.POINTER(kf_tracks_out), C.c_void_p]),
+    "kf_bin_hits_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "kf_measure_peak": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "kf_gather_hits": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
                                  C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -260,6 +264,12 @@ def kf_autotune_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x,
 def kf_bin_hits(ctx, n_hits, x, y, z, half_len, perm_out, offsets_out, packed_out=None, stream=None):
     _check(ctx, load().kf_bin_hits(ctx, int(n_hits), _ptr(x), _ptr(y), _ptr(z), float(half_len), _ptr(perm_out),
                                    _ptr(offsets_out), _ptr(packed_out), _stream(stream)))
+
+
+def kf_bin_hits_static(n_hits, x, y, z, half_len, perm_out, offsets_out, packed_out=None, stream=None) -> int:
+    """Allocation-free binning (no context); returns the library's status code."""
+    return load().kf_bin_hits_static(int(n_hits), _ptr(x), _ptr(y), _ptr(z), float(half_len), _ptr(perm_out),
+                                     _ptr(offsets_out), _ptr(packed_out), _stream(stream))
 
 
 def binned_layers(layer_dicts):
