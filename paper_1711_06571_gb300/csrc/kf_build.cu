@@ -32,7 +32,7 @@ __device__ __forceinline__ int find_event(const int32_t *__restrict__ eoff, int 
     return lo;
 }
 
-// Window of a predicted state on a barrel layer (SURVEY reading: +- nsigma in the
+// Window of a predicted state on a barrel layer (a reading: +- nsigma in the
 // azimuth of the predicted position, with its variance from P and the hit
 // resolution, and in z).
 struct Window {
