@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tracks", type=int, default=N_TRACKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
+    ap.add_argument("--serving-rates", default="auto",
+                    help="comma-separated arrival rates (events/s) of the serving sweep, or auto")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed device-resident fit steps (the command the profiles capture)")
     return ap.parse_args()
@@ -141,6 +144,77 @@ def oracle_baseline(geom, tk, n_sample, threads):
     dt = time.perf_counter() - t0
     upd = int(np.sum((r["ndof"][:n_sample] + 5) // 2))
     return upd / dt, upd, dt
+
+
+SERVING_WORKLOAD = ("serving loop: Poisson arrivals, event sizes log-uniform 500-50,000 tracks (16-event pool at the "
+                    "log-uniform quantiles), 17 barrel layers, 20% noise hits per layer, best-hit build + final "
+                    "fit per event, 40 GB device-memory budget")
+
+
+def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
+    """Events through kf_server: first as fast as they can be submitted (the
+    saturation throughput), then Poisson streams at fractions of it.  Latency is
+    the library's own submit -> results-in-caller-arrays time per event."""
+    from paper_1711_06571_gb300 import kf, synth
+    sizes = np.exp(np.linspace(np.log(500), np.log(50000), pool_size)).astype(np.int64)
+    pool = []
+    for i, sz in enumerate(sizes):
+        ev = synth.gen_event(geom, int(sz), synth.BASE_SEED + 500 + i)
+        L = len(ev["layers"])
+        lay = [ev["layers"][l] if l >= 3 else None for l in range(L)]
+        xs = [None if ly is None else np.ascontiguousarray(ly["x"], np.float32) for ly in lay]
+        ys = [None if ly is None else np.ascontiguousarray(ly["y"], np.float32) for ly in lay]
+        zs = [None if ly is None else np.ascontiguousarray(ly["z"], np.float32) for ly in lay]
+        surf = [int(ly["surf"]) for ly in ev["layers"]]
+        pool.append((ev["n"], surf, xs, ys, zs, np.ascontiguousarray(ev["seed_hits"], np.float32), L))
+    srv = kf.kf_server_create(ctx, geom, kf.server_params(mem_budget_bytes=40 << 30, max_batches=4,
+                                                          max_batch_events=16))
+
+    def stream(rate, n_ev, seed):
+        t_arr, _ = synth.serving_stream(seed, n_ev, rate if rate else 1.0)
+        pick = np.random.default_rng(seed + 1).integers(0, pool_size, n_ev)
+        kf.kf_server_stats_get(srv, reset=True)
+        tickets, tracks, lag = [], 0, 0.0
+        t0 = time.perf_counter()
+        for i in range(n_ev):
+            if rate:
+                dt = t0 + t_arr[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                else:
+                    lag = max(lag, -dt)
+            n, surf, xs, ys, zs, sh, L = pool[pick[i]]
+            res = dict(hit_idx=np.empty((L, n), np.int32), state=np.empty((6, n)), cov=np.empty((21, n)),
+                       chi2=np.empty(n), ndof=np.empty(n, np.int32), status=np.empty(n, np.uint32))
+            while True:
+                rc, t = kf.kf_server_submit(srv, n, surf, xs, ys, zs, sh, **res)
+                if rc != kf.KF_EAGAIN:
+                    break
+                time.sleep(2e-4)
+            if rc != kf.KF_OK:
+                raise RuntimeError(f"kf_server_submit: {rc}")
+            tickets.append(t)
+            tracks += n
+        bad = [t for t in tickets if kf.kf_server_wait(srv, t, 120000)[0] != kf.KF_OK]
+        wall = time.perf_counter() - t0
+        st = kf.kf_server_stats_get(srv, reset=True)
+        if bad or st["rc"] != kf.KF_OK:
+            raise RuntimeError(f"serving: {len(bad)} events failed")
+        return dict(rate_hz=rate if rate else "saturation", events=n_ev, tracks=int(tracks),
+                    p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], max_ms=st["max_ms"], events_per_s=n_ev / wall,
+                    tracks_per_s=tracks / wall, mean_batch_events=st["mean_batch_events"],
+                    peak_device_bytes=int(st["peak_bytes_in_use"]), max_submit_lag_ms=lag * 1e3)
+
+    try:
+        stream(None, 32, synth.BASE_SEED + 600)  # warm-up: pool, streams, pinned arena
+        sat = stream(None, 400, synth.BASE_SEED + 601)
+        if rates is None:
+            rates = [f * sat["events_per_s"] for f in (0.25, 0.5, 0.8)]
+        runs = [stream(r, int(min(600, max(60, r * seconds_per_rate))), synth.BASE_SEED + 610 + k)
+                for k, r in enumerate(rates)]
+    finally:
+        kf.kf_server_destroy(srv)
+    return dict(workload=SERVING_WORKLOAD, saturation=sat, rates=runs)
 
 
 def run_reference(args, world, rank):
@@ -303,6 +377,12 @@ def main():
     # the host results equal the device-resident run
     same = np.array_equal(ho["chi2"].numpy(), out["chi2"].cpu().numpy())
 
+    # serving loop: events of mixed sizes through kf_server (one rank's GPU each)
+    serving = None
+    if not args.no_serving:
+        rates = None if args.serving_rates == "auto" else [float(v) for v in args.serving_rates.split(",")]
+        serving = serving_sweep(ctx, geom, rates)
+
     # parity on a sample against the FP64 oracle
     import oracle
     parity = None
@@ -322,8 +402,10 @@ def main():
                       max_chi2_rel=float(res["chi2rel"].max()), max_cov_norm=float(res["dcov"].max()),
                       tolerance=dict(param_over_sigma=1e-3, chi2_rel=1e-3))
         if not args.no_cpu_baseline:
+            # about 15 s of oracle work on all host cores: size the sample from a short probe
             threads = os.cpu_count() or 1
-            n_sample = min(n, 150_000)
+            _, _, dt0 = oracle_baseline(geom, tk, min(n, 20_000), threads)
+            n_sample = int(min(n, max(20_000, 20_000 * 15.0 / max(dt0, 1e-3))))
             v, upd, dt = oracle_baseline(geom, tk, n_sample, threads)
             cpu_baseline = dict(value=v, unit=UNIT, cores=threads, kind="oracle",
                                 sample=f"first {n_sample} tracks of the workload ({upd} updates, {dt:.1f} s)")
@@ -340,7 +422,7 @@ def main():
                          ms_per_step=t_e2e * 1e3, api="kf_fit_host", host_matches_device=bool(same)),
                 fp64_path=dict(value=updates_per_step * world / (ms64 * 1e-3), unit=UNIT, fit_ms=ms64,
                                speedup_of_mixed=ms64 / fit_avg),
-                gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity)
+                gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity, serving=serving)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -75,7 +75,7 @@ extern "C" {
 
 typedef struct kf_ctx kf_ctx;
 
-/* One detector surface (Sec. 3 ideal barrel; Sec. 4.1 "cylinder with lids").
+/* One detector surface (Sec. 3: ideal barrel layers; Sec. 4.1: barrel closed by end-cap disks).
  * kind 0: barrel cylinder r = pos, |z| <= half_or_rin.
  * kind 1: disk z = pos, half_or_rin <= r <= r_out.
  * x_x0: thickness in radiation lengths at normal incidence.
@@ -153,8 +153,8 @@ const char *kf_version(void);
 
 /* ---------------------------------------------------------------- seeding */
 
-/* Seed estimate (Sec. 2: "initial estimate of the track parameters based on a
- * few hits in the innermost regions"; the estimate itself is a reading): for
+/* Seed estimate (Sec. 2: seeding gives first track parameters from a handful
+ * of hits on the innermost layers; the estimate itself is a reading): for
  * each track, hit 0 and the next two hits at least 2 cm apart in x-y (hits
  * 0, 1, 2 on a barrel); signed curvature of the circle through them, 1/pT =
  * |k| / (kappa |Bz|), q = -sign(k), phi = tangent at hit 0, theta from the
@@ -265,7 +265,7 @@ typedef struct {
 /* Best-hit track building (Sec. 2: project the candidate outwards, use the KF
  * to pick the most likely continuation on each layer; here one candidate per
  * seed keeps the minimum-chi2 hit).  Tracks of several events run in one
- * launch (Sec. 4.2 "multiple events at a time").  Per track: KF fit over its
+ * launch (Sec. 4.2: several events processed together).  Per track: KF fit over its
  * three seed hits (layers 0..2 of the event), then for every later layer:
  * propagate, add scattering noise, open a window of +- nsigma in phi
  * (position and hit resolution) and z, enumerate the window's bins (z
@@ -296,6 +296,112 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
 int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_binned_layer *layers,
                    const int32_t *event_offsets, const float *seed_hits, const int32_t *hit_idx, int32_t *offsets_out,
                    uint8_t *layer_out, float *x_out, float *y_out, float *z_out, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A serving loop over whole events (Sec. 4.2: several events in flight at a
+ * time; Sec. 4.3: copies overlapped with processing).  Callers submit events
+ * from host memory as they arrive; a dispatcher thread inside the library
+ * admits queued events while the device memory of the batches in flight stays
+ * under a budget, merges the admitted events (up to max_batch_events, arrival
+ * order) into one batch and runs each batch on its own stream: copy in, bin
+ * every build layer of every event in one segmented pass, seed, best-hit
+ * build, gather, final fit, copy out.  Batches overlap one another on the
+ * device.  Every track's arithmetic is that of kf_make_seeds, kf_bin_hits,
+ * kf_build_besthit, kf_gather_hits and kf_fit (grid schedule), so an event's
+ * results are bit-identical whatever it was batched with.
+ * The server owns its threads, streams, a device memory pool and a
+ * page-locked host staging arena; the context must outlive it. */
+typedef struct kf_server kf_server;
+
+typedef struct {
+    size_t mem_budget_bytes;   /* device bytes the batches in flight may hold; 0 = 40 GiB */
+    size_t host_staging_bytes; /* page-locked staging arena; 0 = 1 GiB */
+    int32_t max_batches;       /* batches in flight (one stream each), 1..16; 0 = 4 */
+    int32_t max_batch_events;  /* events merged into one batch, 1..64; 0 = 16 */
+    kf_fit_params fit;         /* seed_cov == 0 selects the kf_fit defaults; schedule is ignored */
+    kf_build_params build;     /* nsigma == 0 selects the kf_build_besthit defaults */
+    double batch_window_ms;    /* a free stream waits until the oldest queued event is this
+                                  old (or max_batch_events are queued) before it starts a
+                                  batch: larger batches for some latency; 0 = start at once */
+} kf_server_params;
+
+/* One event, all host memory, read during kf_server_submit only (it is
+ * copied into the staging arena before the call returns).
+ *   n_tracks > 0 seeds; n_layers 4..KF_MAX_SURFACES, all barrels; the first
+ *   three layers are the seed layers.
+ *   surface [n_layers]: geometry index of each layer.
+ *   n_hits [n_layers]: hits of each layer (layers 0..2 are not read).
+ *   x, y, z [n_layers]: per layer, a host array of n_hits[l] FP32 coordinates
+ *     (layers 0..2 are not read and may be NULL).
+ *   seed_hits [n_tracks][3][3]: hit k of track t, (x, y, z) at 9t + 3k. */
+typedef struct {
+    int32_t n_tracks;
+    int32_t n_layers;
+    const int32_t *surface;
+    const int32_t *n_hits;
+    const float *const *x;
+    const float *const *y;
+    const float *const *z;
+    const float *seed_hits;
+} kf_event;
+
+/* Where an event's results go: host arrays the caller keeps alive until the
+ * ticket has completed (the dispatcher thread writes them).  Any may be NULL.
+ *   hit_idx [n_layers][n_tracks]: as kf_build_besthit's hit_idx_out.
+ *   state [6][n_tracks], cov [21][n_tracks], chi2, ndof: final fit over the
+ *     seed hits and the chosen hits, as kf_fit.
+ *   status [n_tracks]: build status | final-fit status (KF_ST_* bits). */
+typedef struct {
+    int32_t *hit_idx;
+    double *state;
+    double *cov;
+    double *chi2;
+    int32_t *ndof;
+    uint32_t *status;
+} kf_event_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches;
+    int32_t queued;             /* events waiting for admission */
+    int32_t in_flight_events;
+    int32_t in_flight_batches;
+    int32_t pad_;
+    size_t bytes_in_use;        /* device bytes reserved by the batches in flight */
+    size_t peak_bytes_in_use;   /* maximum of bytes_in_use (never above the budget) */
+    double mean_batch_events;
+    double p50_ms, p99_ms, max_ms, mean_ms; /* submit -> results in the caller's arrays */
+    double events_per_s, tracks_per_s;      /* completed since the last reset */
+} kf_server_stats;
+
+/* Start a server on the context's device.  params: host, NULL = defaults.
+ * Returns KF_EINVAL (bad geometry or parameters), KF_ENOMEM (pool or staging
+ * arena), KF_ECUDA. */
+int kf_server_create(kf_ctx *ctx, const kf_geometry *geom, const kf_server_params *params, kf_server **out);
+
+/* Queue one event; *ticket receives its id.  Thread-safe.  Returns KF_EBUSY
+ * (and counts a rejection) when the event alone needs more device memory than
+ * the budget or more staging than the whole arena, KF_EAGAIN when the staging
+ * arena is full for now (retry after earlier events complete), KF_EINVAL for
+ * a malformed event. */
+int kf_server_submit(kf_server *s, const kf_event *ev, const kf_event_result *res, uint64_t *ticket);
+
+/* KF_EAGAIN while the ticket is queued or in flight; then, once, its result
+ * code (KF_OK, or KF_ENOMEM / KF_ECUDA if it could not run) with the latency in
+ * *latency_ms (may be NULL); KF_EINVAL for an unknown or already reported ticket. */
+int kf_server_poll(kf_server *s, uint64_t ticket, double *latency_ms);
+
+/* kf_server_poll that blocks up to timeout_ms; KF_ETIMEOUT when it runs out. */
+int kf_server_wait(kf_server *s, uint64_t ticket, double timeout_ms, double *latency_ms);
+
+/* Counters and latency percentiles of the events completed since the last
+ * reset; reset != 0 starts a new window.  Returns KF_ECUDA if a CUDA error
+ * has been seen (the counters are still filled). */
+int kf_server_stats_get(kf_server *s, kf_server_stats *out, int reset);
+
+/* Finish the batches in flight, drop queued events, free everything.  NULL is
+ * accepted. */
+void kf_server_destroy(kf_server *s);
 
 /* ---------------------------------------------------------------- measurement */
 

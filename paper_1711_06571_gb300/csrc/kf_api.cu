@@ -800,3 +800,11 @@ int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_bin
 }
 
 }  // extern "C"
+
+// Context services for the serving runtime (kf_server.cu).
+namespace kfd {
+int ctx_geom(kf_ctx *ctx, const kf_geometry *g, Geom &G) { return to_geom(ctx, g, G); }
+int ctx_fit_params(kf_ctx *ctx, const kf_fit_params *p, kf_fit_params &q) { return check_fit_params(ctx, p, q); }
+int ctx_device(const kf_ctx *ctx) { return ctx->device; }
+int ctx_fail(kf_ctx *ctx, int code, const char *msg) { return fail(ctx, code, "%s", msg); }
+}  // namespace kfd

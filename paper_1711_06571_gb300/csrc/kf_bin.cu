@@ -1,6 +1,7 @@
 // kf_bin.cu -- per-layer hit binning into the (phi, z) grid used to select hit
-// candidates during building (Sec. 3.1: "data structures for selecting hit
-// candidates"), as a stable counting sort on the GPU.
+// candidates during building (Sec. 3.1: the hit structures that candidate
+// selection searches), as a stable counting sort on the GPU.  Segmented
+// versions bin many (event, layer) pairs of one batch in a single pass.
 //
 //   1. key of every hit, in FP64 with explicit rounding (no contraction), and a
 //      histogram of keys (atomics into offsets[1..]);
@@ -135,6 +136,144 @@ cudaError_t launch_bin(int n, const float *x, const float *y, const float *z, do
     scatter_hits_kernel<<<grid, b, 0, st>>>(n, key, cursor, tmp);
     rank_kernel<<<grid, b, 0, st>>>(n, key, offsets, tmp, perm);
     if (packed) pack_kernel<<<grid, b, 0, st>>>(n, perm, x, y, z, reinterpret_cast<float4 *>(packed));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ many layers at once
+// Segmented form for the serving loop: nseg layers (of several events) with
+// their hits concatenated, seg_off[s] .. seg_off[s+1]-1 the hits of layer s;
+// one launch per pass for all of them.  Per layer the result equals launch_bin's
+// (perm holds indices local to the layer).  Scratch: key[H], cursor[nseg][NBINS],
+// tmp[H] int32.
+
+__device__ __forceinline__ int seg_of(const int32_t *__restrict__ seg_off, int nseg, int i)
+{
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void seg_key_kernel(int H, int nseg, const int32_t *__restrict__ seg_off, const double *__restrict__ half,
+                               const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
+                               int32_t *__restrict__ key, int32_t *__restrict__ offsets)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= H) return;
+    const int s = seg_of(seg_off, nseg, i);
+    const int32_t k = bin_key(x[i], y[i], z[i], half[s]);
+    key[i] = k;
+    atomicAdd(&offsets[(size_t)s * (KF_NBINS + 1) + k + 1], 1);
+}
+
+__global__ void __launch_bounds__(1024) seg_scan_kernel(int32_t *__restrict__ offsets, int32_t *__restrict__ cursor)
+{
+    // one block per segment: the body of scan_kernel on that segment's counts
+    int32_t *counts = offsets + (size_t)blockIdx.x * (KF_NBINS + 1) + 1;
+    int32_t *cur = cursor + (size_t)blockIdx.x * KF_NBINS;
+    __shared__ int32_t warp_tot[32];
+    const int tid = threadIdx.x;
+    constexpr int PER = KF_NBINS / 1024;
+    int32_t loc[PER];
+    int32_t s = 0;
+    const int base = tid * PER;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        s += counts[base + j];
+        loc[j] = s;
+    }
+    int32_t v = s;
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = warp_tot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int32_t o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    const int32_t excl = v - s + (wid > 0 ? warp_tot[wid - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        int32_t incl = excl + loc[j];
+        int32_t cnt = j == 0 ? loc[0] : loc[j] - loc[j - 1];
+        counts[base + j] = incl;
+        cur[base + j] = incl - cnt;
+    }
+}
+
+__global__ void seg_scatter_kernel(int H, int nseg, const int32_t *__restrict__ seg_off,
+                                   const int32_t *__restrict__ key, int32_t *__restrict__ cursor,
+                                   int32_t *__restrict__ tmp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= H) return;
+    const int s = seg_of(seg_off, nseg, i);
+    const int pos = atomicAdd(&cursor[(size_t)s * KF_NBINS + key[i]], 1);
+    tmp[seg_off[s] + pos] = i - seg_off[s];
+}
+
+__global__ void seg_rank_kernel(int H, int nseg, const int32_t *__restrict__ seg_off, const int32_t *__restrict__ key,
+                                const int32_t *__restrict__ offsets, const int32_t *__restrict__ tmp,
+                                int32_t *__restrict__ perm)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H) return;
+    const int s = seg_of(seg_off, nseg, p);
+    const int base = seg_off[s];
+    const int32_t i = tmp[p];  // local index
+    const int32_t k = key[base + i];
+    const int32_t *off = offsets + (size_t)s * (KF_NBINS + 1);
+    const int32_t b0 = off[k], b1 = off[k + 1];
+    int r = 0;
+    for (int j = b0; j < b1; ++j) r += tmp[base + j] < i;
+    perm[base + b0 + r] = i;
+}
+
+__global__ void seg_pack_kernel(int H, int nseg, const int32_t *__restrict__ seg_off, const int32_t *__restrict__ perm,
+                                const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
+                                float4 *__restrict__ packed)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= H) return;
+    const int s = seg_of(seg_off, nseg, p);
+    const int base = seg_off[s];
+    const int i = perm[p];
+    packed[p] = make_float4(x[base + i], y[base + i], z[base + i], __int_as_float(i));
+}
+
+size_t bin_segments_scratch_bytes(int H, int nseg)
+{
+    return ((size_t)2 * (H > 0 ? H : 1) + (size_t)nseg * KF_NBINS) * sizeof(int32_t) + 256;
+}
+
+cudaError_t launch_bin_segments(int nseg, int H, const int32_t *seg_off, const double *half, const float *x,
+                                const float *y, const float *z, int32_t *perm, int32_t *offsets, float *packed,
+                                void *scratch, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(offsets, 0, (size_t)nseg * (KF_NBINS + 1) * sizeof(int32_t), st);
+    if (e != cudaSuccess || H <= 0 || nseg <= 0) return e;
+    int32_t *key = reinterpret_cast<int32_t *>(scratch);
+    int32_t *cursor = key + H;
+    int32_t *tmp = cursor + (size_t)nseg * KF_NBINS;
+    const int b = 256, grid = (H + b - 1) / b;
+    seg_key_kernel<<<grid, b, 0, st>>>(H, nseg, seg_off, half, x, y, z, key, offsets);
+    seg_scan_kernel<<<nseg, 1024, 0, st>>>(offsets, cursor);
+    seg_scatter_kernel<<<grid, b, 0, st>>>(H, nseg, seg_off, key, cursor, tmp);
+    seg_rank_kernel<<<grid, b, 0, st>>>(H, nseg, seg_off, key, offsets, tmp, perm);
+    if (packed) seg_pack_kernel<<<grid, b, 0, st>>>(H, nseg, seg_off, perm, x, y, z, reinterpret_cast<float4 *>(packed));
     return cudaGetLastError();
 }
 

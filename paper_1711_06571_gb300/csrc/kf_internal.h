@@ -48,6 +48,11 @@ size_t bin_scratch_bytes(int n_hits);
 cudaError_t launch_bin(int n_hits, const float *x, const float *y, const float *z, double half_len, int32_t *perm,
                        int32_t *offsets, float *packed, void *scratch, cudaStream_t st);
 
+size_t bin_segments_scratch_bytes(int H, int nseg);
+cudaError_t launch_bin_segments(int nseg, int H, const int32_t *seg_off, const double *half, const float *x,
+                                const float *y, const float *z, int32_t *perm, int32_t *offsets, float *packed,
+                                void *scratch, cudaStream_t st);
+
 // kf_build.cu
 struct LayerDev {
     const float4 *packed;
@@ -85,5 +90,11 @@ cudaError_t launch_gather(int n, int n_events, int n_layers, const LayerDev *lay
 
 // kf_peak.cu
 cudaError_t measure_peak(int which, int sm_count, void *scratch, double *flops_per_s);
+
+// kf_api.cu: context services used by the serving runtime
+int ctx_geom(kf_ctx *ctx, const kf_geometry *g, Geom &G);
+int ctx_fit_params(kf_ctx *ctx, const kf_fit_params *p, kf_fit_params &q);
+int ctx_device(const kf_ctx *ctx);
+int ctx_fail(kf_ctx *ctx, int code, const char *msg);
 
 }  // namespace kfd

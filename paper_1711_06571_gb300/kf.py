@@ -88,6 +88,32 @@ class kf_build_params(C.Structure):
                 ("warp_coop", C.c_int32)]
 
 
+class kf_server_params(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_size_t), ("host_staging_bytes", C.c_size_t), ("max_batches", C.c_int32),
+                ("max_batch_events", C.c_int32), ("fit", kf_fit_params), ("build", kf_build_params),
+                ("batch_window_ms", C.c_double)]
+
+
+class kf_event(C.Structure):
+    _fields_ = [("n_tracks", C.c_int32), ("n_layers", C.c_int32), ("surface", C.POINTER(C.c_int32)),
+                ("n_hits", C.POINTER(C.c_int32)), ("x", C.POINTER(C.c_void_p)), ("y", C.POINTER(C.c_void_p)),
+                ("z", C.POINTER(C.c_void_p)), ("seed_hits", C.c_void_p)]
+
+
+class kf_event_result(C.Structure):
+    _fields_ = [("hit_idx", C.c_void_p), ("state", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p),
+                ("ndof", C.c_void_p), ("status", C.c_void_p)]
+
+
+class kf_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("batches", C.c_uint64), ("queued", C.c_int32), ("in_flight_events", C.c_int32),
+                ("in_flight_batches", C.c_int32), ("pad_", C.c_int32), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes_in_use", C.c_size_t), ("mean_batch_events", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("max_ms", C.c_double), ("mean_ms", C.c_double),
+                ("events_per_s", C.c_double), ("tracks_per_s", C.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -118,6 +144,14 @@ _SIGS = {
     "kf_gather_hits": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
                                  C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p]),
+    "kf_server_create": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_server_params),
+                                   C.POINTER(C.c_void_p)]),
+    "kf_server_submit": (C.c_int, [C.c_void_p, C.POINTER(kf_event), C.POINTER(kf_event_result),
+                                   C.POINTER(C.c_uint64)]),
+    "kf_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double)]),
+    "kf_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(C.c_double)]),
+    "kf_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(kf_server_stats), C.c_int]),
+    "kf_server_destroy": (None, [C.c_void_p]),
 }
 
 
@@ -318,3 +352,103 @@ def kf_measure_peak(ctx, which: int) -> float:
     v = C.c_double(0.0)
     _check(ctx, load().kf_measure_peak(ctx, int(which), C.byref(v)))
     return v.value
+
+
+# ---------------------------------------------------------------- serving
+
+class Server:
+    """Handle of a kf_server: the raw pointer plus the result arrays of the
+    tickets not yet reported (the dispatcher thread writes into them)."""
+
+    def __init__(self, ptr, ctx):
+        self.ptr = ptr
+        self.ctx = ctx
+        self.results = {}
+
+
+def server_params(mem_budget_bytes=0, host_staging_bytes=0, max_batches=0, max_batch_events=0, fit=None,
+                  build=None, batch_window_ms=0.0):
+    p = kf_server_params(mem_budget_bytes=int(mem_budget_bytes), host_staging_bytes=int(host_staging_bytes),
+                         max_batches=int(max_batches), max_batch_events=int(max_batch_events),
+                         batch_window_ms=float(batch_window_ms))
+    if fit is not None:
+        p.fit = fit
+    if build is not None:
+        p.build = build
+    return p
+
+
+def kf_server_create(ctx, geom, params=None) -> Server:
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    p = params if params is not None else server_params()
+    out = C.c_void_p()
+    _check(ctx, load().kf_server_create(ctx, C.byref(g), C.byref(p), C.byref(out)))
+    return Server(out, ctx)
+
+
+def _np_ptr(a, dtype):
+    import numpy as np
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
+        raise ValueError(f"expected a C-contiguous numpy array of {dtype}")
+    return C.c_void_p(a.ctypes.data)
+
+
+def kf_server_submit(srv: Server, n_tracks, surfaces, x, y, z, seed_hits, hit_idx=None, state=None, cov=None,
+                     chi2=None, ndof=None, status=None):
+    """Queue one event.  surfaces: list of geometry indices (first three = seed
+    layers); x, y, z: per layer numpy float32 arrays (layers 0..2 may be None);
+    seed_hits: float32 [n_tracks, 3, 3]; result arrays: numpy, shapes as in the
+    C header.  Returns (code, ticket): code KF_OK, KF_EBUSY or KF_EAGAIN."""
+    import numpy as np
+    L = len(surfaces)
+    sf = (C.c_int32 * L)(*[int(v) for v in surfaces])
+    nh = (C.c_int32 * L)(*[0 if x[l] is None else int(len(x[l])) for l in range(L)])
+    xs = (C.c_void_p * L)(*[None if x[l] is None else _np_ptr(x[l], np.float32).value for l in range(L)])
+    ys = (C.c_void_p * L)(*[None if y[l] is None else _np_ptr(y[l], np.float32).value for l in range(L)])
+    zs = (C.c_void_p * L)(*[None if z[l] is None else _np_ptr(z[l], np.float32).value for l in range(L)])
+    ev = kf_event(n_tracks=int(n_tracks), n_layers=L, surface=sf, n_hits=nh,
+                  x=C.cast(xs, C.POINTER(C.c_void_p)), y=C.cast(ys, C.POINTER(C.c_void_p)),
+                  z=C.cast(zs, C.POINTER(C.c_void_p)), seed_hits=_np_ptr(seed_hits, np.float32))
+    res = kf_event_result(_np_ptr(hit_idx, np.int32), _np_ptr(state, np.float64), _np_ptr(cov, np.float64),
+                          _np_ptr(chi2, np.float64), _np_ptr(ndof, np.int32), _np_ptr(status, np.uint32))
+    t = C.c_uint64(0)
+    rc = load().kf_server_submit(srv.ptr, C.byref(ev), C.byref(res), C.byref(t))
+    if rc == KF_OK:
+        srv.results[t.value] = (hit_idx, state, cov, chi2, ndof, status)
+    elif rc == KF_EINVAL:
+        raise KfError(rc, "kf_server_submit: malformed event")
+    return rc, t.value
+
+
+def kf_server_poll(srv: Server, ticket):
+    """(code, latency_ms); KF_EAGAIN while pending."""
+    lat = C.c_double(0.0)
+    rc = load().kf_server_poll(srv.ptr, int(ticket), C.byref(lat))
+    if rc != KF_EAGAIN:
+        srv.results.pop(int(ticket), None)
+    return rc, lat.value
+
+
+def kf_server_wait(srv: Server, ticket, timeout_ms=60000.0):
+    lat = C.c_double(0.0)
+    rc = load().kf_server_wait(srv.ptr, int(ticket), float(timeout_ms), C.byref(lat))
+    if rc != KF_ETIMEOUT:
+        srv.results.pop(int(ticket), None)
+    return rc, lat.value
+
+
+def kf_server_stats_get(srv: Server, reset=False) -> dict:
+    st = kf_server_stats()
+    rc = load().kf_server_stats_get(srv.ptr, C.byref(st), int(bool(reset)))
+    d = {name: getattr(st, name) for name, _ in kf_server_stats._fields_ if name != "pad_"}
+    d["rc"] = rc
+    return d
+
+
+def kf_server_destroy(srv: Server):
+    if srv is not None and srv.ptr:
+        load().kf_server_destroy(srv.ptr)
+        srv.ptr = None
+        srv.results.clear()

@@ -2,7 +2,7 @@
 
 This module makes inputs only.  It simulates "truth": charged particles from the
 origin in a uniform longitudinal field, crossing an ideal barrel of cylinders
-(optionally closed by end-cap disks, the "cylinder with lids" of Sec. 4.1),
+(optionally closed by end-cap disks, the barrel-plus-disks detector of Sec. 4.1),
 with a multiple-scattering kick at every crossing and Gaussian hit smearing.
 It holds no step of the Kalman filter: it does not fit, seed, bin or select.
 The crossing points are computed here by intersecting the helix circle with

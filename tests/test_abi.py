@@ -56,6 +56,8 @@ def test_struct_layouts_match_header(libpath, tmp_path):
         "kf_surface": kf.kf_surface, "kf_geometry": kf.kf_geometry, "kf_fit_params": kf.kf_fit_params,
         "kf_seeds": kf.kf_seeds, "kf_track_hits": kf.kf_track_hits, "kf_tracks_out": kf.kf_tracks_out,
         "kf_binned_layer": kf.kf_binned_layer, "kf_build_params": kf.kf_build_params,
+        "kf_server_params": kf.kf_server_params, "kf_event": kf.kf_event, "kf_event_result": kf.kf_event_result,
+        "kf_server_stats": kf.kf_server_stats,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for name, py in structs.items():
@@ -79,3 +81,8 @@ def test_calls_fail_loudly_without_a_context(libpath):
     L = kf.load(libpath)
     assert L.kf_fit(None, None, None, 0, None, None, None, None) == kf.KF_EINVAL
     assert L.kf_bin_hits(None, 0, None, None, None, 1.0, None, None, None, None) == kf.KF_EINVAL
+    out = C.c_void_p()
+    assert L.kf_server_create(None, None, None, C.byref(out)) == kf.KF_EINVAL
+    assert L.kf_server_submit(None, None, None, None) == kf.KF_EINVAL
+    assert L.kf_server_poll(None, 1, None) == kf.KF_EINVAL
+    L.kf_server_destroy(None)
