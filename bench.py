@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--tracks", type=int, default=N_TRACKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
+    ap.add_argument("--part", default="all", choices=["all", "build", "serving", "uneven"],
+                    help="build / serving: only that measurement, printed as its own JSON line")
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="--impl reference: tracks of the workload the oracle fits per step "
+                         "(0: sized so the run takes about two minutes)")
     ap.add_argument("--serving-rates", default="auto",
                     help="comma-separated arrival rates (events/s) of the serving sweep, or auto")
     ap.add_argument("--quick", action="store_true",
@@ -107,24 +112,38 @@ def dist_init(args):
     return world, rank, local
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM)
+
+
+def rank_seed(rank):
+    """Each rank fits its own tracks: independent units, no exchange step."""
+    from paper_1711_06571_gb300 import synth
+    return synth.BASE_SEED + 2 + 1000 * rank
+
+
+def aggregate(ms_local, units_local, world):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    ms = max_over_ranks(ms_local, world)
+    total = sum_over_ranks(units_local, world)
+    return ms, total, total / (ms * 1e-3)
 
 
 def barrier(world):
@@ -133,17 +152,144 @@ def barrier(world):
         dist.barrier()
 
 
-def oracle_baseline(geom, tk, n_sample, threads):
-    """FP64 oracle fit of the first n_sample tracks on `threads` host threads."""
+def oracle_baseline(geom, tk, n_sample, threads, passes=1):
+    """FP64 oracle fit of the first n_sample tracks on `threads` host threads,
+    `passes` times over."""
     import oracle
     oracle.build_lib()
     off = tk["offsets"]
     sub = dict(offsets=off[:n_sample + 1], layer=tk["layer"], x=tk["x"], y=tk["y"], z=tk["z"])
+    upd = 0
     t0 = time.perf_counter()
-    r = oracle.fit(geom, sub, t1=n_sample, threads=threads)
+    for _ in range(passes):
+        r = oracle.fit(geom, sub, t1=n_sample, threads=threads)
+        upd += int(np.sum((r["ndof"][:n_sample] + 5) // 2))
     dt = time.perf_counter() - t0
-    upd = int(np.sum((r["ndof"][:n_sample] + 5) // 2))
     return upd / dt, upd, dt
+
+
+BUILD_WORKLOAD = ("best-hit build of 10 events x 20,000 tracks, 17 barrel layers + 20% uniform noise hits per "
+                  "layer, 1024 phi x 64 z bins, window 3 sigma, <= 32 candidates, chi2 cut 30, all events in one "
+                  "launch")
+
+
+def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000):
+    """One step: bin every layer of every event (kf_bin_hits_batched), seed
+    estimate from the seed hits (kf_make_seeds), best-hit build of all events
+    (kf_build_besthit).  Inputs resident on the device."""
+    import torch
+    from paper_1711_06571_gb300 import kf, run, synth
+    events = [synth.gen_event(geom, n_tracks, synth.BASE_SEED + 300 + e) for e in range(n_events)]
+    L = len(events[0]["layers"])
+    segs = [ev["layers"][l] for ev in events for l in range(L)]
+    so = np.concatenate([[0], np.cumsum([len(ly["x"]) for ly in segs])]).astype(np.int64)
+    half = [geom["surfaces"][ly["surf"]]["half_or_rin"] for ly in segs]
+    H, ns = int(so[-1]), len(segs)
+    dev = torch.device("cuda")
+    x, y, z = (torch.from_numpy(np.concatenate([ly[k] for ly in segs]).astype(np.float32)).to(dev)
+               for k in ("x", "y", "z"))
+    perm = torch.empty(H, dtype=torch.int32, device=dev)
+    offs = torch.empty((ns, kf.KF_NBINS + 1), dtype=torch.int32, device=dev)
+    packed = torch.empty((H, 4), dtype=torch.float32, device=dev)
+    layers = kf.binned_layers([dict(n_hits=int(so[i + 1] - so[i]), surface=int(segs[i]["surf"]),
+                                    packed=packed[so[i]:so[i + 1]] if so[i + 1] > so[i] else packed,
+                                    offsets=offs[i]) for i in range(ns)])
+    counts = [ev["n"] for ev in events]
+    eoff = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    n = int(eoff[-1])
+    sh = np.concatenate([ev["seed_hits"].reshape(-1, 9) for ev in events]).astype(np.float32).reshape(n, 3, 3)
+    sk = dict(offsets=(np.arange(n + 1) * 3).astype(np.int32), layer=np.zeros(3 * n, np.uint8),
+              x=sh[:, :, 0].reshape(-1), y=sh[:, :, 1].reshape(-1), z=sh[:, :, 2].reshape(-1))
+    dsk = run.hits_to_device(sk)
+    sh9 = torch.from_numpy(np.ascontiguousarray(sh.reshape(n, 9).T)).to(dev)
+    g = kf.make_geometry(geom)
+    seed_st = torch.empty((6, n), dtype=torch.float32, device=dev)
+    seed_q = torch.empty(n, dtype=torch.int8, device=dev)
+    idx = torch.empty((L, n), dtype=torch.int32, device=dev)
+    out = run.alloc_fit_out(n)
+    fp, bp = kf.fit_params(), kf.build_params()
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        kf.kf_bin_hits_batched(ctx, so, half, x, y, z, perm, offs, packed)
+        kf.kf_make_seeds(ctx, g, n, dsk["offsets"], dsk["x"], dsk["y"], dsk["z"], seed_st, seed_q)
+        if evs:
+            evs[1].record(stream)
+        kf.kf_build_besthit(ctx, g, fp, bp, n_events, L, layers, eoff, seed_st, seed_q, sh9, idx, out["state"],
+                            out["cov"], out["chi2"], out["ndof"], out["status"])
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for k in range(steps):
+        step(evs[k])
+    torch.cuda.synchronize()
+    t_bin = float(np.mean([a.elapsed_time(b) for a, b, _ in evs]))
+    t_build = float(np.mean([b.elapsed_time(c) for _, b, c in evs]))
+    t_step = float(np.mean([a.elapsed_time(c) for a, _, c in evs]))
+    units = n * (L - 3)  # track-layer build steps per launch
+    found = float((idx[3:] >= 0).float().mean().item())
+    return dict(workload=BUILD_WORKLOAD, value=units / (t_step * 1e-3), unit="track-layer build steps/s",
+                ms_per_step=t_step, bin_and_seed_ms=t_bin, build_launch_ms=t_build,
+                build_kernel_steps_per_s=units / (t_build * 1e-3), hits_binned=H, tracks=n,
+                steps_measured=steps, fraction_of_steps_with_a_hit=found,
+                gpu_launches_per_step=5 + 1 + 4)
+
+
+UNEVEN_WORKLOAD = ("KF fit of 2,000,000 tracks, |eta| < 2.5, 17 barrel cylinders + 2 x 12 end-cap disks at "
+                   "|z| = 30-270 cm (4-26 hits per track), mixed precision, tracks bucketed by hit count, "
+                   "persistent kernel with an atomic work queue replayed as a CUDA graph, launch shape from "
+                   "kf_autotune_fit")
+
+
+def uneven_bench(ctx, steps, warmup, n_tracks=2_000_000):
+    """The uneven batch in one persistent launch: autotune, then time the
+    graph-replayed persistent fit and, for comparison, the grid schedule."""
+    import torch
+    from paper_1711_06571_gb300 import kf, run, synth
+    geom = synth.geometry("lids")
+    g = kf.make_geometry(geom)
+    # the generator runs on the GPU here (2e6 tracks take minutes on the host)
+    tk = synth.gen_tracks(geom, n_tracks, synth.BASE_SEED + 4, eta_max=2.5, min_hits=4, device="cuda")
+    n = tk["n"]
+    nh = np.diff(tk["offsets"])
+    dh = run.hits_to_device(tk)
+    seeds = run.make_seeds(ctx, g, dh)
+    out = run.alloc_fit_out(n)
+    stream = torch.cuda.current_stream()
+    p_grid = kf.fit_params(schedule=kf.KF_SCHED_GRID)
+    p_pers = kf.fit_params(schedule=kf.KF_SCHED_PERSISTENT)
+    report = kf.kf_autotune_fit(ctx, g, p_pers, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"],
+                                dh["y"], dh["z"], out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+
+    def timed(params):
+        def launch():
+            kf.kf_fit(ctx, g, params, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                      out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+        for _ in range(warmup):
+            launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            launch()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    ms_pers = timed(p_pers)
+    upd = int(((out["ndof"] + 5) // 2).clamp(min=0).sum().item())
+    ms_grid = timed(p_grid)
+    return dict(workload=UNEVEN_WORKLOAD, value=upd / (ms_pers * 1e-3), unit="updates/s", ms_per_launch=ms_pers,
+                tracks=int(n), updates_per_launch=upd, hits_per_track=dict(min=int(nh.min()), max=int(nh.max()),
+                                                                          mean=float(nh.mean())),
+                autotune="block,tracks_per_thread,chunk,ms = " + report, grid_schedule_ms=ms_grid,
+                persistent_speedup=ms_grid / ms_pers, steps_measured=steps)
 
 
 SERVING_WORKLOAD = ("serving loop: Poisson arrivals, event sizes log-uniform 500-50,000 tracks (16-event pool at the "
@@ -176,6 +322,7 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
         kf.kf_server_stats_get(srv, reset=True)
         tickets, tracks, lag = [], 0, 0.0
         t0 = time.perf_counter()
+        t_sub = 0.0
         for i in range(n_ev):
             if rate:
                 dt = t0 + t_arr[i] - time.perf_counter()
@@ -195,6 +342,7 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
                 raise RuntimeError(f"kf_server_submit: {rc}")
             tickets.append(t)
             tracks += n
+        t_sub = time.perf_counter() - t0
         bad = [t for t in tickets if kf.kf_server_wait(srv, t, 120000)[0] != kf.KF_OK]
         wall = time.perf_counter() - t0
         st = kf.kf_server_stats_get(srv, reset=True)
@@ -203,7 +351,9 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
         return dict(rate_hz=rate if rate else "saturation", events=n_ev, tracks=int(tracks),
                     p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], max_ms=st["max_ms"], events_per_s=n_ev / wall,
                     tracks_per_s=tracks / wall, mean_batch_events=st["mean_batch_events"],
-                    peak_device_bytes=int(st["peak_bytes_in_use"]), max_submit_lag_ms=lag * 1e3)
+                    peak_device_bytes=int(st["peak_bytes_in_use"]), max_submit_lag_ms=lag * 1e3,
+                    submit_loop_s=t_sub, wall_s=wall, batch_device_ms=st["batch_device_ms"],
+                    copy_out_ms_per_batch=st["copy_out_ms"], stage_ms_per_event=st["stage_ms"])
 
     try:
         stream(None, 32, synth.BASE_SEED + 600)  # warm-up: pool, streams, pinned arena
@@ -224,8 +374,14 @@ def run_reference(args, world, rank):
         return
     geom = synth.geometry("barrel17")
     threads = os.cpu_count() or 1
-    n_sample = 40_000
-    tk = synth.gen_tracks(geom, n_sample, synth.BASE_SEED + 2)
+    n_sample = args.ref_sample
+    if n_sample <= 0:
+        # size each step so that the whole run takes about two minutes of oracle time
+        tk = synth.gen_tracks(geom, 4000, rank_seed(0))
+        _, _, dt = oracle_baseline(geom, tk, 4000, threads)
+        per_step = 120.0 / max(1, args.steps + args.warmup)
+        n_sample = int(min(200_000, max(500, 4000 * per_step / max(dt, 1e-4))))
+    tk = synth.gen_tracks(geom, n_sample, rank_seed(0))
     vals = []
     for i in range(args.warmup + args.steps):
         v, upd, dt = oracle_baseline(geom, tk, n_sample, threads)
@@ -257,9 +413,19 @@ def main():
     ctx = run.context(local)
     geom = synth.geometry("barrel17")
     g = kf.make_geometry(geom)
+    if args.part != "all":
+        if rank == 0:
+            if args.part == "build":
+                r = build_bench(ctx, geom, args.steps, args.warmup)
+            elif args.part == "uneven":
+                r = uneven_bench(ctx, args.steps, args.warmup)
+            else:
+                rates = None if args.serving_rates == "auto" else [float(v) for v in args.serving_rates.split(",")]
+                r = serving_sweep(ctx, geom, rates)
+            print(json.dumps(dict(part=args.part, **r)), flush=True)
+        return
     n = args.tracks
-    # each rank fits its own tracks (independent units, no exchange step)
-    tk = synth.gen_tracks(geom, n, synth.BASE_SEED + 2 + 1000 * rank)
+    tk = synth.gen_tracks(geom, n, rank_seed(rank))
     n = tk["n"]
     dh = run.hits_to_device(tk)
     seeds = run.make_seeds(ctx, g, dh)
@@ -298,9 +464,7 @@ def main():
     clk = clocks.stop()
     ms_local = e0.elapsed_time(e1) / args.steps
     fit_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = max_over_ranks(ms_local, world)
-    total_updates = sum_over_ranks(updates_per_step, world)
-    value = total_updates / (ms * 1e-3)
+    ms, total_updates, value = aggregate(ms_local, updates_per_step, world)
 
     # roofline of the fit kernel: FP64 pipe (dominant), FP32 pipe, HBM
     nh = len(tk["x"])
@@ -377,6 +541,11 @@ def main():
     # the host results equal the device-resident run
     same = np.array_equal(ho["chi2"].numpy(), out["chi2"].cpu().numpy())
 
+    # best-hit build of 10 events x 20,000 tracks
+    build = build_bench(ctx, geom, max(10, args.steps // 4), max(3, args.warmup // 2))
+    # uneven batch: barrel + disks, persistent kernel in a CUDA graph, autotuned
+    uneven = uneven_bench(ctx, max(10, args.steps // 4), max(3, args.warmup // 2))
+
     # serving loop: events of mixed sizes through kf_server (one rank's GPU each)
     serving = None
     if not args.no_serving:
@@ -404,11 +573,14 @@ def main():
         if not args.no_cpu_baseline:
             # about 15 s of oracle work on all host cores: size the sample from a short probe
             threads = os.cpu_count() or 1
-            _, _, dt0 = oracle_baseline(geom, tk, min(n, 20_000), threads)
-            n_sample = int(min(n, max(20_000, 20_000 * 15.0 / max(dt0, 1e-3))))
-            v, upd, dt = oracle_baseline(geom, tk, n_sample, threads)
+            _, _, dt0 = oracle_baseline(geom, tk, min(n, 50_000), threads)
+            want = 50_000 * 15.0 / max(dt0, 1e-3)  # tracks in about 15 s
+            n_sample = int(min(n, max(50_000, want)))
+            passes = max(1, int(round(want / n_sample)))
+            v, upd, dt = oracle_baseline(geom, tk, n_sample, threads, passes)
             cpu_baseline = dict(value=v, unit=UNIT, cores=threads, kind="oracle",
-                                sample=f"first {n_sample} tracks of the workload ({upd} updates, {dt:.1f} s)")
+                                sample=f"first {n_sample} tracks of the workload, {passes} pass(es) "
+                                       f"({upd} updates, {dt:.1f} s)")
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
@@ -422,7 +594,8 @@ def main():
                          ms_per_step=t_e2e * 1e3, api="kf_fit_host", host_matches_device=bool(same)),
                 fp64_path=dict(value=updates_per_step * world / (ms64 * 1e-3), unit=UNIT, fit_ms=ms64,
                                speedup_of_mixed=ms64 / fit_avg),
-                gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity, serving=serving)
+                gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity, build=build, uneven_batch=uneven,
+                serving=serving)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

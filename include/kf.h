@@ -218,6 +218,24 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
 int kf_bin_hits(kf_ctx *ctx, int32_t n_hits, const float *x, const float *y, const float *z, double half_len,
                 int32_t *perm_out, int32_t *offsets_out, float *packed_out, void *stream);
 
+/* The binning of kf_bin_hits for many layers at once (several layers of
+ * several events, Sec. 4.2), in one pass of five kernels instead of five per
+ * layer.  Segment s holds hits segment_offsets[s] .. segment_offsets[s+1]-1 of
+ * the concatenated x, y, z and is binned with its own half_len[s]; its results
+ * are exactly those of kf_bin_hits on that segment alone:
+ *   perm_out: device [H] (H = segment_offsets[n_segments]), at the segment's
+ *     positions, indices local to the segment;
+ *   offsets_out: device [n_segments][KF_NBINS + 1], segment s's CSR offsets
+ *     (local) at s * (KF_NBINS + 1);
+ *   packed_out: device [H][4] or NULL, at the segment's positions, index bits
+ *     local to the segment.
+ * segment_offsets: host [n_segments + 1], starting at 0, non-decreasing
+ * (empty segments are allowed); half_len: host [n_segments], each > 0.  Both
+ * are copied before the call returns. */
+int kf_bin_hits_batched(kf_ctx *ctx, int32_t n_segments, const int32_t *segment_offsets, const double *half_len,
+                        const float *x, const float *y, const float *z, int32_t *perm_out, int32_t *offsets_out,
+                        float *packed_out, void *stream);
+
 /* Binning without any allocation.  The paper has no counterpart: this is the
  * binning of kf_bin_hits for callers that cannot call cudaMalloc, such as a
  * host framework that owns all device memory and hands it out itself, or a
@@ -372,6 +390,9 @@ typedef struct {
     double mean_batch_events;
     double p50_ms, p99_ms, max_ms, mean_ms; /* submit -> results in the caller's arrays */
     double events_per_s, tracks_per_s;      /* completed since the last reset */
+    double batch_device_ms;    /* mean time of a batch on its stream, first copy in to last copy out */
+    double copy_out_ms;        /* mean host time per batch copying results into callers' arrays */
+    double stage_ms;           /* mean host time per event staging its hits in kf_server_submit */
 } kf_server_stats;
 
 /* Start a server on the context's device.  params: host, NULL = defaults.

@@ -622,6 +622,48 @@ int kf_bin_hits(kf_ctx *ctx, int32_t n_hits, const float *x, const float *y, con
     return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "binning kernels");
 }
 
+int kf_bin_hits_batched(kf_ctx *ctx, int32_t n_segments, const int32_t *segment_offsets, const double *half_len,
+                        const float *x, const float *y, const float *z, int32_t *perm_out, int32_t *offsets_out,
+                        float *packed_out, void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (n_segments <= 0 || !segment_offsets || !half_len)
+        return fail(ctx, KF_EINVAL, "n_segments > 0, segment_offsets and half_len required");
+    if (segment_offsets[0] != 0) return fail(ctx, KF_EINVAL, "segment_offsets[0] must be 0");
+    for (int s = 0; s < n_segments; ++s) {
+        if (segment_offsets[s + 1] < segment_offsets[s])
+            return fail(ctx, KF_EINVAL, "segment_offsets must not decrease");
+        if (!(half_len[s] > 0)) return fail(ctx, KF_EINVAL, "half_len[%d] must be > 0", s);
+    }
+    const int H = segment_offsets[n_segments];
+    int rc = set_dev(ctx);
+    if (rc) return rc;
+    NEED_DEV(offsets_out, "offsets_out");
+    if (H > 0) {
+        NEED_DEV(x, "x");
+        NEED_DEV(y, "y");
+        NEED_DEV(z, "z");
+        NEED_DEV(perm_out, "perm_out");
+        OPT_DEV(packed_out, "packed_out");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t so = ((size_t)(n_segments + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
+    const size_t hl = ((size_t)n_segments * sizeof(double) + 255) & ~(size_t)255;
+    void *wsp = nullptr;
+    if ((rc = ws_get(ctx, st, so + hl + bin_segments_scratch_bytes(H, n_segments), &wsp))) return rc;
+    char *w = static_cast<char *>(wsp);
+    // one copy from a pageable buffer of our own, staged by the runtime before the call returns
+    std::vector<char> stage(so + (size_t)n_segments * sizeof(double));
+    memcpy(stage.data(), segment_offsets, (size_t)(n_segments + 1) * sizeof(int32_t));
+    memcpy(stage.data() + so, half_len, (size_t)n_segments * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(w, stage.data(), stage.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_bin_segments(n_segments, H, reinterpret_cast<const int32_t *>(w),
+                                reinterpret_cast<const double *>(w + so), x, y, z, perm_out, offsets_out, packed_out,
+                                w + so + hl, st);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "segmented binning kernels");
+}
+
 // device copy of the layer table and event offsets, in the stream's workspace after `skip` bytes
 static int upload_layers(kf_ctx *ctx, cudaStream_t st, int n_events, int n_layers, const kf_binned_layer *layers,
                          const int32_t *event_offsets, size_t extra, void **ws_out, LayerDev **dl, int32_t **deoff,
@@ -645,19 +687,13 @@ static int upload_layers(kf_ctx *ctx, cudaStream_t st, int n_events, int n_layer
     void *wsp = nullptr;
     int rc = ws_get(ctx, st, tbl_al + eo_al + extra, &wsp);
     if (rc) return rc;
-    // stage through a small pinned buffer so the copy is ordered on the stream
-    void *pin = nullptr;
-    if (cudaMallocHost(&pin, tbl + eo) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, KF_ENOMEM, "pinned staging");
-    }
-    memcpy(pin, host.data(), tbl);
-    memcpy((char *)pin + tbl, event_offsets, eo);
-    cudaError_t e = cudaMemcpyAsync(wsp, pin, tbl, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync((char *)wsp + tbl_al, (char *)pin + tbl, eo, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFreeHost(pin);
+    // one copy from a pageable buffer of our own (the caller's arrays may be
+    // page-locked): the runtime stages a pageable source before the call
+    // returns, so the copy is ordered on the stream without waiting for it
+    std::vector<char> stage(tbl_al + eo);
+    memcpy(stage.data(), host.data(), tbl);
+    memcpy(stage.data() + tbl_al, event_offsets, eo);
+    cudaError_t e = cudaMemcpyAsync(wsp, stage.data(), stage.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "uploading the layer table");
     (void)need_xyz;
     *ws_out = (char *)wsp + tbl_al + eo_al;

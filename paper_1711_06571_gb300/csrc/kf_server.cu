@@ -54,6 +54,7 @@ class PinnedArena {
     // returns nullptr when no block is large enough
     void *alloc(size_t bytes)
     {
+        std::lock_guard<std::mutex> lk(mu_);
         bytes = (bytes + 255) & ~(size_t)255;
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second >= bytes) {
@@ -69,6 +70,7 @@ class PinnedArena {
     void release(void *p)
     {
         if (!p) return;
+        std::lock_guard<std::mutex> lk(mu_);
         const size_t off = static_cast<char *>(p) - static_cast<char *>(base_);
         auto u = used_.find(off);
         if (u == used_.end()) return;
@@ -90,6 +92,7 @@ class PinnedArena {
     }
 
   private:
+    std::mutex mu_;
     void *base_ = nullptr;
     size_t size_ = 0;
     std::map<size_t, size_t> free_, used_;
@@ -113,7 +116,7 @@ struct Done {
 
 struct Batch {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
     bool busy = false;
     std::vector<Event> events;
     void *dev = nullptr;
@@ -122,6 +125,7 @@ struct Batch {
     int N = 0, L = 0;
     // offsets of the results inside `host`
     size_t o_idx = 0, o_st = 0, o_cov = 0, o_chi = 0, o_nd = 0, o_sts = 0, o_bsts = 0;
+    const char *err = nullptr;  // CUDA error text of a failed launch
 };
 
 inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -160,6 +164,8 @@ struct kf_server {
     uint64_t submitted = 0, completed = 0, rejected = 0, n_batches = 0, batch_events = 0;
     std::vector<double> lat;
     uint64_t tracks_done = 0;
+    double dev_ms_sum = 0, copy_ms_sum = 0, stage_ms_sum = 0;
+    uint64_t timed_batches = 0, staged_events = 0;
     Clock::time_point t_reset;
     std::string err;
     std::atomic<bool> stop{false};
@@ -168,6 +174,7 @@ struct kf_server {
     size_t event_bytes(int n, int L, int64_t hb) const;
     static size_t batch_host_bytes(int n, int L);
     int launch(Batch &b);
+    void copy_out(Batch &b);
     void finish(Batch &b, bool ok);
     void loop();
 };
@@ -264,6 +271,7 @@ int kf_server::launch(Batch &b)
         cudaGetLastError();
         return KF_ENOMEM;
     }
+    cudaEventRecord(b.start, st);
     char *D = static_cast<char *>(b.dev);
     char *Hh = b.host;
     auto dp = [&](size_t off) { return D + off; };
@@ -425,7 +433,7 @@ int kf_server::launch(Batch &b)
     if (e == cudaSuccess) e = ef;
     if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
     if (e != cudaSuccess) {
-        err = cudaGetErrorString(e);
+        b.err = cudaGetErrorString(e);
         cudaGetLastError();
         cudaStreamSynchronize(st);  // the copies out of b.host must end before it is reused
         cudaGetLastError();
@@ -436,15 +444,15 @@ int kf_server::launch(Batch &b)
     return KF_OK;
 }
 
-// Hand the results of a finished batch to the callers (lock held).
-void kf_server::finish(Batch &b, bool ok)
+// Copy a finished batch's results into the callers' arrays.  Runs without the
+// lock: only the dispatcher touches a busy batch and its events.
+void kf_server::copy_out(Batch &b)
 {
-    const auto now = Clock::now();
     const int N = b.N, L = b.L;
     int t0 = 0;
     for (auto &x : b.events) {
         const int n = x.n;
-        if (ok) {
+        {
             const kf_event_result &r = x.res;
             if (r.hit_idx)
                 for (int l = 0; l < L; ++l)
@@ -463,6 +471,16 @@ void kf_server::finish(Batch &b, bool ok)
                 for (int t = 0; t < n; ++t) r.status[t] = fs[t] | bs[t];
             }
         }
+        t0 += n;
+    }
+}
+
+// Report the events of a finished batch and free its staging (lock held).
+void kf_server::finish(Batch &b, bool ok)
+{
+    const auto now = Clock::now();
+    for (auto &x : b.events) {
+        const int n = x.n;
         Done d;
         d.rc = ok ? KF_OK : KF_ECUDA;
         d.latency_ms = std::chrono::duration<double, std::milli>(now - x.t_submit).count();
@@ -476,7 +494,6 @@ void kf_server::finish(Batch &b, bool ok)
         in_use -= x.dev_bytes;
         arena.release(x.stage);
         x.stage = nullptr;
-        t0 += n;
     }
     arena.release(b.host);
     b.host = nullptr;
@@ -500,6 +517,17 @@ void kf_server::loop()
             if (q != cudaSuccess) {
                 err = cudaGetErrorString(q);
                 cudaGetLastError();
+            } else {
+                float dms = 0.f;
+                if (cudaEventElapsedTime(&dms, b.start, b.done) != cudaSuccess) cudaGetLastError();
+                lk.unlock();
+                const auto c0 = Clock::now();
+                copy_out(b);
+                const double cms = std::chrono::duration<double, std::milli>(Clock::now() - c0).count();
+                lk.lock();
+                dev_ms_sum += dms;
+                copy_ms_sum += cms;
+                ++timed_batches;
             }
             finish(b, q == cudaSuccess);
             progress = true;
@@ -530,8 +558,13 @@ void kf_server::loop()
             }
             if (take.empty()) break;
             b.events = std::move(take);
+            b.busy = true;  // owned by this thread while unlocked
+            lk.unlock();
             int rc = launch(b);
+            lk.lock();
             if (rc != KF_OK) {
+                b.busy = false;
+                if (b.err) err = b.err;
                 // back to the front of the queue, in order
                 for (auto it = b.events.rbegin(); it != b.events.rend(); ++it) queue.push_front(std::move(*it));
                 const size_t tried = b.events.size();
@@ -555,7 +588,6 @@ void kf_server::loop()
                 // else: wait for a batch in flight to return its memory
                 break;
             }
-            b.busy = true;
             in_use += bytes;
             peak = std::max(peak, in_use);
             ++n_batches;
@@ -616,10 +648,11 @@ int kf_server_create(kf_ctx *ctx, const kf_geometry *geom, const kf_server_param
     s->batches.resize(P.max_batches);
     for (auto &b : s->batches) {
         if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreate(&b.start) != cudaSuccess || cudaEventCreate(&b.done) != cudaSuccess) {
             cudaGetLastError();
             for (auto &c : s->batches) {
                 if (c.stream) cudaStreamDestroy(c.stream);
+                if (c.start) cudaEventDestroy(c.start);
                 if (c.done) cudaEventDestroy(c.done);
             }
             cudaMemPoolDestroy(s->pool);
@@ -661,13 +694,10 @@ int kf_server_submit(kf_server *s, const kf_event *ev, const kf_event_result *re
     x.res = res ? *res : kf_event_result{};
     x.dev_bytes = s->event_bytes(n, L, hb);
     x.t_submit = t_submit;
-    std::unique_lock<std::mutex> lk(s->mu);
-    if (x.dev_bytes > s->p.mem_budget_bytes) {
-        ++s->rejected;
-        return KF_EBUSY;
-    }
     const size_t stage_bytes = 4 * (3 * (size_t)hb + 9 * (size_t)n);
-    if (stage_bytes + s->batch_host_bytes(n, L) > s->p.host_staging_bytes) {
+    if (x.dev_bytes > s->p.mem_budget_bytes ||
+        stage_bytes + s->batch_host_bytes(n, L) > s->p.host_staging_bytes) {
+        std::lock_guard<std::mutex> lk(s->mu);
         ++s->rejected;
         return KF_EBUSY;
     }
@@ -690,6 +720,10 @@ int kf_server_submit(kf_server *s, const kf_event *ev, const kf_event_result *re
             sy[3 * t + k] = ev->seed_hits[9 * t + 3 * k + 1];
             sz[3 * t + k] = ev->seed_hits[9 * t + 3 * k + 2];
         }
+    const double sms = std::chrono::duration<double, std::milli>(Clock::now() - t_submit).count();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stage_ms_sum += sms;
+    ++s->staged_events;
     x.ticket = s->next_ticket++;
     *ticket = x.ticket;
     s->pending[x.ticket] = 1;
@@ -768,7 +802,12 @@ int kf_server_stats_get(kf_server *s, kf_server_stats *out, int reset)
     const double secs = std::chrono::duration<double>(Clock::now() - s->t_reset).count();
     out->events_per_s = secs > 0 ? (double)v.size() / secs : 0.0;
     out->tracks_per_s = secs > 0 ? (double)s->tracks_done / secs : 0.0;
+    out->batch_device_ms = s->timed_batches ? s->dev_ms_sum / (double)s->timed_batches : 0.0;
+    out->copy_out_ms = s->timed_batches ? s->copy_ms_sum / (double)s->timed_batches : 0.0;
+    out->stage_ms = s->staged_events ? s->stage_ms_sum / (double)s->staged_events : 0.0;
     if (reset) {
+        s->dev_ms_sum = s->copy_ms_sum = s->stage_ms_sum = 0;
+        s->timed_batches = s->staged_events = 0;
         s->lat.clear();
         s->tracks_done = 0;
         s->t_reset = Clock::now();
@@ -794,6 +833,7 @@ void kf_server_destroy(kf_server *s)
         if (b.stream) cudaStreamSynchronize(b.stream);
         if (b.host) s->arena.release(b.host);
         if (b.stream) cudaStreamDestroy(b.stream);
+        if (b.start) cudaEventDestroy(b.start);
         if (b.done) cudaEventDestroy(b.done);
     }
     if (s->pool) cudaMemPoolDestroy(s->pool);

@@ -111,7 +111,8 @@ class kf_server_stats(C.Structure):
                 ("in_flight_batches", C.c_int32), ("pad_", C.c_int32), ("bytes_in_use", C.c_size_t),
                 ("peak_bytes_in_use", C.c_size_t), ("mean_batch_events", C.c_double), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("max_ms", C.c_double), ("mean_ms", C.c_double),
-                ("events_per_s", C.c_double), ("tracks_per_s", C.c_double)]
+                ("events_per_s", C.c_double), ("tracks_per_s", C.c_double), ("batch_device_ms", C.c_double),
+                ("copy_out_ms", C.c_double), ("stage_ms", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -138,6 +139,9 @@ _SIGS = {
                                    C.POINTER(kf_build_params), C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
                                    C.POINTER(C.c_int32), C.POINTER(kf_seeds), C.c_void_p, C.c_void_p,
                                    C.POINTER(kf_tracks_out), C.c_void_p]),
+    "kf_bin_hits_batched": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "kf_bin_hits_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "kf_measure_peak": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
@@ -298,6 +302,17 @@ def kf_autotune_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x,
 def kf_bin_hits(ctx, n_hits, x, y, z, half_len, perm_out, offsets_out, packed_out=None, stream=None):
     _check(ctx, load().kf_bin_hits(ctx, int(n_hits), _ptr(x), _ptr(y), _ptr(z), float(half_len), _ptr(perm_out),
                                    _ptr(offsets_out), _ptr(packed_out), _stream(stream)))
+
+
+def kf_bin_hits_batched(ctx, segment_offsets, half_len, x, y, z, perm_out, offsets_out, packed_out=None,
+                        stream=None):
+    """Bin many layers in one pass: segment_offsets (n_segments + 1) and half_len (n_segments) are host
+    sequences; x, y, z the concatenated device coordinates."""
+    ns = len(half_len)
+    so = (C.c_int32 * (ns + 1))(*[int(v) for v in segment_offsets])
+    hl = (C.c_double * ns)(*[float(v) for v in half_len])
+    _check(ctx, load().kf_bin_hits_batched(ctx, ns, so, hl, _ptr(x), _ptr(y), _ptr(z), _ptr(perm_out),
+                                           _ptr(offsets_out), _ptr(packed_out), _stream(stream)))
 
 
 def kf_bin_hits_static(n_hits, x, y, z, half_len, perm_out, offsets_out, packed_out=None, stream=None) -> int:

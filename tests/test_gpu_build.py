@@ -85,6 +85,45 @@ def test_binning_edge_cases(ctx, oracle_mod):
         np.testing.assert_array_equal(pg, po)
 
 
+def test_batched_binning_equals_per_layer(ctx, oracle_mod):
+    """kf_bin_hits_batched over every layer of two events plus the edge cases
+    (empty segments included) gives, per segment, exactly the per-layer call's
+    results, and the per-layer call equals the oracle on these inputs."""
+    g = synth.geometry("barrel17")
+    segs = []
+    for e in range(2):
+        ev = synth.gen_event(g, 3000 + 1700 * e, synth.BASE_SEED + 13 + e)
+        segs += [(ly["x"], ly["y"], ly["z"], g["surfaces"][ly["surf"]]["half_or_rin"]) for ly in ev["layers"]]
+    z0 = np.zeros(0, np.float32)
+    segs.insert(5, (z0, z0, z0, 12.5))
+    segs.append((np.full(999, 20.0, np.float32), np.full(999, 0.001, np.float32), np.ones(999, np.float32), 40.0))
+    segs.append((z0, z0, z0, 3.0))
+    sizes = [len(s[0]) for s in segs]
+    so = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    H, ns = int(so[-1]), len(segs)
+    dev = torch.device("cuda")
+    xt, yt, zt = (torch.from_numpy(np.concatenate([s[k] for s in segs]).astype(np.float32)).to(dev) for k in range(3))
+    perm = torch.empty(H, dtype=torch.int32, device=dev)
+    off = torch.full((ns, kf.KF_NBINS + 1), -5, dtype=torch.int32, device=dev)
+    packed = torch.empty((H, 4), dtype=torch.float32, device=dev)
+    kf.kf_bin_hits_batched(ctx, so, [s[3] for s in segs], xt, yt, zt, perm, off, packed)
+    torch.cuda.synchronize()
+    perm_h, off_h, pk_h = perm.cpu().numpy(), off.cpu().numpy(), packed.cpu().numpy()
+    for i, (x, y, z, half) in enumerate(segs):
+        a, b = so[i], so[i + 1]
+        pg, og, pkg = _bin_gpu(ctx, x, y, z, half)
+        np.testing.assert_array_equal(off_h[i], og)
+        np.testing.assert_array_equal(perm_h[a:b], pg)
+        np.testing.assert_array_equal(pk_h[a:b].view(np.int32), pkg.view(np.int32))
+        if i in (0, 5, ns - 2):
+            po, oo = oracle_mod.bin_layer(x, y, z, half)
+            np.testing.assert_array_equal(og, oo)
+    with pytest.raises(kf.KfError):
+        kf.kf_bin_hits_batched(ctx, [0, 3, 2], [1.0, 1.0], xt, yt, zt, perm, off, packed)
+    with pytest.raises(kf.KfError):
+        kf.kf_bin_hits_batched(ctx, [0, 3], [0.0], xt, yt, zt, perm, off, packed)
+
+
 # ------------------------------------------------------------------ building
 
 def _binned_oracle_event(oracle_mod, g, ev):
