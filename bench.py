@@ -288,7 +288,7 @@ def uneven_bench(ctx, steps, warmup, n_tracks=2_000_000):
     return dict(workload=UNEVEN_WORKLOAD, value=upd / (ms_pers * 1e-3), unit="updates/s", ms_per_launch=ms_pers,
                 tracks=int(n), updates_per_launch=upd, hits_per_track=dict(min=int(nh.min()), max=int(nh.max()),
                                                                           mean=float(nh.mean())),
-                autotune="block,tracks_per_thread,chunk,ms = " + report, grid_schedule_ms=ms_grid,
+                autotune="block,tracks_per_thread,grid,ms = " + report, grid_schedule_ms=ms_grid,
                 persistent_speedup=ms_grid / ms_pers, steps_measured=steps)
 
 

@@ -193,11 +193,12 @@ int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, in
 int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
                 const kf_track_hits *hits, const kf_tracks_out *out, int32_t n_chunks);
 
-/* Choose block size, tracks per thread and work-queue chunk of the persistent
+/* Choose block size and tracks per thread (per work-queue grab) of the persistent
  * fit for this (n, hit count) by timing candidates on the given inputs (it
  * runs the fit several times and overwrites out).  The choice is cached in the
  * context and used by later kf_fit calls with schedule = KF_SCHED_PERSISTENT.
- * report (host, may be NULL) receives "block,tpt,chunk,ms" of the winner. */
+ * report (host, may be NULL) receives "block,tracks_per_thread,grid,ms" of the
+ * winner. */
 int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
                     const kf_seeds *seeds, const kf_track_hits *hits, const kf_tracks_out *out, void *stream,
                     char *report, size_t report_len);

@@ -21,7 +21,7 @@ struct Buf {
 };
 
 struct Tuned {
-    int block = 128, grid = 0, chunk = 64;
+    int block = 128, grid = 0, chunk = 1;  // chunk: tracks per thread per queue grab
     float ms = 0.f;
 };
 
@@ -548,7 +548,7 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     Tuned best;
     best.ms = 1e30f;
     const int blocks[3] = {64, 128, 256};
-    const int chunks[3] = {32, 64, 128};
+    const int chunks[3] = {1, 2, 4};  // tracks per thread per grab
     for (int bi = 0; bi < 3; ++bi) {
         const int occ = persistent_blocks_per_sm(fp64, blocks[bi]);
         if (occ <= 0) continue;
@@ -584,7 +584,7 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
         ctx->tuned[{fp64 ? 1 : 0, n_bucket(n)}] = best;
     }
     if (report && report_len)
-        snprintf(report, report_len, "%d,%d,%d,%d,%.4f", best.block, 1, best.chunk, best.grid, best.ms);
+        snprintf(report, report_len, "%d,%d,%d,%.4f", best.block, best.chunk, best.grid, best.ms);
     return KF_OK;
 }
 

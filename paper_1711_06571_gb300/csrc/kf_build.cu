@@ -150,11 +150,19 @@ __device__ __forceinline__ bool shared_factor(const C pc[21], const Surf &sf, Ld
                 (double)pc[pk(2, 1)], (double)(pc[pk(2, 2)] + vz), fs);
 }
 
+// The build parameters a layer step reads.
+struct StepKnobs {
+    int ms_on;
+    int max_cand;
+    float nsigma;
+    float chi2_cut;
+};
+
 // One build layer for one track with per-thread scoring: propagate, transport,
 // scattering noise, window, candidates, update.  JOSEPH selects the covariance
 // update form (the FP64 steps).
 template <bool JOSEPH, class T, class P, class C>
-__device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], T alpha, T mass2, const BuildArgs &a,
+__device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], T alpha, T mass2, const StepKnobs &a,
                                                      const Surf &sf, const LayerDev &ly, double &chi2,
                                                      unsigned &status, bool &alive)
 {
@@ -198,7 +206,7 @@ __device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], 
 
 // FP64 layer step for a mixed-path track at a near-tangent crossing
 __device__ __forceinline__ StepOut layer_step_fp64(Track<float, ff> &st, float pc[21], double alpha, double mass2,
-                                                   const BuildArgs &a, const Surf &sf, const LayerDev &ly,
+                                                   const StepKnobs &a, const Surf &sf, const LayerDev &ly,
                                                    double &chi2, unsigned &status, bool &alive)
 {
     Track<double, double> sd;
@@ -227,6 +235,22 @@ __device__ __forceinline__ StepOut layer_step_fp64(Track<float, ff> &st, float p
         for (int i = 0; i < 21; ++i) pc[i] = (float)pd[i];
     }
     return o;
+}
+
+// layer_step_fp64 out of line, so that the FP32 layer loop stays compact in
+// the instruction cache (about 2% of the steps are near-tangent)
+struct Fp64LayerIO {
+    MixedIO m;
+    StepOut o;
+    int alive;
+};
+static __device__ __noinline__ Fp64LayerIO layer_step_fp64_out_of_line(Fp64LayerIO io, double alpha, double mass2,
+                                                                       StepKnobs kn, const Surf *sf, LayerDev ly)
+{
+    bool alive = io.alive != 0;
+    io.o = layer_step_fp64(io.m.st, io.m.p, alpha, mass2, kn, *sf, ly, io.m.chi2, io.m.status, alive);
+    io.alive = alive;
+    return io;
 }
 
 // Warp-cooperative scoring of one layer: every lane of the warp calls it; lanes
@@ -350,7 +374,9 @@ __device__ __forceinline__ void score_coop(const Track<T, P> &st, bool do_step, 
 // (whose updates are the FP64 ones) and in FP64 on the all-FP64 path; a mixed
 // step at a near-tangent crossing runs in FP64.
 template <bool FP64, bool COOP>
-__global__ void __launch_bounds__(128) build_kernel(const Geom g, const BuildArgs a)
+// three blocks per SM (at most 168 registers a thread): 12 warps to hide the
+// FP64 and memory latencies of the layer steps
+__global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const BuildArgs a)
 {
     using T = typename sel_t<FP64>::T;
     using P = typename sel_t<FP64>::P;
@@ -387,6 +413,7 @@ __global__ void __launch_bounds__(128) build_kernel(const Geom g, const BuildArg
 #pragma unroll
     for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
     C pc[21];
+    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
     const int n1 = min(a.n64, 3);
     int k = 0;
     for (; k < n1 && alive; ++k) {
@@ -408,7 +435,10 @@ __global__ void __launch_bounds__(128) build_kernel(const Geom g, const BuildArg
             sincos_pos(st.phi, sphi, cphi);
         }
         if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
-        if (!kf_update<true>(st, pd, hx, hy, hz, sf, chi2)) {
+        // the first hit meets the diagonal seed covariance: the structured update
+        const bool ok = k == 0 ? kf_seed_update(st, pd, hx, hy, hz, sf, chi2)
+                               : kf_update<true>(st, pd, hx, hy, hz, sf, chi2);
+        if (!ok) {
             status |= KF_ST_CHOL_FAIL;
             alive = false;
             break;
@@ -453,14 +483,22 @@ __global__ void __launch_bounds__(128) build_kernel(const Geom g, const BuildArg
         bool near_tangent = false;
         if constexpr (!FP64) near_tangent = alive && crossing_sine(st, alpha, sf) > 0.8f;
         if (near_tangent) {
-            if constexpr (!FP64) so = layer_step_fp64(st, pc, alphad, g.mass2d, a, sf, ly, chi2, status, alive);
+            if constexpr (!FP64) {
+                Fp64LayerIO io;
+                mixed_pack(io.m, st, pc, chi2, status);
+                io.alive = alive;
+                io = layer_step_fp64_out_of_line(io, alphad, g.mass2d, kn, &sf, ly);
+                mixed_unpack(io.m, st, pc, chi2, status);
+                alive = io.alive != 0;
+                so = io.o;
+            }
         }
         // the cooperative path needs the S factor shared by a layer's candidates; the
         // condition is the same for every lane (all events share the geometry)
         const bool coop = COOP && sf.var_rad == sf.var_rphi;
         if (!coop) {
             if (alive && !near_tangent)
-                so = layer_step_thread<false>(st, pc, alpha, mass2, a, sf, ly, chi2, status, alive);
+                so = layer_step_thread<false>(st, pc, alpha, mass2, kn, sf, ly, chi2, status, alive);
         } else {
             // every lane of the warp takes part in the shuffles, stepping or not
             bool do_step = alive && !near_tangent;

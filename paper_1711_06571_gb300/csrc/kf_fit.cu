@@ -198,6 +198,15 @@ __device__ __forceinline__ bool fp64_step(Track<float, ff> &st, float pf[21], in
     return true;
 }
 
+// fp64_step out of line (a near-tangent crossing is about 2% of the steps)
+static __device__ __noinline__ MixedIO fp64_step_out_of_line(MixedIO m, int k, double alpha, double mass2,
+                                                             int ms_on, const Surf *sf, float hx, float hy,
+                                                             float hz)
+{
+    m.ok = fp64_step(m.st, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
+    return m;
+}
+
 template <class C>
 __device__ __forceinline__ void store_cov(double *o_cov, int n, int t, const C p[21])
 {
@@ -279,9 +288,11 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
             if (near_tangent) {
                 // near-tangent crossing: the whole step in FP64 (Joseph form)
                 if constexpr (!FP64) {
-                    if (!fp64_step(st, pf, k, kbd * (double)(-q), mass2d, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h],
-                                   chi2, status))
-                        break;
+                    MixedIO m;
+                    mixed_pack(m, st, pf, chi2, status);
+                    m = fp64_step_out_of_line(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
+                                              a.hz[h]);
+                    if (!mixed_unpack(m, st, pf, chi2, status)) break;
                 }
             } else if (!fit_step<false, T>(st, pf, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
                                            status)) {
@@ -317,24 +328,29 @@ __global__ void __launch_bounds__(128) fit_kernel(const Geom g, const FitArgs a)
     fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
 }
 
-// Persistent form: a grid sized to the machine; each warp takes chunks of
-// a.chunk consecutive entries of a.order (tracks sorted by descending hit
-// count, so a warp's 32 tracks cross nearly the same number of layers) from
-// an atomic work counter until the queue is empty (dynamic load balancing in
-// place of the work stealing of Sec. 3.2).
+// Persistent form: a grid sized to the machine; each block takes
+// BLOCK * a.chunk consecutive entries of a.order (a.chunk = tracks per thread;
+// the order groups tracks by hit count and seed 1/pT, so neighbouring threads
+// cross nearly the same layers) from an atomic work counter until the queue is
+// empty: dynamic load balancing in place of the work stealing of Sec. 3.2.  The
+// whole block takes work together and meets at a barrier between grabs, so its
+// warps run the same part of the loop at the same time (warps that drift apart
+// in a loop of this size compete for the instruction cache).
 template <bool FP64, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const Geom g, const FitArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
+    __shared__ int s_base;
     load_geom(g, s_surf);
-    const int lane = threadIdx.x & 31;
+    const int per = BLOCK * a.chunk;
     for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(a.queue, a.chunk);
-        base = __shfl_sync(0xffffffffu, base, 0);
+        if (threadIdx.x == 0) s_base = atomicAdd(a.queue, per);
+        __syncthreads();
+        const int base = s_base;
+        __syncthreads();  // every thread has read s_base before thread 0 writes the next one
         if (base >= a.count) break;
-        const int end = min(base + a.chunk, a.count);
-        for (int i = base + lane; i < end; i += 32) {
+        const int end = min(base + per, a.count);
+        for (int i = base + (int)threadIdx.x; i < end; i += BLOCK) {
             const int t = a.t_begin + (a.order ? a.order[i] : i);
             fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
         }

@@ -29,7 +29,7 @@ struct FitArgs {
     // persistent schedule
     const int32_t *order;  // processing order (tracks sorted by hit count), or null
     int32_t *queue;        // work counter, zeroed before the launch
-    int chunk;             // tracks taken per queue grab (multiple of 32)
+    int chunk;             // tracks per thread per queue grab (a block takes blockDim * chunk)
     int pad2_;
 };
 

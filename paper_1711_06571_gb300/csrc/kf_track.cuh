@@ -409,6 +409,52 @@ __device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, f
 // a seed phase) the update runs in FP64, Joseph form.
 constexpr float UPDATE_FP64_RATIO = 100.f;
 
+// A mixed-path track handed by value to an out-of-line FP64 routine.  The
+// rarely taken FP64 branches of the FP32 layer loop are kept out of line so that
+// the loop's own code stays compact in the instruction cache (warps of a
+// persistent kernel run different parts of the loop at the same time).
+struct MixedIO {
+    Track<float, ff> st;
+    float p[21];
+    double chi2;
+    unsigned status;
+    int ok;
+};
+
+__device__ __forceinline__ void mixed_pack(MixedIO &m, const Track<float, ff> &st, const float p[21], double chi2,
+                                           unsigned status)
+{
+    m.st = st;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) m.p[i] = p[i];
+    m.chi2 = chi2;
+    m.status = status;
+    m.ok = 0;
+}
+__device__ __forceinline__ bool mixed_unpack(const MixedIO &m, Track<float, ff> &st, float p[21], double &chi2,
+                                             unsigned &status)
+{
+    st = m.st;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) p[i] = m.p[i];
+    chi2 = m.chi2;
+    status = m.status;
+    return m.ok != 0;
+}
+
+// the FP64 Joseph update of an FP32 covariance, out of line
+static __device__ __noinline__ MixedIO kf_update_fp64_of_f32(MixedIO m, float hx, float hy, float hz,
+                                                             const Surf *sf)
+{
+    double pd[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pd[i] = f2d(m.p[i]);
+    m.ok = kf_update<true>(m.st, pd, hx, hy, hz, *sf, m.chi2);
+#pragma unroll
+    for (int i = 0; i < 21; ++i) m.p[i] = d2f(pd[i]);
+    return m;
+}
+
 template <class Pp>
 __device__ __forceinline__ bool kf_update_mixed(Track<float, Pp> &st, float p[21], float hx, float hy, float hz,
                                                 const Surf &sf, double &chi2)
@@ -418,13 +464,11 @@ __device__ __forceinline__ bool kf_update_mixed(Track<float, Pp> &st, float p[21
     const bool informative = p[pk(0, 0)] > UPDATE_FP64_RATIO * rxx || p[pk(1, 1)] > UPDATE_FP64_RATIO * ryy ||
                              p[pk(2, 2)] > UPDATE_FP64_RATIO * rzz;
     if (informative) {
-        double pd[21];
-#pragma unroll
-        for (int i = 0; i < 21; ++i) pd[i] = f2d(p[i]);
-        const bool ok = kf_update<true>(st, pd, hx, hy, hz, sf, chi2);
-#pragma unroll
-        for (int i = 0; i < 21; ++i) p[i] = d2f(pd[i]);
-        return ok;
+        MixedIO m;
+        unsigned status = 0u;
+        mixed_pack(m, st, p, chi2, status);
+        m = kf_update_fp64_of_f32(m, hx, hy, hz, &sf);
+        return mixed_unpack(m, st, p, chi2, status);
     }
     return kf_update<false>(st, p, hx, hy, hz, sf, chi2);
 }
