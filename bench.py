@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=0,
                     help="--impl reference: tracks of the workload the oracle fits per step "
                          "(0: sized so the run takes about two minutes)")
+    ap.add_argument("--serving-memory", default="pinned", choices=["pinned", "pageable"],
+                    help="client buffers of the serving sweep: page-locked (allocated once) or pageable")
+    ap.add_argument("--serving-copy", action="store_true", help="serving sweep: staged copies instead of zero-copy")
     ap.add_argument("--serving-rates", default="auto",
                     help="comma-separated arrival rates (events/s) of the serving sweep, or auto")
     ap.add_argument("--quick", action="store_true",
@@ -301,32 +304,64 @@ SERVING_WORKLOAD = ("serving loop: Poisson arrivals, event sizes log-uniform 500
                     "fit per event, 40 GB device-memory budget")
 
 
-def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
+def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0, memory="pinned", zero_copy=True):
     """Events through kf_server: first as fast as they can be submitted (the
     saturation throughput), then Poisson streams at fractions of it.  Latency is
-    the library's own submit -> results-in-caller-arrays time per event."""
+    the library's own submit -> results-in-caller-arrays time per event.
+
+    memory = "pinned": the client keeps its events and result buffers in
+    page-locked memory allocated once (what a serving client does), so the
+    server's kernels read the hits in place (zero_copy) and write the results
+    straight into the caller's arrays.  memory = "pageable": ordinary numpy
+    arrays, result arrays freshly allocated per request."""
+    import torch
     from paper_1711_06571_gb300 import kf, synth
+
+    def host(a):
+        a = np.ascontiguousarray(a)
+        return torch.from_numpy(a).pin_memory().numpy() if memory == "pinned" else a
+
     sizes = np.exp(np.linspace(np.log(500), np.log(50000), pool_size)).astype(np.int64)
     pool = []
     for i, sz in enumerate(sizes):
         ev = synth.gen_event(geom, int(sz), synth.BASE_SEED + 500 + i)
         L = len(ev["layers"])
         lay = [ev["layers"][l] if l >= 3 else None for l in range(L)]
-        xs = [None if ly is None else np.ascontiguousarray(ly["x"], np.float32) for ly in lay]
-        ys = [None if ly is None else np.ascontiguousarray(ly["y"], np.float32) for ly in lay]
-        zs = [None if ly is None else np.ascontiguousarray(ly["z"], np.float32) for ly in lay]
+        xs = [None if ly is None else host(np.asarray(ly["x"], np.float32)) for ly in lay]
+        ys = [None if ly is None else host(np.asarray(ly["y"], np.float32)) for ly in lay]
+        zs = [None if ly is None else host(np.asarray(ly["z"], np.float32)) for ly in lay]
         surf = [int(ly["surf"]) for ly in ev["layers"]]
-        pool.append((ev["n"], surf, xs, ys, zs, np.ascontiguousarray(ev["seed_hits"], np.float32), L))
+        pool.append((ev["n"], surf, xs, ys, zs, host(np.asarray(ev["seed_hits"], np.float32)), L))
+    max_events = 600
+    ring = 96  # result buffers of the client: at most this many requests outstanding
+    arena = None
+    if memory == "pinned":
+        # page-locked result buffers allocated once, reused round robin
+        L = pool[0][6]
+        per = max(p[0] for p in pool) * (4 * L + 48 + 168 + 8 + 4 + 4) + 6 * 64
+        arena = torch.empty(per * ring, dtype=torch.uint8).pin_memory().numpy()
     srv = kf.kf_server_create(ctx, geom, kf.server_params(mem_budget_bytes=40 << 30, max_batches=4,
                                                           max_batch_events=16))
+
+    def results(n, L, slot):
+        shapes = (("hit_idx", (L, n), np.int32), ("state", (6, n), np.float64), ("cov", (21, n), np.float64),
+                  ("chi2", (n,), np.float64), ("ndof", (n,), np.int32), ("status", (n,), np.uint32))
+        if arena is None:
+            return {k: np.empty(sh, dt) for k, sh, dt in shapes}
+        out, off = {}, (slot % ring) * (len(arena) // ring)
+        for k, sh, dt in shapes:
+            nb = int(np.prod(sh)) * np.dtype(dt).itemsize
+            out[k] = arena[off:off + nb].view(dt).reshape(sh)
+            off += (nb + 63) // 64 * 64
+        return out
 
     def stream(rate, n_ev, seed):
         t_arr, _ = synth.serving_stream(seed, n_ev, rate if rate else 1.0)
         pick = np.random.default_rng(seed + 1).integers(0, pool_size, n_ev)
         kf.kf_server_stats_get(srv, reset=True)
         tickets, tracks, lag = [], 0, 0.0
+        done_early = set()
         t0 = time.perf_counter()
-        t_sub = 0.0
         for i in range(n_ev):
             if rate:
                 dt = t0 + t_arr[i] - time.perf_counter()
@@ -335,10 +370,13 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
                 else:
                     lag = max(lag, -dt)
             n, surf, xs, ys, zs, sh, L = pool[pick[i]]
-            res = dict(hit_idx=np.empty((L, n), np.int32), state=np.empty((6, n)), cov=np.empty((21, n)),
-                       chi2=np.empty(n), ndof=np.empty(n, np.int32), status=np.empty(n, np.uint32))
+            if arena is not None and i >= ring:  # the buffer's previous request must be done
+                if kf.kf_server_wait(srv, tickets[i - ring], 120000)[0] != kf.KF_OK:
+                    raise RuntimeError("serving: an event failed")
+                done_early.add(i - ring)
+            res = results(n, L, i)
             while True:
-                rc, t = kf.kf_server_submit(srv, n, surf, xs, ys, zs, sh, **res)
+                rc, t = kf.kf_server_submit(srv, n, surf, xs, ys, zs, sh, zero_copy=zero_copy, **res)
                 if rc != kf.KF_EAGAIN:
                     break
                 time.sleep(2e-4)
@@ -347,7 +385,8 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
             tickets.append(t)
             tracks += n
         t_sub = time.perf_counter() - t0
-        bad = [t for t in tickets if kf.kf_server_wait(srv, t, 120000)[0] != kf.KF_OK]
+        bad = [t for i, t in enumerate(tickets)
+               if i not in done_early and kf.kf_server_wait(srv, t, 120000)[0] != kf.KF_OK]
         wall = time.perf_counter() - t0
         st = kf.kf_server_stats_get(srv, reset=True)
         if bad or st["rc"] != kf.KF_OK:
@@ -357,18 +396,18 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0):
                     tracks_per_s=tracks / wall, mean_batch_events=st["mean_batch_events"],
                     peak_device_bytes=int(st["peak_bytes_in_use"]), max_submit_lag_ms=lag * 1e3,
                     submit_loop_s=t_sub, wall_s=wall, batch_device_ms=st["batch_device_ms"],
-                    copy_out_ms_per_batch=st["copy_out_ms"], stage_ms_per_event=st["stage_ms"])
+                    copy_out_ms_per_batch=st["copy_out_ms"], submit_ms_per_event=st["stage_ms"])
 
     try:
         stream(None, 32, synth.BASE_SEED + 600)  # warm-up: pool, streams, pinned arena
         sat = stream(None, 400, synth.BASE_SEED + 601)
         if rates is None:
             rates = [f * sat["events_per_s"] for f in (0.25, 0.5, 0.8)]
-        runs = [stream(r, int(min(600, max(60, r * seconds_per_rate))), synth.BASE_SEED + 610 + k)
+        runs = [stream(r, int(min(max_events, max(60, r * seconds_per_rate))), synth.BASE_SEED + 610 + k)
                 for k, r in enumerate(rates)]
     finally:
         kf.kf_server_destroy(srv)
-    return dict(workload=SERVING_WORKLOAD, saturation=sat, rates=runs)
+    return dict(workload=SERVING_WORKLOAD, client_memory=memory, zero_copy=zero_copy, saturation=sat, rates=runs)
 
 
 def run_reference(args, world, rank):
@@ -425,7 +464,7 @@ def main():
                 r = uneven_bench(ctx, args.steps, args.warmup)
             else:
                 rates = None if args.serving_rates == "auto" else [float(v) for v in args.serving_rates.split(",")]
-                r = serving_sweep(ctx, geom, rates)
+                r = serving_sweep(ctx, geom, rates, memory=args.serving_memory, zero_copy=not args.serving_copy)
             print(json.dumps(dict(part=args.part, **r)), flush=True)
         return
     n = args.tracks
@@ -556,7 +595,7 @@ def main():
     serving = None
     if not args.no_serving:
         rates = None if args.serving_rates == "auto" else [float(v) for v in args.serving_rates.split(",")]
-        serving = serving_sweep(ctx, geom, rates)
+        serving = serving_sweep(ctx, geom, rates, memory=args.serving_memory, zero_copy=not args.serving_copy)
 
     # parity on a sample against the FP64 oracle
     import oracle

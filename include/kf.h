@@ -345,15 +345,22 @@ typedef struct {
                                   batch: larger batches for some latency; 0 = start at once */
 } kf_server_params;
 
-/* One event, all host memory, read during kf_server_submit only (it is
- * copied into the staging arena before the call returns).
+/* One event, all host memory.
  *   n_tracks > 0 seeds; n_layers 4..KF_MAX_SURFACES, all barrels; the first
  *   three layers are the seed layers.
  *   surface [n_layers]: geometry index of each layer.
  *   n_hits [n_layers]: hits of each layer (layers 0..2 are not read).
  *   x, y, z [n_layers]: per layer, a host array of n_hits[l] FP32 coordinates
  *     (layers 0..2 are not read and may be NULL).
- *   seed_hits [n_tracks][3][3]: hit k of track t, (x, y, z) at 9t + 3k. */
+ *   seed_hits [n_tracks][3][3]: hit k of track t, (x, y, z) at 9t + 3k.
+ *   flags: 0 = the coordinate and seed-hit arrays are copied into the staging
+ *     arena before kf_server_submit returns; KF_EVENT_ZERO_COPY = the caller
+ *     keeps them unchanged until the ticket completes and the kernels read them
+ *     in place (any host memory on a GPU that reads pageable memory, such as a
+ *     Grace-Blackwell board; elsewhere page-locked memory, else they are copied).
+ * The small arrays (surface, n_hits and the x, y, z pointer arrays) are read
+ * during the call only. */
+#define KF_EVENT_ZERO_COPY 1
 typedef struct {
     int32_t n_tracks;
     int32_t n_layers;
@@ -363,10 +370,15 @@ typedef struct {
     const float *const *y;
     const float *const *z;
     const float *seed_hits;
+    int32_t flags;
+    int32_t pad_;
 } kf_event;
 
 /* Where an event's results go: host arrays the caller keeps alive until the
- * ticket has completed (the dispatcher thread writes them).  Any may be NULL.
+ * ticket has completed.  A kernel writes them in place where the GPU can reach
+ * them (any host memory on a GPU that reads pageable memory, else page-locked
+ * memory); otherwise the dispatcher thread copies them from staging.  Any may
+ * be NULL.
  *   hit_idx [n_layers][n_tracks]: as kf_build_besthit's hit_idx_out.
  *   state [6][n_tracks], cov [21][n_tracks], chi2, ndof: final fit over the
  *     seed hits and the chosen hits, as kf_fit.

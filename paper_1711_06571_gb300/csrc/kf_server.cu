@@ -2,16 +2,21 @@
 // a dispatcher thread admits them as device memory and stream slots free up,
 // merges the admitted ones into batches (continuous batching: a batch is formed
 // from whatever is queued when a slot frees, while earlier batches still run)
-// and runs every batch on its own stream, so batches overlap on the device and
-// their copies overlap other batches' kernels (Sec. 4.2: several events at a
-// time; Sec. 4.3: copies overlapped with processing).
+// and runs every batch on its own stream, so batches overlap on the device
+// (Sec. 4.2: several events at a time; Sec. 4.3: copies overlapped with
+// processing).
 //
-// Per batch, on its stream: copy the events' build-layer hits and seed hits in,
-// bin every (event, layer) in one segmented pass, seed, best-hit build of all
-// events in one launch, gather the chosen hits, final fit, copy the results
-// out, release the batch memory.  The per-track arithmetic is the same as in
-// the direct entry points, so a result does not depend on what it was batched
-// with.
+// Per batch, on its stream: one copy of the batch's tables, a kernel that
+// gathers every event's build-layer hits and seed hits from host memory, one
+// segmented binning pass over every (event, layer), seeds, best-hit build of
+// all events in one launch, gather of the chosen hits, final fit, and a kernel
+// that writes every event's results into its caller's arrays.  The host copies
+// nothing: on a GPU that reads host memory over the CPU-GPU link (a
+// Grace-Blackwell board: pageable memory included, at about 200 GB/s against
+// about 15 GB/s for one CPU core's memcpy) the kernels move the data; elsewhere
+// the same kernels read page-locked staging.  The per-track arithmetic is that
+// of the direct entry points, so a result does not depend on what it was
+// batched with.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -102,9 +107,14 @@ struct Event {
     uint64_t ticket = 0;
     int n = 0, L = 0;
     std::vector<int32_t> surface, n_hits;  // per layer
-    int64_t hb = 0;                       // hits of the build layers (3..L-1)
-    float *stage = nullptr;               // pinned: x[hb] y[hb] z[hb] sx[3n] sy[3n] sz[3n]
-    kf_event_result res{};
+    int64_t hb = 0;                        // hits of the build layers (3..L-1)
+    // where the kernels read the inputs: the caller's arrays (zero-copy) or the staging
+    std::vector<const float *> x, y, z;  // per layer (layers 0..2 unused)
+    const float *seed_hits = nullptr;    // [n][3][3]
+    float *stage = nullptr;              // page-locked staging: x[hb] y[hb] z[hb] seed_hits[9n], or null
+    kf_event_result res{};               // the caller's result arrays
+    kf_event_result dres{};              // the same as the kernels address them (direct_out)
+    bool direct_out = true;              // the kernels write dres directly (else via the batch's staging)
     size_t dev_bytes = 0;
     Clock::time_point t_submit;
 };
@@ -114,34 +124,202 @@ struct Done {
     double latency_ms = 0;
 };
 
+// One segment of the batch's hit arrays (a build layer of one event).
+struct SegIn {
+    const float *x, *y, *z;
+    int32_t count, dst;
+};
+
+// One event of a batch: its seed hits and where its results go.
+struct EvIO {
+    const float *seed_hits;  // [n][3][3]
+    int32_t *hit_idx;        // [L][n]
+    double *state;           // [6][n]
+    double *cov;             // [21][n]
+    double *chi2;
+    int32_t *ndof;
+    uint32_t *status;
+    int32_t n, t0;
+};
+
 struct Batch {
     cudaStream_t stream = nullptr;
     cudaEvent_t start = nullptr, done = nullptr;
     bool busy = false;
     std::vector<Event> events;
     void *dev = nullptr;
-    size_t dev_bytes = 0;
-    char *host = nullptr;  // pinned: tables in, results out
+    char *host = nullptr;  // page-locked: tables, then staged results of events without direct output
+    std::vector<size_t> staged_res;  // per event: offset of its staged results in `host` (or SIZE_MAX)
     int N = 0, L = 0;
-    // offsets of the results inside `host`
-    size_t o_idx = 0, o_st = 0, o_cov = 0, o_chi = 0, o_nd = 0, o_sts = 0, o_bsts = 0;
     const char *err = nullptr;  // CUDA error text of a failed launch
 };
 
 inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
-__global__ void seed_soa_kernel(int n, const float *__restrict__ sx, const float *__restrict__ sy,
-                                const float *__restrict__ sz, float *__restrict__ sh9)
+// One event's results staged in page-locked memory: the caller's arrays, each
+// starting on a 256-byte boundary (the doubles must be 8-byte aligned whatever
+// n and L are).
+struct ResLayout {
+    size_t idx, st, cov, chi, nd, sts, total;
+};
+inline ResLayout res_layout(int n, int L)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        sh9[(3 * k + 0) * (size_t)n + t] = sx[3 * t + k];
-        sh9[(3 * k + 1) * (size_t)n + t] = sy[3 * t + k];
-        sh9[(3 * k + 2) * (size_t)n + t] = sz[3 * t + k];
+    ResLayout r;
+    const size_t m = (size_t)n;
+    r.idx = 0;
+    r.st = r.idx + al(4 * (size_t)L * m);
+    r.cov = r.st + al(48 * m);
+    r.chi = r.cov + al(168 * m);
+    r.nd = r.chi + al(8 * m);
+    r.sts = r.nd + al(4 * m);
+    r.total = r.sts + al(4 * m);
+    return r;
+}
+inline size_t result_bytes(int n, int L) { return res_layout(n, L).total; }
+
+// blockIdx.y = segment; the blocks along x stride over its hits
+__global__ void gather_hits_kernel(const SegIn *__restrict__ seg, float *__restrict__ x, float *__restrict__ y,
+                                   float *__restrict__ z)
+{
+    const SegIn g = seg[blockIdx.y];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.count; j += gridDim.x * blockDim.x) {
+        x[g.dst + j] = g.x[j];
+        y[g.dst + j] = g.y[j];
+        z[g.dst + j] = g.z[j];
     }
 }
+
+__device__ __forceinline__ int event_of(const int32_t *__restrict__ eoff, int n_events, int t)
+{
+    int lo = 0, hi = n_events - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (eoff[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// seed hits of every track: CSR arrays (3 hits a track) for the seed estimate
+// and the [9][N] planes the build and the gather read
+__global__ void gather_seeds_kernel(int N, int E, const EvIO *__restrict__ ev, const int32_t *__restrict__ eoff,
+                                    float *__restrict__ sx, float *__restrict__ sy, float *__restrict__ sz,
+                                    int32_t *__restrict__ soff, float *__restrict__ sh9)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const EvIO e = ev[event_of(eoff, E, t)];
+    const float *h = e.seed_hits + 9 * (size_t)(t - e.t0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float hx = h[3 * k + 0], hy = h[3 * k + 1], hz = h[3 * k + 2];
+        sx[3 * t + k] = hx;
+        sy[3 * t + k] = hy;
+        sz[3 * t + k] = hz;
+        sh9[(3 * k + 0) * (size_t)N + t] = hx;
+        sh9[(3 * k + 1) * (size_t)N + t] = hy;
+        sh9[(3 * k + 2) * (size_t)N + t] = hz;
+    }
+    soff[t] = 3 * t;
+    if (t == N - 1) soff[N] = 3 * N;
+}
+
+// every track's results into its event's arrays ([k][n] planes of the event)
+__global__ void scatter_results_kernel(int N, int E, int L, const EvIO *__restrict__ ev,
+                                       const int32_t *__restrict__ eoff, const int32_t *__restrict__ idx,
+                                       const double *__restrict__ st, const double *__restrict__ cov,
+                                       const double *__restrict__ chi2, const int32_t *__restrict__ ndof,
+                                       const uint32_t *__restrict__ fsts, const uint32_t *__restrict__ bsts)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const EvIO e = ev[event_of(eoff, E, t)];
+    const size_t n = (size_t)e.n, u = (size_t)(t - e.t0);
+    if (e.hit_idx)
+        for (int l = 0; l < L; ++l) e.hit_idx[l * n + u] = idx[(size_t)l * N + t];
+    if (e.state)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) e.state[i * n + u] = st[(size_t)i * N + t];
+    if (e.cov)
+#pragma unroll
+        for (int i = 0; i < 21; ++i) e.cov[i * n + u] = cov[(size_t)i * N + t];
+    if (e.chi2) e.chi2[u] = chi2[t];
+    if (e.ndof) e.ndof[u] = ndof[t];
+    if (e.status) e.status[u] = fsts[t] | bsts[t];
+}
+
+struct CopyJob {
+    char *dst;
+    const char *src;
+    size_t bytes;
+};
+
+// Host copies shared between the calling thread and a few worker threads.
+class CopyPool {
+  public:
+    void start(int workers)
+    {
+        for (int i = 0; i < workers; ++i) threads_.emplace_back([this] { work(); });
+    }
+    ~CopyPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : threads_) t.join();
+    }
+    // copy every job; returns when all are done
+    void run(const std::vector<CopyJob> &jobs)
+    {
+        if (jobs.empty()) return;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            jobs_ = &jobs;
+            next_ = 0;
+            left_ = jobs.size();
+        }
+        cv_.notify_all();
+        drain();
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [this] { return left_ == 0; });
+        jobs_ = nullptr;
+    }
+
+  private:
+    void drain()
+    {
+        for (;;) {
+            const CopyJob *j = nullptr;
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                if (!jobs_ || next_ >= jobs_->size()) return;
+                j = &(*jobs_)[next_++];
+            }
+            memcpy(j->dst, j->src, j->bytes);
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--left_ == 0) done_.notify_all();
+        }
+    }
+    void work()
+    {
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [this] { return stop_ || (jobs_ && next_ < jobs_->size()); });
+                if (stop_) return;
+            }
+            drain();
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    std::vector<std::thread> threads_;
+    const std::vector<CopyJob> *jobs_ = nullptr;
+    size_t next_ = 0, left_ = 0;
+    bool stop_ = false;
+};
 
 }  // namespace
 
@@ -149,7 +327,7 @@ struct kf_server {
     kf_ctx *ctx = nullptr;
     int device = 0;
     Geom geom{};
-    std::vector<kf_surface> surfaces;
+    bool host_access = false;  // kernels may read and write pageable host memory
     kf_server_params p{};
     cudaMemPool_t pool = nullptr;
     PinnedArena arena;
@@ -169,6 +347,7 @@ struct kf_server {
     Clock::time_point t_reset;
     std::string err;
     std::atomic<bool> stop{false};
+    CopyPool copies;  // declared before the dispatcher thread: destroyed after it is joined
     std::thread worker;
 
     size_t event_bytes(int n, int L, int64_t hb) const;
@@ -178,6 +357,33 @@ struct kf_server {
     void finish(Batch &b, bool ok);
     void loop();
 };
+
+// Device address of page-locked host memory p, else null.
+static const void *pinned_view(const void *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Address under which a kernel can reach host memory p: p itself where the GPU
+// reads pageable memory, the mapped address of page-locked memory, else null.
+static const void *device_view(const kf_server *s, const void *p)
+{
+    if (!p) return nullptr;
+    if (s->host_access) return p;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) return at.devicePointer;
+    return nullptr;
+}
 
 size_t kf_server::event_bytes(int n, int L, int64_t hb) const
 {
@@ -194,22 +400,22 @@ size_t kf_server::event_bytes(int n, int L, int64_t hb) const
     b += al(4 * (size_t)n + 4) + al((size_t)L * n) + 3 * al(4 * (size_t)L * n) + al(gather_scratch_bytes(n));
     b += al(24 * (size_t)n) + al((size_t)n);                    // final-fit seeds
     b += al(48 * (size_t)n) + al(168 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * (size_t)n);  // outputs
-    b += al(sizeof(LayerDev) * (size_t)L);                      // layer table
+    b += al(sizeof(LayerDev) * (size_t)L) + al(sizeof(SegIn) * nseg) + al(sizeof(EvIO));  // tables
     // a merged batch rounds each of its ~40 arrays up once: an event's share of
     // that rounding is below 40 * 256 bytes, so the sum over a batch's events
     // bounds the batch's allocation
     return b + 40 * 256;
 }
 
-// Pinned bytes of a one-event batch's tables and results (a bound: the batch
-// layout below rounds each of its arrays up to 256 bytes).
+// Page-locked bytes of a one-event batch (tables, staged results; a bound).
 size_t kf_server::batch_host_bytes(int n, int L)
 {
-    return (size_t)n * (4 * (size_t)L + 48 + 168 + 8 + 4 + 4 + 4 + 4) + 4 * (size_t)L * 8 +
-           sizeof(LayerDev) * (size_t)L + 13 * 256 + 64;
+    const size_t nseg = (size_t)(L - 3);
+    return sizeof(SegIn) * nseg + 12 * nseg + sizeof(EvIO) + sizeof(LayerDev) * (size_t)L + 16 +
+           result_bytes(n, L) + 16 * 256;
 }
 
-// Launch one batch on its stream (called with the lock held).
+// Launch one batch on its stream (the dispatcher, without the lock).
 int kf_server::launch(Batch &b)
 {
     const int E = (int)b.events.size();
@@ -223,44 +429,37 @@ int kf_server::launch(Batch &b)
     const int nseg = E * (L - 3);
     b.N = N;
     b.L = L;
-    // ---- device layout
+    // ---- device layout: the tables first (one copy), then the work arrays
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
         o += al(bytes);
         return r;
     };
+    const size_t d_seg = take(sizeof(SegIn) * (size_t)nseg), d_segoff = take(4 * (size_t)(nseg + 1)),
+                 d_half = take(8 * (size_t)nseg), d_ev = take(sizeof(EvIO) * (size_t)E),
+                 d_ltab = take(sizeof(LayerDev) * (size_t)E * L), d_eoff = take(4 * (size_t)(E + 1));
+    const size_t tables = o;
     const size_t d_x = take(4 * HB), d_y = take(4 * HB), d_z = take(4 * HB), d_perm = take(4 * HB),
                  d_pk = take(16 * HB), d_off = take(4 * (size_t)nseg * (KF_NBINS + 1)),
-                 d_bs = take(bin_segments_scratch_bytes((int)HB, nseg)), d_segoff = take(4 * (size_t)(nseg + 1)),
-                 d_half = take(8 * (size_t)nseg), d_sx = take(12 * (size_t)N), d_sy = take(12 * (size_t)N),
-                 d_sz = take(12 * (size_t)N), d_sh9 = take(36 * (size_t)N), d_soff = take(4 * (size_t)(N + 1)),
-                 d_seed = take(24 * (size_t)N), d_q = take(N), d_idx = take(4 * (size_t)L * N),
-                 d_bsts = take(4 * (size_t)N), d_ord1 = take(4 * (order_scratch_ints() + N)),
-                 d_ltab = take(sizeof(LayerDev) * (size_t)E * L), d_eoff = take(4 * (size_t)(E + 1)),
-                 d_goff = take(4 * (size_t)(N + 1)), d_glay = take((size_t)L * N), d_gx = take(4 * (size_t)L * N),
-                 d_gy = take(4 * (size_t)L * N), d_gz = take(4 * (size_t)L * N), d_gsc = take(gather_scratch_bytes(N)),
-                 d_fseed = take(24 * (size_t)N), d_fq = take(N), d_ord2 = take(4 * (order_scratch_ints() + N)),
-                 d_st = take(48 * (size_t)N), d_cov = take(168 * (size_t)N), d_chi = take(8 * (size_t)N),
-                 d_nd = take(4 * (size_t)N), d_sts = take(4 * (size_t)N);
-    b.dev_bytes = o;
-    // ---- pinned host: tables in, results out
-    size_t h = 0;
-    auto htake = [&](size_t bytes) {
-        size_t r = h;
-        h += al(bytes);
-        return r;
-    };
-    const size_t h_segoff = htake(4 * (size_t)(nseg + 1)), h_half = htake(8 * (size_t)nseg),
-                 h_soff = htake(4 * (size_t)(N + 1)), h_ltab = htake(sizeof(LayerDev) * (size_t)E * L),
-                 h_eoff = htake(4 * (size_t)(E + 1));
-    b.o_idx = htake(4 * (size_t)L * N);
-    b.o_st = htake(48 * (size_t)N);
-    b.o_cov = htake(168 * (size_t)N);
-    b.o_chi = htake(8 * (size_t)N);
-    b.o_nd = htake(4 * (size_t)N);
-    b.o_sts = htake(4 * (size_t)N);
-    b.o_bsts = htake(4 * (size_t)N);
+                 d_bs = take(bin_segments_scratch_bytes((int)HB, nseg)), d_sx = take(12 * (size_t)N),
+                 d_sy = take(12 * (size_t)N), d_sz = take(12 * (size_t)N), d_sh9 = take(36 * (size_t)N),
+                 d_soff = take(4 * (size_t)(N + 1)), d_seed = take(24 * (size_t)N), d_q = take(N),
+                 d_idx = take(4 * (size_t)L * N), d_bsts = take(4 * (size_t)N),
+                 d_ord1 = take(4 * (order_scratch_ints() + N)), d_goff = take(4 * (size_t)(N + 1)),
+                 d_glay = take((size_t)L * N), d_gx = take(4 * (size_t)L * N), d_gy = take(4 * (size_t)L * N),
+                 d_gz = take(4 * (size_t)L * N), d_gsc = take(gather_scratch_bytes(N)), d_fseed = take(24 * (size_t)N),
+                 d_fq = take(N), d_ord2 = take(4 * (order_scratch_ints() + N)), d_st = take(48 * (size_t)N),
+                 d_cov = take(168 * (size_t)N), d_chi = take(8 * (size_t)N), d_nd = take(4 * (size_t)N),
+                 d_sts = take(4 * (size_t)N);
+    // ---- page-locked host: the tables, then staged results of events the kernels cannot write directly
+    size_t h = tables;
+    b.staged_res.assign(E, SIZE_MAX);
+    for (int ev = 0; ev < E; ++ev)
+        if (!b.events[ev].direct_out) {
+            b.staged_res[ev] = h;
+            h += al(result_bytes(b.events[ev].n, L));
+        }
     b.host = static_cast<char *>(arena.alloc(h));
     if (!b.host) return KF_EAGAIN;
     cudaStream_t st = b.stream;
@@ -275,34 +474,39 @@ int kf_server::launch(Batch &b)
     char *D = static_cast<char *>(b.dev);
     char *Hh = b.host;
     auto dp = [&](size_t off) { return D + off; };
-    int32_t *segoff = reinterpret_cast<int32_t *>(Hh + h_segoff);
-    double *half = reinterpret_cast<double *>(Hh + h_half);
-    int32_t *soff = reinterpret_cast<int32_t *>(Hh + h_soff);
-    LayerDev *ltab = reinterpret_cast<LayerDev *>(Hh + h_ltab);
-    int32_t *eoff = reinterpret_cast<int32_t *>(Hh + h_eoff);
-    // tables
-    int64_t hpos = 0;
-    int seg = 0, tpos = 0;
+    SegIn *seg = reinterpret_cast<SegIn *>(Hh + d_seg);
+    int32_t *segoff = reinterpret_cast<int32_t *>(Hh + d_segoff);
+    double *half = reinterpret_cast<double *>(Hh + d_half);
+    EvIO *eio = reinterpret_cast<EvIO *>(Hh + d_ev);
+    LayerDev *ltab = reinterpret_cast<LayerDev *>(Hh + d_ltab);
+    int32_t *eoff = reinterpret_cast<int32_t *>(Hh + d_eoff);
+    int64_t lpos = 0;
+    int sg = 0, tpos = 0, max_count = 0;
     eoff[0] = 0;
     for (int ev = 0; ev < E; ++ev) {
-        Event &x = b.events[ev];
-        // copies of this event's build-layer hits and seed hits into the batch arrays
-        e = cudaMemcpyAsync(dp(d_x) + 4 * hpos, x.stage, 4 * x.hb, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dp(d_y) + 4 * hpos, x.stage + x.hb, 4 * x.hb, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dp(d_z) + 4 * hpos, x.stage + 2 * x.hb, 4 * x.hb, cudaMemcpyHostToDevice, st);
-        const float *sbase = x.stage + 3 * x.hb;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dp(d_sx) + 12 * (size_t)tpos, sbase, 12 * (size_t)x.n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dp(d_sy) + 12 * (size_t)tpos, sbase + 3 * x.n, 12 * (size_t)x.n,
-                                cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dp(d_sz) + 12 * (size_t)tpos, sbase + 6 * x.n, 12 * (size_t)x.n,
-                                cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) break;
-        int64_t lpos = hpos;
+        const Event &x = b.events[ev];
+        EvIO &io = eio[ev];
+        io.seed_hits = x.seed_hits;
+        io.n = x.n;
+        io.t0 = tpos;
+        if (x.direct_out) {
+            io.hit_idx = x.dres.hit_idx;
+            io.state = x.dres.state;
+            io.cov = x.dres.cov;
+            io.chi2 = x.dres.chi2;
+            io.ndof = x.dres.ndof;
+            io.status = x.dres.status;
+        } else {  // the caller's layout inside the batch's page-locked block
+            char *r = static_cast<char *>(const_cast<void *>(device_view(this, Hh + b.staged_res[ev])));
+            if (!r) r = Hh + b.staged_res[ev];
+            const ResLayout rl = res_layout(x.n, L);
+            io.hit_idx = reinterpret_cast<int32_t *>(r + rl.idx);
+            io.state = reinterpret_cast<double *>(r + rl.st);
+            io.cov = reinterpret_cast<double *>(r + rl.cov);
+            io.chi2 = reinterpret_cast<double *>(r + rl.chi);
+            io.ndof = reinterpret_cast<int32_t *>(r + rl.nd);
+            io.status = reinterpret_cast<uint32_t *>(r + rl.sts);
+        }
         for (int l = 0; l < L; ++l) {
             LayerDev &ld = ltab[(size_t)ev * L + l];
             ld.surface = x.surface[l];
@@ -313,29 +517,43 @@ int kf_server::launch(Batch &b)
                 ld.n_hits = 0;
                 continue;
             }
-            segoff[seg] = (int32_t)lpos;
-            half[seg] = geom.s[x.surface[l]].halfd;
-            ld.n_hits = x.n_hits[l];
+            const int m = x.n_hits[l];
+            seg[sg] = SegIn{x.x[l], x.y[l], x.z[l], m, (int32_t)lpos};
+            segoff[sg] = (int32_t)lpos;
+            half[sg] = geom.s[x.surface[l]].halfd;
+            max_count = std::max(max_count, m);
+            ld.n_hits = m;
             ld.packed = reinterpret_cast<const float4 *>(dp(d_pk) + 16 * lpos);
-            ld.offsets = reinterpret_cast<const int32_t *>(dp(d_off) + 4 * (size_t)seg * (KF_NBINS + 1));
+            ld.offsets = reinterpret_cast<const int32_t *>(dp(d_off) + 4 * (size_t)sg * (KF_NBINS + 1));
             ld.x = reinterpret_cast<const float *>(dp(d_x) + 4 * lpos);
             ld.y = reinterpret_cast<const float *>(dp(d_y) + 4 * lpos);
             ld.z = reinterpret_cast<const float *>(dp(d_z) + 4 * lpos);
-            lpos += x.n_hits[l];
-            ++seg;
+            lpos += m;
+            ++sg;
         }
-        hpos += x.hb;
         tpos += x.n;
         eoff[ev + 1] = tpos;
     }
     segoff[nseg] = (int32_t)HB;
-    for (int t = 0; t <= N; ++t) soff[t] = 3 * t;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp(d_segoff), segoff, 4 * (size_t)(nseg + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp(d_half), half, 8 * (size_t)nseg, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp(d_soff), soff, 4 * (size_t)(N + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dp(d_ltab), ltab, sizeof(LayerDev) * (size_t)E * L, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp(d_eoff), eoff, 4 * (size_t)(E + 1), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(D, Hh, tables, cudaMemcpyHostToDevice, st);
+    // inputs: every event's build-layer hits and seed hits, read where they are
+    if (e == cudaSuccess && HB > 0) {
+        dim3 grid((unsigned)std::max(1, std::min((max_count + 1023) / 1024, 64)), (unsigned)nseg);
+        gather_hits_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const SegIn *>(dp(d_seg)),
+                                                 reinterpret_cast<float *>(dp(d_x)),
+                                                 reinterpret_cast<float *>(dp(d_y)),
+                                                 reinterpret_cast<float *>(dp(d_z)));
+        e = cudaGetLastError();
+    }
+    const int32_t *deoff = reinterpret_cast<const int32_t *>(dp(d_eoff));
+    const EvIO *dev_io = reinterpret_cast<const EvIO *>(dp(d_ev));
+    float *sh9 = reinterpret_cast<float *>(dp(d_sh9));
+    if (e == cudaSuccess) {
+        gather_seeds_kernel<<<(N + 127) / 128, 128, 0, st>>>(
+            N, E, dev_io, deoff, reinterpret_cast<float *>(dp(d_sx)), reinterpret_cast<float *>(dp(d_sy)),
+            reinterpret_cast<float *>(dp(d_sz)), reinterpret_cast<int32_t *>(dp(d_soff)), sh9);
+        e = cudaGetLastError();
+    }
     // bin every build layer of every event
     if (e == cudaSuccess)
         e = launch_bin_segments(nseg, (int)HB, reinterpret_cast<int32_t *>(dp(d_segoff)),
@@ -346,16 +564,9 @@ int kf_server::launch(Batch &b)
     // seeds from the three seed hits
     float *seed = reinterpret_cast<float *>(dp(d_seed));
     int8_t *q = reinterpret_cast<int8_t *>(dp(d_q));
-    float *sh9 = reinterpret_cast<float *>(dp(d_sh9));
     if (e == cudaSuccess)
         e = launch_seeds(geom, N, N, 0, reinterpret_cast<int32_t *>(dp(d_soff)), reinterpret_cast<float *>(dp(d_sx)),
                          reinterpret_cast<float *>(dp(d_sy)), reinterpret_cast<float *>(dp(d_sz)), seed, q, st);
-    if (e == cudaSuccess) {
-        seed_soa_kernel<<<(N + 127) / 128, 128, 0, st>>>(N, reinterpret_cast<float *>(dp(d_sx)),
-                                                         reinterpret_cast<float *>(dp(d_sy)),
-                                                         reinterpret_cast<float *>(dp(d_sz)), sh9);
-        e = cudaGetLastError();
-    }
     // best-hit build of all events
     int32_t *idx = reinterpret_cast<int32_t *>(dp(d_idx));
     int32_t *ord1 = reinterpret_cast<int32_t *>(dp(d_ord1));
@@ -373,7 +584,7 @@ int kf_server::launch(Batch &b)
         a.nsigma = (float)p.build.nsigma;
         a.chi2_cut = (float)p.build.chi2_cut;
         a.layers = reinterpret_cast<const LayerDev *>(dp(d_ltab));
-        a.event_off = reinterpret_cast<const int32_t *>(dp(d_eoff));
+        a.event_off = deoff;
         a.seed_state = seed;
         a.q = q;
         a.seed_hits = sh9;
@@ -388,9 +599,8 @@ int kf_server::launch(Batch &b)
     float *gx = reinterpret_cast<float *>(dp(d_gx)), *gy = reinterpret_cast<float *>(dp(d_gy)),
           *gz = reinterpret_cast<float *>(dp(d_gz));
     if (e == cudaSuccess)
-        e = launch_gather(N, E, L, reinterpret_cast<const LayerDev *>(dp(d_ltab)),
-                          reinterpret_cast<const int32_t *>(dp(d_eoff)), sh9, idx, goff, glay, gx, gy, gz, dp(d_gsc),
-                          st);
+        e = launch_gather(N, E, L, reinterpret_cast<const LayerDev *>(dp(d_ltab)), deoff, sh9, idx, goff, glay, gx,
+                          gy, gz, dp(d_gsc), st);
     float *fseed = reinterpret_cast<float *>(dp(d_fseed));
     int8_t *fq = reinterpret_cast<int8_t *>(dp(d_fq));
     int32_t *ord2 = reinterpret_cast<int32_t *>(dp(d_ord2));
@@ -420,22 +630,22 @@ int kf_server::launch(Batch &b)
         a.order = ord2 + order_scratch_ints();
         e = launch_fit(geom, a, p.fit.precision == KF_PREC_FP64, 128, st);
     }
-    // results out
-    struct {
-        size_t d, h, bytes;
-    } outs[] = {{d_idx, b.o_idx, 4 * (size_t)L * N}, {d_st, b.o_st, 48 * (size_t)N},
-                {d_cov, b.o_cov, 168 * (size_t)N}, {d_chi, b.o_chi, 8 * (size_t)N},
-                {d_nd, b.o_nd, 4 * (size_t)N},    {d_sts, b.o_sts, 4 * (size_t)N},
-                {d_bsts, b.o_bsts, 4 * (size_t)N}};
-    for (auto &c : outs)
-        if (e == cudaSuccess) e = cudaMemcpyAsync(Hh + c.h, dp(c.d), c.bytes, cudaMemcpyDeviceToHost, st);
+    // results: every event's slice into its arrays
+    if (e == cudaSuccess) {
+        scatter_results_kernel<<<(N + 127) / 128, 128, 0, st>>>(
+            N, E, L, dev_io, deoff, idx, reinterpret_cast<const double *>(dp(d_st)),
+            reinterpret_cast<const double *>(dp(d_cov)), reinterpret_cast<const double *>(dp(d_chi)),
+            reinterpret_cast<const int32_t *>(dp(d_nd)), reinterpret_cast<const uint32_t *>(dp(d_sts)),
+            reinterpret_cast<const uint32_t *>(dp(d_bsts)));
+        e = cudaGetLastError();
+    }
     cudaError_t ef = cudaFreeAsync(b.dev, st);
     if (e == cudaSuccess) e = ef;
     if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
     if (e != cudaSuccess) {
         b.err = cudaGetErrorString(e);
         cudaGetLastError();
-        cudaStreamSynchronize(st);  // the copies out of b.host must end before it is reused
+        cudaStreamSynchronize(st);  // nothing may still read b.host when it is reused
         cudaGetLastError();
         arena.release(b.host);
         b.host = nullptr;
@@ -444,35 +654,34 @@ int kf_server::launch(Batch &b)
     return KF_OK;
 }
 
-// Copy a finished batch's results into the callers' arrays.  Runs without the
-// lock: only the dispatcher touches a busy batch and its events.
+// Copy the staged results of a finished batch's events into their callers'
+// arrays (events whose arrays are not page-locked).  Runs without the lock:
+// only the dispatcher touches a busy batch and its events.  The copies are cut
+// into pieces shared with the copy threads (one core copies about 15 GB/s).
 void kf_server::copy_out(Batch &b)
 {
-    const int N = b.N, L = b.L;
-    int t0 = 0;
-    for (auto &x : b.events) {
-        const int n = x.n;
-        {
-            const kf_event_result &r = x.res;
-            if (r.hit_idx)
-                for (int l = 0; l < L; ++l)
-                    memcpy(r.hit_idx + (size_t)l * n, b.host + b.o_idx + 4 * ((size_t)l * N + t0), 4 * (size_t)n);
-            if (r.state)
-                for (int i = 0; i < 6; ++i)
-                    memcpy(r.state + (size_t)i * n, b.host + b.o_st + 8 * ((size_t)i * N + t0), 8 * (size_t)n);
-            if (r.cov)
-                for (int i = 0; i < 21; ++i)
-                    memcpy(r.cov + (size_t)i * n, b.host + b.o_cov + 8 * ((size_t)i * N + t0), 8 * (size_t)n);
-            if (r.chi2) memcpy(r.chi2, b.host + b.o_chi + 8 * (size_t)t0, 8 * (size_t)n);
-            if (r.ndof) memcpy(r.ndof, b.host + b.o_nd + 4 * (size_t)t0, 4 * (size_t)n);
-            if (r.status) {
-                const uint32_t *fs = reinterpret_cast<const uint32_t *>(b.host + b.o_sts) + t0;
-                const uint32_t *bs = reinterpret_cast<const uint32_t *>(b.host + b.o_bsts) + t0;
-                for (int t = 0; t < n; ++t) r.status[t] = fs[t] | bs[t];
-            }
-        }
-        t0 += n;
+    const int L = b.L;
+    std::vector<CopyJob> jobs;
+    auto add = [&](void *dst, const char *src, size_t bytes) {
+        constexpr size_t PIECE = (size_t)1 << 20;
+        for (size_t o = 0; o < bytes; o += PIECE)
+            jobs.push_back(CopyJob{static_cast<char *>(dst) + o, src + o, std::min(PIECE, bytes - o)});
+    };
+    for (size_t ev = 0; ev < b.events.size(); ++ev) {
+        if (b.staged_res[ev] == SIZE_MAX) continue;
+        const Event &x = b.events[ev];
+        const kf_event_result &r = x.res;
+        const size_t n = (size_t)x.n;
+        const char *src = b.host + b.staged_res[ev];
+        const ResLayout rl = res_layout(x.n, L);
+        if (r.hit_idx) add(r.hit_idx, src + rl.idx, 4 * L * n);
+        if (r.state) add(r.state, src + rl.st, 48 * n);
+        if (r.cov) add(r.cov, src + rl.cov, 168 * n);
+        if (r.chi2) add(r.chi2, src + rl.chi, 8 * n);
+        if (r.ndof) add(r.ndof, src + rl.nd, 4 * n);
+        if (r.status) add(r.status, src + rl.sts, 4 * n);
     }
+    copies.run(jobs);
 }
 
 // Report the events of a finished batch and free its staging (lock held).
@@ -632,6 +841,12 @@ int kf_server_create(kf_ctx *ctx, const kf_geometry *geom, const kf_server_param
     s->p = P;
     s->device = dev;
     s->geom = G;
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        pageable = 0;
+    }
+    s->host_access = pageable != 0;
     cudaMemPoolProps props;
     memset(&props, 0, sizeof props);
     props.allocType = cudaMemAllocationTypePinned;
@@ -661,6 +876,7 @@ int kf_server_create(kf_ctx *ctx, const kf_geometry *geom, const kf_server_param
         }
     }
     s->t_reset = Clock::now();
+    s->copies.start(3);
     s->worker = std::thread([s] { s->loop(); });
     *out = s;
     return KF_OK;
@@ -672,7 +888,7 @@ int kf_server_submit(kf_server *s, const kf_event *ev, const kf_event_result *re
     const auto t_submit = Clock::now();
     const int n = ev->n_tracks, L = ev->n_layers;
     if (n <= 0 || L < 4 || L > KF_MAX_SURFACES || !ev->surface || !ev->n_hits || !ev->x || !ev->y || !ev->z ||
-        !ev->seed_hits)
+        !ev->seed_hits || (ev->flags & ~KF_EVENT_ZERO_COPY))
         return KF_EINVAL;
     int64_t hb = 0;
     for (int l = 0; l < L; ++l) {
@@ -694,32 +910,64 @@ int kf_server_submit(kf_server *s, const kf_event *ev, const kf_event_result *re
     x.res = res ? *res : kf_event_result{};
     x.dev_bytes = s->event_bytes(n, L, hb);
     x.t_submit = t_submit;
-    const size_t stage_bytes = 4 * (3 * (size_t)hb + 9 * (size_t)n);
-    if (x.dev_bytes > s->p.mem_budget_bytes ||
-        stage_bytes + s->batch_host_bytes(n, L) > s->p.host_staging_bytes) {
+    x.x.assign(L, nullptr);
+    x.y.assign(L, nullptr);
+    x.z.assign(L, nullptr);
+    // results: written by the kernels into page-locked arrays; pageable arrays get
+    // them from staging (a GPU write into pageable memory faults every fresh page
+    // in through the host, which measured slower than a host copy)
+    {
+        const void *r[6] = {x.res.hit_idx, x.res.state, x.res.cov, x.res.chi2, x.res.ndof, x.res.status};
+        const void *v[6];
+        bool all = true;
+        for (int i = 0; i < 6; ++i) {
+            v[i] = pinned_view(r[i]);
+            all = all && (!r[i] || v[i]);
+        }
+        x.direct_out = all;
+        x.dres = kf_event_result{(int32_t *)v[0], (double *)v[1], (double *)v[2], (double *)v[3], (int32_t *)v[4],
+                                 (uint32_t *)v[5]};
+    }
+    // inputs: read in place (zero-copy) where the kernels can reach them, else staged
+    bool in_place = (ev->flags & KF_EVENT_ZERO_COPY) != 0;
+    if (in_place) {
+        x.seed_hits = static_cast<const float *>(device_view(s, ev->seed_hits));
+        in_place = x.seed_hits != nullptr;
+        for (int l = 3; l < L && in_place; ++l) {
+            if (ev->n_hits[l] == 0) continue;
+            x.x[l] = static_cast<const float *>(device_view(s, ev->x[l]));
+            x.y[l] = static_cast<const float *>(device_view(s, ev->y[l]));
+            x.z[l] = static_cast<const float *>(device_view(s, ev->z[l]));
+            in_place = x.x[l] && x.y[l] && x.z[l];
+        }
+    }
+    const size_t stage_bytes = in_place ? 0 : 4 * (3 * (size_t)hb + 9 * (size_t)n);
+    const size_t host_need = stage_bytes + s->batch_host_bytes(n, L);
+    if (x.dev_bytes > s->p.mem_budget_bytes || host_need > s->p.host_staging_bytes) {
         std::lock_guard<std::mutex> lk(s->mu);
         ++s->rejected;
         return KF_EBUSY;
     }
-    x.stage = static_cast<float *>(s->arena.alloc(stage_bytes));
-    if (!x.stage) return KF_EAGAIN;  // host staging full: retry after results come back
-    // stage the event: build-layer x, y, z, then the seed hits as three CSR arrays
-    float *px = x.stage, *py = px + hb, *pz = py + hb;
-    int64_t pos = 0;
-    for (int l = 3; l < L; ++l) {
-        const int m = ev->n_hits[l];
-        memcpy(px + pos, ev->x[l], 4 * (size_t)m);
-        memcpy(py + pos, ev->y[l], 4 * (size_t)m);
-        memcpy(pz + pos, ev->z[l], 4 * (size_t)m);
-        pos += m;
-    }
-    float *sx = x.stage + 3 * hb, *sy = sx + 3 * n, *sz = sy + 3 * n;
-    for (int t = 0; t < n; ++t)
-        for (int k = 0; k < 3; ++k) {
-            sx[3 * t + k] = ev->seed_hits[9 * t + 3 * k + 0];
-            sy[3 * t + k] = ev->seed_hits[9 * t + 3 * k + 1];
-            sz[3 * t + k] = ev->seed_hits[9 * t + 3 * k + 2];
+    if (!in_place) {
+        x.stage = static_cast<float *>(s->arena.alloc(stage_bytes));
+        if (!x.stage) return KF_EAGAIN;  // staging full: retry after earlier events complete
+        float *base = static_cast<float *>(const_cast<void *>(device_view(s, x.stage)));
+        if (!base) base = x.stage;  // the arena is page-locked: always reachable
+        float *px = x.stage, *py = px + hb, *pz = py + hb;
+        int64_t pos = 0;
+        for (int l = 3; l < L; ++l) {
+            const int m = ev->n_hits[l];
+            memcpy(px + pos, ev->x[l], 4 * (size_t)m);
+            memcpy(py + pos, ev->y[l], 4 * (size_t)m);
+            memcpy(pz + pos, ev->z[l], 4 * (size_t)m);
+            x.x[l] = base + pos;
+            x.y[l] = base + hb + pos;
+            x.z[l] = base + 2 * hb + pos;
+            pos += m;
         }
+        memcpy(x.stage + 3 * hb, ev->seed_hits, 36 * (size_t)n);
+        x.seed_hits = base + 3 * hb;
+    }
     const double sms = std::chrono::duration<double, std::milli>(Clock::now() - t_submit).count();
     std::lock_guard<std::mutex> lk(s->mu);
     s->stage_ms_sum += sms;

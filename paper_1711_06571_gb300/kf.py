@@ -25,6 +25,7 @@ KF_EAGAIN = -5
 KF_EBUSY = -6
 KF_ESIZE = -7
 KF_STATIC_MAX_HITS = 262144
+KF_EVENT_ZERO_COPY = 1
 
 KF_ST_NO_INTERSECT = 1
 KF_ST_CHOL_FAIL = 2
@@ -97,7 +98,8 @@ class kf_server_params(C.Structure):
 class kf_event(C.Structure):
     _fields_ = [("n_tracks", C.c_int32), ("n_layers", C.c_int32), ("surface", C.POINTER(C.c_int32)),
                 ("n_hits", C.POINTER(C.c_int32)), ("x", C.POINTER(C.c_void_p)), ("y", C.POINTER(C.c_void_p)),
-                ("z", C.POINTER(C.c_void_p)), ("seed_hits", C.c_void_p)]
+                ("z", C.POINTER(C.c_void_p)), ("seed_hits", C.c_void_p), ("flags", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 class kf_event_result(C.Structure):
@@ -411,11 +413,13 @@ def _np_ptr(a, dtype):
 
 
 def kf_server_submit(srv: Server, n_tracks, surfaces, x, y, z, seed_hits, hit_idx=None, state=None, cov=None,
-                     chi2=None, ndof=None, status=None):
+                     chi2=None, ndof=None, status=None, zero_copy=False):
     """Queue one event.  surfaces: list of geometry indices (first three = seed
     layers); x, y, z: per layer numpy float32 arrays (layers 0..2 may be None);
     seed_hits: float32 [n_tracks, 3, 3]; result arrays: numpy, shapes as in the
-    C header.  Returns (code, ticket): code KF_OK, KF_EBUSY or KF_EAGAIN."""
+    C header.  zero_copy: the input arrays stay alive and unchanged until the
+    ticket completes (the handle keeps references to them until it is reported).
+    Returns (code, ticket): code KF_OK, KF_EBUSY or KF_EAGAIN."""
     import numpy as np
     L = len(surfaces)
     sf = (C.c_int32 * L)(*[int(v) for v in surfaces])
@@ -425,13 +429,14 @@ def kf_server_submit(srv: Server, n_tracks, surfaces, x, y, z, seed_hits, hit_id
     zs = (C.c_void_p * L)(*[None if z[l] is None else _np_ptr(z[l], np.float32).value for l in range(L)])
     ev = kf_event(n_tracks=int(n_tracks), n_layers=L, surface=sf, n_hits=nh,
                   x=C.cast(xs, C.POINTER(C.c_void_p)), y=C.cast(ys, C.POINTER(C.c_void_p)),
-                  z=C.cast(zs, C.POINTER(C.c_void_p)), seed_hits=_np_ptr(seed_hits, np.float32))
+                  z=C.cast(zs, C.POINTER(C.c_void_p)), seed_hits=_np_ptr(seed_hits, np.float32),
+                  flags=KF_EVENT_ZERO_COPY if zero_copy else 0)
     res = kf_event_result(_np_ptr(hit_idx, np.int32), _np_ptr(state, np.float64), _np_ptr(cov, np.float64),
                           _np_ptr(chi2, np.float64), _np_ptr(ndof, np.int32), _np_ptr(status, np.uint32))
     t = C.c_uint64(0)
     rc = load().kf_server_submit(srv.ptr, C.byref(ev), C.byref(res), C.byref(t))
     if rc == KF_OK:
-        srv.results[t.value] = (hit_idx, state, cov, chi2, ndof, status)
+        srv.results[t.value] = (hit_idx, state, cov, chi2, ndof, status) + ((x, y, z, seed_hits) if zero_copy else ())
     elif rc == KF_EINVAL:
         raise KfError(rc, "kf_server_submit: malformed event")
     return rc, t.value

@@ -39,11 +39,13 @@ def _result_arrays(n, L):
                 chi2=np.zeros(n), ndof=np.zeros(n, np.int32), status=np.zeros(n, np.uint32))
 
 
-def submit(srv, ev):
+def submit(srv, ev, zero_copy=False, pinned_results=False):
     surf, xs, ys, zs, sh = _event_arrays(ev)
     n, L = ev["n"], len(surf)
     res = _result_arrays(n, L)
-    rc, t = kf.kf_server_submit(srv, n, surf, xs, ys, zs, sh, **res)
+    if pinned_results:  # page-locked result arrays
+        res = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in res.items()}
+    rc, t = kf.kf_server_submit(srv, n, surf, xs, ys, zs, sh, zero_copy=zero_copy, **res)
     return rc, t, res
 
 
@@ -95,10 +97,11 @@ def test_server_alone_and_mixed_match_direct_path(ctx, geom):
         assert_identical(res, exp[0], "alone")
     finally:
         kf.kf_server_destroy(srv)
-    # mixed: all four merged into one batch by the batch window
+    # mixed: all four merged into one batch by the batch window, with inputs read in
+    # place or staged and results in pageable or page-locked arrays
     srv = kf.kf_server_create(ctx, geom, kf.server_params(max_batch_events=16, batch_window_ms=2000))
     try:
-        subs = [submit(srv, ev) for ev in events]
+        subs = [submit(srv, ev, zero_copy=(i % 2 == 0), pinned_results=(i == 1)) for i, ev in enumerate(events)]
         assert all(rc == kf.KF_OK for rc, _, _ in subs)
         for (rc, t, res), e, i in zip(subs, exp, range(len(events))):
             rc, _ = kf.kf_server_wait(srv, t, 60000)
@@ -118,7 +121,7 @@ def test_server_many_events_overlapping_batches(ctx, geom):
     exp = [direct(ctx, geom, ev) for ev in events]
     srv = kf.kf_server_create(ctx, geom, kf.server_params(max_batches=3, max_batch_events=3))
     try:
-        subs = [submit(srv, ev) for ev in events]
+        subs = [submit(srv, ev, zero_copy=True) for ev in events]
         for (rc, t, res), e, i in zip(subs, exp, range(len(events))):
             assert rc == kf.KF_OK
             assert kf.kf_server_wait(srv, t, 60000)[0] == kf.KF_OK
