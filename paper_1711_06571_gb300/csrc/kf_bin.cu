@@ -18,12 +18,42 @@ namespace kfd {
 
 constexpr double PI_D = 3.14159265358979323846;
 
+// The keys are defined in FP64 with every operation rounded:
+//   u = ((atan2(y, x) + pi) * 1024) / (2 pi),   v = ((z + L) * 64) / (2 L).
+// A single-precision estimate decides floor() wherever it lies farther than
+// BIN_MARGIN from an integer: its error is below 3e-4 bin (atan2f within a few
+// ulp of 2^-22 rad, times 1024 / 2 pi = 163, plus the roundings of the sum and
+// the product), so the FP64 evaluation, which costs tens of FP64 instructions
+// on a GPU whose FP64 rate is 1/64 of FP32, runs only for the ~0.2% of hits
+// within BIN_MARGIN of a bin edge.  Either way the result is the FP64 one.
+constexpr float BIN_MARGIN = 1e-3f;
+constexpr float PI_F_BIN = 3.14159265358979323846f;
+constexpr float PHI_SCALE_F = (float)(1024.0 / (2.0 * PI_D));
+
+__device__ __forceinline__ bool bin_decided(float u)
+{
+    const float f = u - floorf(u);
+    return f > BIN_MARGIN && f < 1.f - BIN_MARGIN;
+}
+
 __device__ __forceinline__ int32_t bin_key(float x, float y, float z, double half_len)
 {
-    // ((atan2(y, x) + pi) * 1024) / (2 pi) and ((z + L) * 64) / (2 L), each op rounded
-    double u = __ddiv_rn(__dmul_rn(__dadd_rn(atan2((double)y, (double)x), PI_D), 1024.0), 2.0 * PI_D);
-    double v = __ddiv_rn(__dmul_rn(__dadd_rn((double)z, half_len), 64.0), __dmul_rn(2.0, half_len));
-    double fu = floor(u), fv = floor(v);
+    const float u32 = (atan2f(y, x) + PI_F_BIN) * PHI_SCALE_F;
+    const float hf = (float)half_len;
+    const float v32 = (z + hf) * (64.f / (2.f * hf));
+    double fu, fv;
+    if (bin_decided(u32)) {
+        fu = (double)floorf(u32);
+    } else {
+        const double u = __ddiv_rn(__dmul_rn(__dadd_rn(atan2((double)y, (double)x), PI_D), 1024.0), 2.0 * PI_D);
+        fu = floor(u);
+    }
+    if (bin_decided(v32)) {
+        fv = (double)floorf(v32);
+    } else {
+        const double v = __ddiv_rn(__dmul_rn(__dadd_rn((double)z, half_len), 64.0), __dmul_rn(2.0, half_len));
+        fv = floor(v);
+    }
     fu = fmin(fmax(fu, 0.0), (double)(KF_NPHI - 1));
     fv = fmin(fmax(fv, 0.0), (double)(KF_NZ - 1));
     return (int32_t)fv * KF_NPHI + (int32_t)fu;
@@ -40,49 +70,52 @@ __global__ void key_kernel(int n, const float *__restrict__ x, const float *__re
     atomicAdd(&counts[k], 1);
 }
 
-// inclusive scan of KF_NBINS counts in place (one block of 1024 threads, 64 per thread)
-__global__ void __launch_bounds__(1024) scan_kernel(int32_t *__restrict__ counts, int32_t *__restrict__ cursor)
+// Inclusive scan of the KF_NBINS counts in place by one block of 1024 threads;
+// counts[k] becomes offsets[k + 1] and cursor[k] = offsets[k].  Warp w owns the
+// contiguous range [w * 2048, (w + 1) * 2048) and reads it 32 entries at a time
+// (coalesced): a first pass sums it, the warp totals are scanned in shared
+// memory, a second pass scans the range with shuffles and a running carry.
+__device__ __forceinline__ void scan_bins_block(int32_t *__restrict__ counts, int32_t *__restrict__ cursor)
 {
     __shared__ int32_t warp_tot[32];
-    const int tid = threadIdx.x;
-    constexpr int PER = KF_NBINS / 1024;
-    int32_t loc[PER];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int PER_WARP = KF_NBINS / 32;
+    const int base = wid * PER_WARP;
     int32_t s = 0;
-    const int base = tid * PER;
+    for (int j = lane; j < PER_WARP; j += 32) s += counts[base + j];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        s += counts[base + j];
-        loc[j] = s;
-    }
-    // exclusive scan of per-thread sums across the block
-    int32_t v = s;
-    const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int32_t o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += o;
-    }
-    if (lane == 31) warp_tot[wid] = v;
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) warp_tot[wid] = s;
     __syncthreads();
     if (wid == 0) {
         int32_t w = warp_tot[lane];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            int32_t o = __shfl_up_sync(0xffffffffu, w, d);
+            const int32_t o = __shfl_up_sync(0xffffffffu, w, d);
             if (lane >= d) w += o;
         }
         warp_tot[lane] = w;
     }
     __syncthreads();
-    const int32_t excl = v - s + (wid > 0 ? warp_tot[wid - 1] : 0);
+    int32_t carry = wid > 0 ? warp_tot[wid - 1] : 0;
+    for (int j = 0; j < PER_WARP; j += 32) {
+        const int i = base + j + lane;
+        const int32_t c = counts[i];
+        int32_t v = c;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        // counts[k] becomes offsets[k + 1]; the cursor of bin k starts at offsets[k]
-        int32_t incl = excl + loc[j];
-        int32_t cnt = j == 0 ? loc[0] : loc[j] - loc[j - 1];
-        counts[base + j] = incl;
-        cursor[base + j] = incl - cnt;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t o = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += o;
+        }
+        counts[i] = carry + v;
+        cursor[i] = carry + v - c;
+        carry += __shfl_sync(0xffffffffu, v, 31);
     }
+}
+
+__global__ void __launch_bounds__(1024) scan_kernel(int32_t *__restrict__ counts, int32_t *__restrict__ cursor)
+{
+    scan_bins_block(counts, cursor);
 }
 
 __global__ void scatter_hits_kernel(int n, const int32_t *__restrict__ key, int32_t *__restrict__ cursor,
@@ -171,47 +204,8 @@ __global__ void seg_key_kernel(int H, int nseg, const int32_t *__restrict__ seg_
 
 __global__ void __launch_bounds__(1024) seg_scan_kernel(int32_t *__restrict__ offsets, int32_t *__restrict__ cursor)
 {
-    // one block per segment: the body of scan_kernel on that segment's counts
-    int32_t *counts = offsets + (size_t)blockIdx.x * (KF_NBINS + 1) + 1;
-    int32_t *cur = cursor + (size_t)blockIdx.x * KF_NBINS;
-    __shared__ int32_t warp_tot[32];
-    const int tid = threadIdx.x;
-    constexpr int PER = KF_NBINS / 1024;
-    int32_t loc[PER];
-    int32_t s = 0;
-    const int base = tid * PER;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        s += counts[base + j];
-        loc[j] = s;
-    }
-    int32_t v = s;
-    const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int32_t o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += o;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int32_t w = warp_tot[lane];
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            int32_t o = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += o;
-        }
-        warp_tot[lane] = w;
-    }
-    __syncthreads();
-    const int32_t excl = v - s + (wid > 0 ? warp_tot[wid - 1] : 0);
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        int32_t incl = excl + loc[j];
-        int32_t cnt = j == 0 ? loc[0] : loc[j] - loc[j - 1];
-        counts[base + j] = incl;
-        cur[base + j] = incl - cnt;
-    }
+    // one block per segment: the scan of scan_kernel on that segment's counts
+    scan_bins_block(offsets + (size_t)blockIdx.x * (KF_NBINS + 1) + 1, cursor + (size_t)blockIdx.x * KF_NBINS);
 }
 
 __global__ void seg_scatter_kernel(int H, int nseg, const int32_t *__restrict__ seg_off,

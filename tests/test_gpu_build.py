@@ -85,6 +85,28 @@ def test_binning_edge_cases(ctx, oracle_mod):
         np.testing.assert_array_equal(pg, po)
 
 
+def test_binning_at_bin_edges(ctx, oracle_mod):
+    """Hits placed on and next to phi and z bin edges (where a single-precision
+    estimate of the key cannot decide and the FP64 evaluation takes over): keys
+    and order equal the oracle's."""
+    half = 36.4
+    rng = np.random.default_rng(11)
+    k = rng.integers(0, 1024, 3000)
+    d = rng.choice([0.0, 1e-9, -1e-9, 1e-7, -1e-7, 3e-6, -3e-6, 2e-5, -2e-5, 1e-4, -1e-4, 4e-3, -4e-3], 3000)
+    phi = -np.pi + 2 * np.pi * (k + d) / 1024.0
+    r = rng.uniform(4.0, 100.0, 3000)
+    kz = rng.integers(0, 65, 3000)
+    dz = rng.choice([0.0, 1e-6, -1e-6, 1e-4, -1e-4, 2e-3, -2e-3], 3000)
+    z = (-half + 2 * half * (kz + dz) / 64.0)
+    x, y = (r * np.cos(phi)).astype(np.float32), (r * np.sin(phi)).astype(np.float32)
+    z = z.astype(np.float32)
+    pg, og, _ = _bin_gpu(ctx, x, y, z, half)
+    po, oo = oracle_mod.bin_layer(x, y, z, half)
+    if not np.array_equal(og, oo) or not np.array_equal(pg, po):
+        # only an atan2 ulp at an exact phi edge may differ between libraries
+        assert _edge_allowed(oracle_mod, x, y, z, half, pg, po)
+
+
 def test_batched_binning_equals_per_layer(ctx, oracle_mod):
     """kf_bin_hits_batched over every layer of two events plus the edge cases
     (empty segments included) gives, per segment, exactly the per-layer call's
