@@ -192,8 +192,14 @@ __device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], 
     score_own(st, pw, sf, ly, w, shared, fs, a.max_cand, best, bchi, bhit, o.capped);
     if (best >= 0 && bchi < (double)a.chi2_cut) {
         bool ok;
-        if constexpr (JOSEPH) ok = kf_update<true>(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
-        else ok = kf_update_mixed(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
+        if constexpr (JOSEPH) {
+            ok = kf_update<true>(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
+        } else if constexpr (sizeof(C) == 4) {  // mixed path: reuse the window's S factor
+            ok = shared ? kf_update_mixed_factored(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2, fs, bchi)
+                        : kf_update_mixed(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
+        } else {
+            ok = kf_update_mixed(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
+        }
         if (ok) {
             o.chosen = best;
         } else {
@@ -531,7 +537,10 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
             float4 bhit = make_float4(0.f, 0.f, 0.f, 0.f);
             score_coop(st, do_step, w, fs, ly, a.max_cand, best, bchi, bhit, so.capped);
             if (do_step && best >= 0 && bchi < (double)a.chi2_cut) {
-                if (kf_update_mixed(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2)) {
+                bool ok;
+                if constexpr (sizeof(C) == 4) ok = kf_update_mixed_factored(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2, fs, bchi);
+                else ok = kf_update_mixed(st, pc, bhit.x, bhit.y, bhit.z, sf, chi2);
+                if (ok) {
                     so.chosen = best;
                 } else {
                     status |= KF_ST_CHOL_FAIL;

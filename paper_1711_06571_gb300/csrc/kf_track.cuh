@@ -344,18 +344,12 @@ __device__ __forceinline__ void add_inc(float &a, float d) { a += d; }
 //                   as P - K G^T + (K S - G) K^T with G = P H^T; stays positive
 //                   definite under the 1e4 seed covariance)
 // C is the covariance type; returns false if S is not positive definite.
-template <bool JOSEPH, class C, class T, class Pp>
-__device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, float hy, float hz, const Surf &sf,
-                                          double &chi2)
+// The gain and the state and covariance update of kf_update, given the LDL^T
+// factor f of S (entries s11..s33) and the residual r.
+template <bool JOSEPH, class C, class T, class Pp, class R>
+__device__ __forceinline__ void kf_apply_gain(Track<T, Pp> &st, C p[21], R r0, R r1, R r2, const Ldl3 &f, C s11,
+                                              C s21, C s22, C s31, C s32, C s33)
 {
-    const auto r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);  // float or double
-    C rxx, rxy, ryy, rzz;
-    meas_cov<C>(sf, hx, hy, rxx, rxy, ryy, rzz);
-    C s11 = p[pk(0, 0)] + rxx, s21 = p[pk(1, 0)] + rxy, s22 = p[pk(1, 1)] + ryy;
-    C s31 = p[pk(2, 0)], s32 = p[pk(2, 1)], s33 = p[pk(2, 2)] + rzz;
-    Ldl3 f;
-    if (!ldl3(wide(s11), wide(s21), wide(s22), wide(s31), wide(s32), wide(s33), f)) return false;
-    chi2 += ldl3_chi2(f, wide(r0), wide(r1), wide(r2));
     C a11, a21, a22, a31, a32, a33;
     ldl3_inverse<C>(f, a11, a21, a22, a31, a32, a33);
     C G[6][3], K[6][3];
@@ -399,6 +393,21 @@ __device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, f
             for (int j = 0; j <= i; ++j)
                 p[pk(i, j)] -= K[i][0] * G[j][0] + K[i][1] * G[j][1] + K[i][2] * G[j][2];
     }
+}
+
+template <bool JOSEPH, class C, class T, class Pp>
+__device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, float hy, float hz, const Surf &sf,
+                                          double &chi2)
+{
+    const auto r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);  // float or double
+    C rxx, rxy, ryy, rzz;
+    meas_cov<C>(sf, hx, hy, rxx, rxy, ryy, rzz);
+    C s11 = p[pk(0, 0)] + rxx, s21 = p[pk(1, 0)] + rxy, s22 = p[pk(1, 1)] + ryy;
+    C s31 = p[pk(2, 0)], s32 = p[pk(2, 1)], s33 = p[pk(2, 2)] + rzz;
+    Ldl3 f;
+    if (!ldl3(wide(s11), wide(s21), wide(s22), wide(s31), wide(s32), wide(s33), f)) return false;
+    chi2 += ldl3_chi2(f, wide(r0), wide(r1), wide(r2));
+    kf_apply_gain<JOSEPH>(st, p, r0, r1, r2, f, s11, s21, s22, s31, s32, s33);
     return true;
 }
 
@@ -477,6 +486,27 @@ __device__ __forceinline__ bool kf_update_mixed(Track<double, Pp> &st, double p[
                                                 const Surf &sf, double &chi2)
 {
     return kf_update<false>(st, p, hx, hy, hz, sf, chi2);
+}
+
+// kf_update_mixed for a hit whose S the caller has already factored (f, from the
+// same FP32 sums kf_update would form) and whose chi2 it has computed (c2): the
+// standard-form update without a second factorisation.  Strongly informative
+// updates still take the FP64 Joseph path.
+template <class Pp>
+__device__ __forceinline__ bool kf_update_mixed_factored(Track<float, Pp> &st, float p[21], float hx, float hy,
+                                                         float hz, const Surf &sf, double &chi2, const Ldl3 &f,
+                                                         double c2)
+{
+    float rxx, rxy, ryy, rzz;
+    meas_cov<float>(sf, hx, hy, rxx, rxy, ryy, rzz);
+    const bool informative = p[pk(0, 0)] > UPDATE_FP64_RATIO * rxx || p[pk(1, 1)] > UPDATE_FP64_RATIO * ryy ||
+                             p[pk(2, 2)] > UPDATE_FP64_RATIO * rzz;
+    if (informative) return kf_update_mixed(st, p, hx, hy, hz, sf, chi2);
+    const float r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);
+    chi2 += c2;
+    kf_apply_gain<false>(st, p, r0, r1, r2, f, p[pk(0, 0)] + rxx, p[pk(1, 0)] + rxy, p[pk(1, 1)] + ryy, p[pk(2, 0)],
+                         p[pk(2, 1)], p[pk(2, 2)] + rzz);
+    return true;
 }
 
 // The first update, at the seed: the prior is seed_cov * I plus scattering
