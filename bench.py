@@ -241,11 +241,34 @@ def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000):
     t_step = float(np.mean([a.elapsed_time(c) for a, _, c in evs]))
     units = n * (L - 3)  # track-layer build steps per launch
     found = float((idx[3:] >= 0).float().mean().item())
+    where = np.concatenate([ev["truth_where"][:, 3:] for ev in events])
+    has = where >= 0
+    eff_best = float(np.mean(idx[3:].t().cpu().numpy()[has] == where[has]))
+
+    # combinatorial building of the same seeds: n_slots candidates per seed
+    ckf = {}
+    for ns in (2, 4, 8):
+        def ckf_launch():
+            kf.kf_build_ckf(ctx, g, fp, bp, ns, n_events, L, layers, eoff, seed_st, seed_q, sh9, idx,
+                            out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+        for _ in range(warmup):
+            ckf_launch()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(steps):
+            ckf_launch()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1) / steps
+        eff = float(np.mean(idx[3:].t().cpu().numpy()[has] == where[has]))
+        ckf[f"{ns}_slots"] = dict(build_launch_ms=ms, candidate_steps_per_s=units * ns / (ms * 1e-3),
+                                  seed_steps_per_s=units / (ms * 1e-3), true_hit_efficiency=eff)
     return dict(workload=BUILD_WORKLOAD, value=units / (t_step * 1e-3), unit="track-layer build steps/s",
                 ms_per_step=t_step, bin_and_seed_ms=t_bin, build_launch_ms=t_build,
                 build_kernel_steps_per_s=units / (t_build * 1e-3), hits_binned=H, tracks=n,
-                steps_measured=steps, fraction_of_steps_with_a_hit=found,
-                gpu_launches_per_step=5 + 1 + 4)
+                steps_measured=steps, fraction_of_steps_with_a_hit=found, true_hit_efficiency=eff_best,
+                gpu_launches_per_step=5 + 1 + 4, combinatorial=ckf)
 
 
 UNEVEN_WORKLOAD = ("KF fit of 2,000,000 tracks, |eta| < 2.5, 17 barrel cylinders + 2 x 12 end-cap disks at "

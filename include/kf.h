@@ -308,6 +308,28 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
                      const kf_seeds *seeds, const float *seed_hits, int32_t *hit_idx_out, const kf_tracks_out *out,
                      void *stream);
 
+/* Combinatorial track building (Sec. 2: building branches to explore several
+ * candidates per seed; Sec. 4.3: a fixed number of candidate slots per seed,
+ * the best candidates kept).  Each seed keeps at most n_slots candidates
+ * (1, 2, 4 or 8), ranked.  After the seed fit, on every later layer each
+ * candidate is propagated and scattered and its window searched as in
+ * kf_build_besthit; its children are the candidate updated with each window
+ * hit whose chi2 is below chi2_cut, and the candidate without a hit on this
+ * layer (a candidate that cannot reach the layer stops and is carried
+ * unchanged).  All children of a seed are ranked -- more hits first, then
+ * smaller total chi2, then the lower rank of the parent, then the lower hit
+ * index, a child without a hit after its parent's hits -- and the first
+ * n_slots are kept.  After the last layer the first candidate is the track:
+ * its hit per layer goes to hit_idx_out and its state to out.  With
+ * n_slots = 1 this is best-hit building.  Mixed precision only
+ * (fit->precision = KF_PREC_MIXED); other arguments as kf_build_besthit.
+ * Scratch: about (140 + 5 * n_layers * n_slots) bytes per seed, in the
+ * context's workspace. */
+int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit, const kf_build_params *bp,
+                 int32_t n_slots, int32_t n_events, int32_t n_layers, const kf_binned_layer *layers,
+                 const int32_t *event_offsets, const kf_seeds *seeds, const float *seed_hits, int32_t *hit_idx_out,
+                 const kf_tracks_out *out, void *stream);
+
 /* Gather the hits a build chose into fit input (for the final fit, Sec. 2):
  * for each track, its three seed hits then every layer with hit_idx >= 0, in
  * layer order.  offsets_out: device [n+1]; layer_out, x_out, y_out, z_out:

@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the batched Kalman-filter track fit and best-hit build.
+"""FP64 CPU oracle for the batched Kalman-filter track fit, best-hit and combinatorial build.
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``; never by the product path.  The
@@ -75,6 +75,13 @@ class StepRec(C.Structure):
                 ("n_cand", C.c_int32), ("capped", C.c_int32), ("best", C.c_int32), ("status", C.c_int32)]
 
 
+class CkfCfg(C.Structure):
+    _fields_ = [("nsigma", C.c_double), ("chi2_cut", C.c_double), ("max_cand", C.c_int32), ("n_slots", C.c_int32)]
+
+
+CKF_MARGIN_DTYPE = np.dtype([("rank_gap", "<f8"), ("cut_gap", "<f8"), ("edge_gap", "<f8"), ("capped", "<i4"),
+                             ("n_kept_last", "<i4")])
+
 STEP_DTYPE = np.dtype([("pred", "<f8", (6,)), ("chi2_best", "<f8"), ("chi2_second", "<f8"),
                        ("phi_lo", "<i4"), ("phi_n", "<i4"), ("z_lo", "<i4"), ("z_hi", "<i4"),
                        ("n_cand", "<i4"), ("capped", "<i4"), ("best", "<i4"), ("status", "<i4")])
@@ -136,6 +143,10 @@ def lib():
             L.or_build_tracks.argtypes = [C.POINTER(FitCfg), C.POINTER(BuildCfg), C.POINTER(Surf), C.c_int,
                                           C.POINTER(Layer), C.c_int, C.c_int, _F, _I32, _I32, _D, _D, _D, _I32,
                                           _U32, C.c_void_p]
+            L.or_ckf_tracks.restype = None
+            L.or_ckf_tracks.argtypes = [C.POINTER(FitCfg), C.POINTER(CkfCfg), C.POINTER(Surf), C.c_int,
+                                        C.POINTER(Layer), C.c_int, C.c_int, _F, _I32, _I32, _D, _D, _D, _I32,
+                                        _U32, C.c_void_p]
             _lib = L
     return _lib
 
@@ -375,4 +386,54 @@ def build_besthit(geom, event, nsigma=3.0, chi2_cut=30.0, max_cand=32, seed_cov=
     _run_ranges(run, t0, t1, threads)
     if record:
         out["rec"] = rec
+    return out
+
+
+def _layers_array(event):
+    lays = event["layers"]
+    keep = []
+    larr = (Layer * len(lays))()
+    for i, ly in enumerate(lays):
+        arrs = [np.ascontiguousarray(ly[k], dtype=np.float32) for k in ("x", "y", "z")]
+        perm = np.ascontiguousarray(ly["perm"], dtype=np.int32) if ly.get("perm") is not None else None
+        offs = np.ascontiguousarray(ly["offsets"], dtype=np.int32) if ly.get("offsets") is not None else None
+        keep += arrs + [perm, offs]
+        larr[i].n = len(arrs[0])
+        larr[i].surf = int(ly["surf"])
+        larr[i].x = _p(arrs[0], C.c_float)
+        larr[i].y = _p(arrs[1], C.c_float)
+        larr[i].z = _p(arrs[2], C.c_float)
+        larr[i].perm = _p(perm, C.c_int32) if perm is not None else None
+        larr[i].offsets = _p(offs, C.c_int32) if offs is not None else None
+    return larr, keep
+
+
+def build_ckf(geom, event, n_slots=4, nsigma=3.0, chi2_cut=30.0, max_cand=32, seed_cov=1e4, ms_on=True, t0=0,
+              t1=None, threads=1):
+    """Combinatorial building of one event (n_slots candidates per seed); event as build_besthit.
+    Returns idx (n, nlay), state, cov, chi2, ndof, status and margin (n, CKF_MARGIN_DTYPE)."""
+    fc = fit_cfg(geom, seed_cov, ms_on)
+    cc = CkfCfg(nsigma=float(nsigma), chi2_cut=float(chi2_cut), max_cand=int(min(max_cand, 1024)),
+                n_slots=int(n_slots))
+    sarr = surfaces(geom)
+    larr, keep = _layers_array(event)
+    nlay = len(event["layers"])
+    sh = np.ascontiguousarray(event["seed_hits"], dtype=np.float32).reshape(-1, 9)
+    si = np.ascontiguousarray(event["seed_idx"], dtype=np.int32).reshape(-1, 3)
+    n = sh.shape[0]
+    if t1 is None:
+        t1 = n
+    out = dict(idx=np.full((n, nlay), -1, np.int32), state=np.zeros((n, 6)), cov=np.zeros((n, 6, 6)),
+               chi2=np.zeros(n), ndof=np.zeros(n, np.int32), status=np.zeros(n, np.uint32),
+               margin=np.zeros(n, CKF_MARGIN_DTYPE))
+    L = lib()
+
+    def run(a, b):
+        L.or_ckf_tracks(C.byref(fc), C.byref(cc), sarr, nlay, larr, int(a), int(b), _p(sh, C.c_float),
+                        _p(si, C.c_int32), _p(out["idx"], C.c_int32), _p(out["state"], C.c_double),
+                        _p(out["cov"], C.c_double), _p(out["chi2"], C.c_double), _p(out["ndof"], C.c_int32),
+                        _p(out["status"], C.c_uint32), out["margin"].ctypes.data)
+
+    _run_ranges(run, t0, t1, threads)
+    del keep
     return out

@@ -938,3 +938,321 @@ void or_build_tracks(const or_fit_cfg *fc, const or_build_cfg *bc, const or_surf
         ndof[t] = nd;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* combinatorial building (Sec. 2: building branches to explore several */
+/* candidates per seed after finding compatible hits on a layer; Sec.   */
+/* 4.3: a fixed number of candidate slots per seed, the best kept)      */
+/* ------------------------------------------------------------------ */
+/*
+ * Reading.  Each seed keeps at most n_slots candidates, ranked.  On every
+ * build layer each candidate is propagated and scattered as in best-hit
+ * building, its window (the same one) is searched, and it has children:
+ * one per window hit with chi2 below the cut (the candidate updated with
+ * that hit), and one without a hit on this layer (a hole: the predicted
+ * state).  A candidate that cannot reach the layer stops and is carried
+ * unchanged.  All children of the seed are ranked -- more hits first, then
+ * smaller total chi2, then the lower rank of the parent, then the lower hit
+ * index (a hole after the hits of its parent) -- and the first n_slots are
+ * kept, in that order.  After the last layer the first candidate is the
+ * track.  With n_slots = 1 this is best-hit building.
+ */
+
+typedef struct {
+    double nsigma;
+    double chi2_cut;
+    int32_t max_cand; /* window hits scored per candidate */
+    int32_t n_slots;  /* candidates kept per seed */
+} or_ckf_cfg;
+
+/* How close one seed came to a different decision, for the tests: the
+ * smallest relative chi2 gap between two children of equal hit count where the
+ * order decided something (the last kept against the first dropped on every
+ * layer, the first against the second on the last layer), the smallest
+ * relative distance of a scored hit's chi2 to the cut, and the smallest
+ * distance (in bins) of a window edge to a bin boundary. */
+typedef struct {
+    double rank_gap;
+    double cut_gap;
+    double edge_gap;
+    int32_t capped;
+    int32_t n_kept_last; /* candidates alive after the last layer */
+} or_ckf_margin;
+
+typedef struct {
+    double st[6], P[36];
+    double chi2;
+    int32_t nh, nu, stopped;
+    uint32_t status;
+} or_cand;
+
+typedef struct {
+    double chi2; /* total chi2 of the child */
+    int32_t nh;
+    int32_t parent;
+    int32_t hit;  /* original hit index, -1: hole or stopped */
+    int32_t pad_;
+    uint32_t status;
+} or_child;
+
+/* 1 when child a ranks before child b */
+static int child_before(const or_child *a, const or_child *b)
+{
+    long long ha = a->hit < 0 ? 0x7fffffffLL : a->hit, hb = b->hit < 0 ? 0x7fffffffLL : b->hit;
+    if (a->nh != b->nh) return a->nh > b->nh;
+    if (a->chi2 != b->chi2) return a->chi2 < b->chi2;
+    if (a->parent != b->parent) return a->parent < b->parent;
+    return ha < hb;
+}
+
+static void rank_gap_update(or_ckf_margin *mg, const or_child *a, const or_child *b)
+{
+    double den, g;
+    if (a->nh != b->nh) return;
+    den = fabs(b->chi2) > 1e-300 ? fabs(b->chi2) : 1e-300;
+    g = (b->chi2 - a->chi2) / den;
+    if (g < mg->rank_gap) mg->rank_gap = g;
+}
+
+static double edge_dist(double u)
+{
+    double f = u - floor(u);
+    return f < 1.0 - f ? f : 1.0 - f;
+}
+
+/* Combinatorial building of one seed.  Arguments as or_build_one; idx gets
+ * the chosen hit per layer of the best candidate; margin may be NULL. */
+unsigned or_ckf_one(const or_fit_cfg *fc, const or_ckf_cfg *cc, const or_surf *surfs, int nlay, const or_layer *lays,
+                    const float seed_hits[9], const int32_t seed_idx[3], int32_t *idx, double st_out[6],
+                    double P_out[36], double *chi2_out, int *ndof, or_ckf_margin *margin)
+{
+    const int C = cc->n_slots;
+    double h1[3], h2[3], h3[3], seed[6];
+    uint8_t lyr[3];
+    float sx[3], sy[3], sz[3];
+    int q, nu = 0, L, i, nc = 1;
+    unsigned status;
+    or_cand *cands, *next, *pred;
+    or_child *kids;
+    int32_t *bp_parent, *bp_hit;
+    int max_kids;
+    or_ckf_margin mg = {1e300, 1e300, 1e300, 0, 0};
+    for (i = 0; i < 3; ++i) {
+        sx[i] = seed_hits[i * 3 + 0];
+        sy[i] = seed_hits[i * 3 + 1];
+        sz[i] = seed_hits[i * 3 + 2];
+        lyr[i] = (uint8_t)lays[i].surf;
+    }
+    h1[0] = sx[0]; h1[1] = sy[0]; h1[2] = sz[0];
+    h2[0] = sx[1]; h2[1] = sy[1]; h2[2] = sz[1];
+    h3[0] = sx[2]; h3[1] = sy[2]; h3[2] = sz[2];
+    or_seed(h1, h2, h3, fc->bz, seed, &q);
+    for (i = 0; i < 3; ++i) idx[i] = seed_idx[i];
+    for (L = 3; L < nlay; ++L) idx[L] = -1;
+    cands = (or_cand *)calloc((size_t)C, sizeof(or_cand));
+    next = (or_cand *)calloc((size_t)C, sizeof(or_cand));
+    pred = (or_cand *)calloc((size_t)C, sizeof(or_cand));
+    max_kids = C * (cc->max_cand + 1);
+    kids = (or_child *)calloc((size_t)max_kids, sizeof(or_child));
+    bp_parent = (int32_t *)calloc((size_t)nlay * C, sizeof(int32_t));
+    bp_hit = (int32_t *)calloc((size_t)nlay * C, sizeof(int32_t));
+    status = or_fit_one(fc, surfs, 3, lyr, sx, sy, sz, seed, q, NULL, cands[0].st, cands[0].P, &cands[0].chi2, ndof,
+                        &nu, NULL);
+    cands[0].nh = 3;
+    cands[0].nu = nu;
+    cands[0].status = status;
+    if (status & (OR_ST_NO_INTERSECT | OR_ST_CHOL_FAIL | OR_ST_NONFINITE)) {
+        memcpy(st_out, cands[0].st, 6 * sizeof(double));
+        memcpy(P_out, cands[0].P, 36 * sizeof(double));
+        *chi2_out = cands[0].chi2;
+        goto done;
+    }
+    for (L = 3; L < nlay; ++L) {
+        const or_layer *ly = &lays[L];
+        const or_surf *sf = &surfs[ly->surf];
+        const double R = sf->pos, Lz = sf->half_or_rin;
+        int nk = 0, r, k, keep;
+        for (r = 0; r < nc; ++r) {
+            or_cand *c = &cands[r];
+            or_cand *pr = &pred[r];
+            double nx[6], J[36], xp, yp, r2, phip, sphi2, dphi, dz, ulo, uhi, vlo, vhi;
+            int32_t cand[1024];
+            int phi_lo, phi_hi, nphi, z_lo, z_hi, zb, ncand = 0, capped = 0, prc;
+            unsigned step = 0;
+            *pr = *c;
+            if (c->stopped) { /* carried unchanged */
+                or_child *kd = &kids[nk++];
+                kd->chi2 = c->chi2;
+                kd->nh = c->nh;
+                kd->parent = r;
+                kd->hit = -1;
+                kd->status = 0;
+                continue;
+            }
+            prc = or_propagate(c->st, q, fc->bz, sf, nx, J);
+            if (prc) {
+                or_child *kd = &kids[nk++];
+                pr->stopped = 1;
+                kd->chi2 = c->chi2;
+                kd->nh = c->nh;
+                kd->parent = r;
+                kd->hit = -1;
+                kd->status = (unsigned)prc;
+                continue;
+            }
+            memcpy(pr->st, nx, sizeof nx);
+            or_transport(J, pr->P);
+            if (fc->ms_on) step |= (unsigned)or_ms_noise(pr->st, fc->mass, sf, pr->P);
+            /* window, as in best-hit building */
+            xp = pr->st[0];
+            yp = pr->st[1];
+            r2 = xp * xp + yp * yp;
+            phip = atan2(yp, xp);
+            sphi2 = (yp * yp * pr->P[0 * 6 + 0] + xp * xp * pr->P[1 * 6 + 1] - 2.0 * xp * yp * pr->P[0 * 6 + 1]) /
+                    (r2 * r2);
+            dphi = cc->nsigma * sqrt(sphi2 + (sf->sig_rphi / R) * (sf->sig_rphi / R));
+            dz = cc->nsigma * sqrt(pr->P[2 * 6 + 2] + sf->sig_3 * sf->sig_3);
+            ulo = ((phip - dphi + OR_PI) * 1024.0) / (2.0 * OR_PI);
+            uhi = ((phip + dphi + OR_PI) * 1024.0) / (2.0 * OR_PI);
+            vlo = ((pr->st[2] - dz + Lz) * 64.0) / (2.0 * Lz);
+            vhi = ((pr->st[2] + dz + Lz) * 64.0) / (2.0 * Lz);
+            phi_lo = (int)floor(ulo);
+            phi_hi = (int)floor(uhi);
+            nphi = phi_hi - phi_lo + 1;
+            if (nphi > OR_NPHI) nphi = OR_NPHI;
+            z_lo = floor_clamp(vlo, 0, OR_NZ - 1);
+            z_hi = floor_clamp(vhi, 0, OR_NZ - 1);
+            if (edge_dist(ulo) < mg.edge_gap) mg.edge_gap = edge_dist(ulo);
+            if (edge_dist(uhi) < mg.edge_gap) mg.edge_gap = edge_dist(uhi);
+            if (vlo > 0.0 && vlo < OR_NZ && edge_dist(vlo) < mg.edge_gap) mg.edge_gap = edge_dist(vlo);
+            if (vhi > 0.0 && vhi < OR_NZ && edge_dist(vhi) < mg.edge_gap) mg.edge_gap = edge_dist(vhi);
+            for (zb = z_lo; zb <= z_hi && !capped; ++zb) {
+                for (k = 0; k < nphi && !capped; ++k) {
+                    int pb = ((phi_lo + k) % OR_NPHI + OR_NPHI) % OR_NPHI;
+                    int key = zb * OR_NPHI + pb, j;
+                    for (j = ly->offsets[key]; j < ly->offsets[key + 1]; ++j) {
+                        if (ncand >= cc->max_cand) {
+                            capped = 1;
+                            break;
+                        }
+                        cand[ncand++] = ly->perm[j];
+                    }
+                }
+            }
+            if (capped) {
+                step |= OR_ST_CAND_CAPPED;
+                mg.capped = 1;
+            }
+            pr->status = c->status | step;
+            for (k = 0; k < ncand; ++k) {
+                int h = cand[k], a, b;
+                double hit[3] = {(double)ly->x[h], (double)ly->y[h], (double)ly->z[h]};
+                double Rm[9], S[9], rr[3], c2 = -1.0;
+                or_meas_cov(sf, hit, Rm);
+                for (a = 0; a < 3; ++a) {
+                    rr[a] = hit[a] - pr->st[a];
+                    for (b = 0; b < 3; ++b) S[a * 3 + b] = pr->P[a * 6 + b] + Rm[a * 3 + b];
+                }
+                if (or_chi2(S, rr, &c2)) continue;
+                if (fabs(c2 - cc->chi2_cut) / cc->chi2_cut < mg.cut_gap) mg.cut_gap = fabs(c2 - cc->chi2_cut) / cc->chi2_cut;
+                if (c2 < cc->chi2_cut) {
+                    or_child *kd = &kids[nk++];
+                    kd->chi2 = c->chi2 + c2;
+                    kd->nh = c->nh + 1;
+                    kd->parent = r;
+                    kd->hit = h;
+                    kd->status = step;
+                }
+            }
+            {
+                or_child *kd = &kids[nk++];
+                kd->chi2 = c->chi2;
+                kd->nh = c->nh;
+                kd->parent = r;
+                kd->hit = -1;
+                kd->status = step;
+            }
+        }
+        /* rank all children (insertion sort: short lists) */
+        for (k = 1; k < nk; ++k) {
+            or_child t = kids[k];
+            int j = k - 1;
+            while (j >= 0 && child_before(&t, &kids[j])) {
+                kids[j + 1] = kids[j];
+                --j;
+            }
+            kids[j + 1] = t;
+        }
+        keep = nk < C ? nk : C;
+        /* decisions that matter: who is kept (the last kept against the first
+         * dropped) and, on the last layer, which candidate is the track */
+        if (nk > keep) rank_gap_update(&mg, &kids[keep - 1], &kids[keep]);
+        if (L == nlay - 1 && keep > 1) rank_gap_update(&mg, &kids[0], &kids[1]);
+        /* the kept children become the candidates */
+        for (k = 0; k < keep; ++k) {
+            const or_child *kd = &kids[k];
+            const or_cand *pr = &pred[kd->parent];
+            or_cand *nw = &next[k];
+            *nw = *pr;
+            nw->status = pr->status | kd->status;
+            if (kd->status & OR_ST_NO_INTERSECT) nw->stopped = 1;
+            if (kd->hit >= 0) {
+                double hit[3] = {(double)ly->x[kd->hit], (double)ly->y[kd->hit], (double)ly->z[kd->hit]};
+                double Rm[9], c2 = 0.0;
+                or_meas_cov(sf, hit, Rm);
+                if (or_update(nw->st, nw->P, hit, Rm, &c2)) {
+                    /* cannot happen: S was factored when the hit was scored */
+                    nw->status |= OR_ST_CHOL_FAIL;
+                }
+                nw->chi2 = kd->chi2;
+                nw->nh = kd->nh;
+                nw->nu += 1;
+            }
+            bp_parent[L * C + k] = kd->parent;
+            bp_hit[L * C + k] = kd->hit;
+        }
+        nc = keep;
+        memcpy(cands, next, (size_t)keep * sizeof(or_cand));
+    }
+    /* the first candidate is the track; its hits by walking the back pointers */
+    {
+        int s = 0;
+        for (L = nlay - 1; L >= 3; --L) {
+            idx[L] = bp_hit[L * C + s];
+            s = bp_parent[L * C + s];
+        }
+    }
+    memcpy(st_out, cands[0].st, 6 * sizeof(double));
+    memcpy(P_out, cands[0].P, 36 * sizeof(double));
+    *chi2_out = cands[0].chi2;
+    status = cands[0].status;
+    nu = cands[0].nu;
+    *ndof = 2 * nu - 5;
+    mg.n_kept_last = nc;
+done:
+    for (i = 0; i < 6; ++i)
+        if (!isfinite(st_out[i])) status |= OR_ST_NONFINITE;
+    if (margin) *margin = mg;
+    free(cands);
+    free(next);
+    free(pred);
+    free(kids);
+    free(bp_parent);
+    free(bp_hit);
+    return status;
+}
+
+/* Combinatorial building of tracks [t0, t1) of one event; arrays as
+ * or_build_tracks, margin (n) may be NULL. */
+void or_ckf_tracks(const or_fit_cfg *fc, const or_ckf_cfg *cc, const or_surf *surfs, int nlay, const or_layer *lays,
+                   int t0, int t1, const float *seed_hits, const int32_t *seed_idx, int32_t *idx, double *state,
+                   double *cov, double *chi2, int32_t *ndof, uint32_t *status, or_ckf_margin *margin)
+{
+    int t;
+    for (t = t0; t < t1; ++t) {
+        int nd = 0;
+        status[t] = or_ckf_one(fc, cc, surfs, nlay, lays, &seed_hits[t * 9], &seed_idx[t * 3], &idx[t * nlay],
+                               &state[t * 6], &cov[t * 36], &chi2[t], &nd, margin ? &margin[t] : NULL);
+        ndof[t] = nd;
+    }
+}

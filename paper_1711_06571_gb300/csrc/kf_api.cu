@@ -797,6 +797,82 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "build kernel");
 }
 
+int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit, const kf_build_params *bp,
+                 int32_t n_slots, int32_t n_events, int32_t n_layers, const kf_binned_layer *layers,
+                 const int32_t *event_offsets, const kf_seeds *seeds, const float *seed_hits, int32_t *hit_idx_out,
+                 const kf_tracks_out *out, void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    kf_fit_params P;
+    int rc = check_fit_params(ctx, fit, P);
+    if (rc) return rc;
+    if (P.precision != KF_PREC_MIXED)
+        return fail(ctx, KF_EINVAL, "combinatorial building runs the mixed precision policy only");
+    if (n_slots != 1 && n_slots != 2 && n_slots != 4 && n_slots != 8)
+        return fail(ctx, KF_EINVAL, "n_slots must be 1, 2, 4 or 8");
+    Geom G;
+    if ((rc = to_geom(ctx, geom, G))) return rc;
+    if ((rc = set_dev(ctx))) return rc;
+    if ((rc = check_events(ctx, geom, n_events, n_layers, layers, event_offsets, false))) return rc;
+    kf_build_params B = {3.0, 30.0, 32, 0};
+    if (bp) B = *bp;
+    if (!(B.nsigma > 0) || !(B.chi2_cut > 0) || B.max_cand < 1 || B.max_cand > 64)
+        return fail(ctx, KF_EINVAL, "build params: nsigma > 0, chi2_cut > 0, 1 <= max_cand <= 64");
+    const int n = event_offsets[n_events];
+    if (n == 0) return KF_OK;
+    if (!seeds || !out) return fail(ctx, KF_EINVAL, "seeds and out are required");
+    NEED_DEV(seeds->state, "seeds.state");
+    NEED_DEV(seeds->q, "seeds.q");
+    NEED_DEV(seed_hits, "seed_hits");
+    NEED_DEV(hit_idx_out, "hit_idx_out");
+    OPT_DEV(out->state, "out.state");
+    OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->chi2, "out.chi2");
+    OPT_DEV(out->ndof, "out.ndof");
+    OPT_DEV(out->status, "out.status");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *rest = nullptr;
+    LayerDev *dl = nullptr;
+    int32_t *deoff = nullptr;
+    const size_t nhist = order_scratch_ints();
+    const size_t ord_bytes = ((nhist + (size_t)n) * sizeof(int32_t) + 255) & ~(size_t)255;
+    if ((rc = upload_layers(ctx, st, n_events, n_layers, layers, event_offsets,
+                            ord_bytes + ckf_scratch_bytes(n, n_layers, n_slots), &rest, &dl, &deoff, false)))
+        return rc;
+    int32_t *hist = reinterpret_cast<int32_t *>(rest);
+    int32_t *order = hist + nhist;
+    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, hist, order, st);
+    if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
+    CkfArgs c;
+    memset(&c, 0, sizeof c);
+    BuildArgs &a = c.b;
+    a.n = n;
+    a.n_events = n_events;
+    a.n_layers = n_layers;
+    a.n64 = P.n_fp64_updates;
+    a.seed_cov = P.seed_cov;
+    a.ms_on = P.ms_on;
+    a.max_cand = B.max_cand;
+    a.nsigma = (float)B.nsigma;
+    a.chi2_cut = (float)B.chi2_cut;
+    a.layers = dl;
+    a.event_off = deoff;
+    a.seed_state = seeds->state;
+    a.q = seeds->q;
+    a.seed_hits = seed_hits;
+    a.hit_idx = hit_idx_out;
+    a.order = order;
+    a.o_state = out->state;
+    a.o_cov = out->cov;
+    a.o_chi2 = out->chi2;
+    a.o_ndof = out->ndof;
+    a.o_status = out->status;
+    c.n_slots = n_slots;
+    ckf_carve(c, static_cast<char *>(rest) + ord_bytes, n, n_layers, n_slots);
+    cudaError_t e = launch_ckf(G, c, st);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "combinatorial build kernels");
+}
+
 int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_binned_layer *layers,
                    const int32_t *event_offsets, const float *seed_hits, const int32_t *hit_idx, int32_t *offsets_out,
                    uint8_t *layer_out, float *x_out, float *y_out, float *z_out, void *stream)

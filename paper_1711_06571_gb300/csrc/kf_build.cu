@@ -379,47 +379,25 @@ __device__ __forceinline__ void score_coop(const Track<T, P> &st, bool do_step, 
 // The build keeps the covariance in FP32 on the mixed path after the seed fit
 // (whose updates are the FP64 ones) and in FP64 on the all-FP64 path; a mixed
 // step at a near-tangent crossing runs in FP64.
-template <bool FP64, bool COOP>
-// three blocks per SM (at most 168 registers a thread): 12 warps to hide the
-// FP64 and memory latencies of the layer steps
-__global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const BuildArgs a)
+// The seed fit of a build track over its three seed hits (layers 0..2 of its
+// event): the first n64 updates with an FP64 covariance (the structured update
+// at the first hit, Joseph form after), the rest in the layer covariance type.
+// Returns whether the track is still alive.
+template <bool FP64>
+__device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf, const LayerDev *lays, int n, int t,
+                                         Track<typename sel_t<FP64>::T, typename sel_t<FP64>::P> &st,
+                                         typename sel_t<FP64>::T pc[21], typename sel_t<FP64>::T alpha,
+                                         typename sel_t<FP64>::T mass2, unsigned &status, double &chi2, int &used,
+                                         bool alive)
 {
     using T = typename sel_t<FP64>::T;
-    using P = typename sel_t<FP64>::P;
-    using C = T;  // covariance type of the build layers
-    __shared__ Surf s_surf[MAX_SURF];
-    for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
-    __syncthreads();
-    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i0 < a.n;
-    const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real track but write nothing
-    const int t = a.order ? a.order[i] : i;
-    const int n = a.n;
-    const int e = find_event(a.event_off, a.n_events, t);
-    const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
-    Track<T, P> st;
-    st.x = from_f<P>(a.seed_state[0 * n + t]);
-    st.y = from_f<P>(a.seed_state[1 * n + t]);
-    st.z = from_f<P>(a.seed_state[2 * n + t]);
-    st.ip = (T)a.seed_state[3 * n + t];
-    st.phi = from_f<P>(a.seed_state[4 * n + t]);
-    st.th = from_f<P>(a.seed_state[5 * n + t]);
-    const int q = a.q[t];
-    const T alpha = FP64 ? T(-q * g.kbd) : T(-q) * T(g.kb);
-    const T mass2 = FP64 ? T(g.mass2d) : T(g.mass2);
-    const double alphad = -q * g.kbd;
-    unsigned status = 0u;
-    double chi2 = 0.0;
-    int used = 0;
-    bool alive = active;
+    using C = T;
     // seed fit over the three seed hits; the first n64 updates with an FP64 covariance
     double pd[21];
 #pragma unroll
     for (int i = 0; i < 21; ++i) pd[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
-    C pc[21];
-    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
     const int n1 = min(a.n64, 3);
     int k = 0;
     for (; k < n1 && alive; ++k) {
@@ -479,6 +457,45 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
         }
         ++used;
     }
+    return alive;
+}
+
+template <bool FP64, bool COOP>
+// three blocks per SM (at most 168 registers a thread): 12 warps to hide the
+// FP64 and memory latencies of the layer steps
+__global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const BuildArgs a)
+{
+    using T = typename sel_t<FP64>::T;
+    using P = typename sel_t<FP64>::P;
+    using C = T;  // covariance type of the build layers
+    __shared__ Surf s_surf[MAX_SURF];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
+    __syncthreads();
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i0 < a.n;
+    const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real track but write nothing
+    const int t = a.order ? a.order[i] : i;
+    const int n = a.n;
+    const int e = find_event(a.event_off, a.n_events, t);
+    const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
+    Track<T, P> st;
+    st.x = from_f<P>(a.seed_state[0 * n + t]);
+    st.y = from_f<P>(a.seed_state[1 * n + t]);
+    st.z = from_f<P>(a.seed_state[2 * n + t]);
+    st.ip = (T)a.seed_state[3 * n + t];
+    st.phi = from_f<P>(a.seed_state[4 * n + t]);
+    st.th = from_f<P>(a.seed_state[5 * n + t]);
+    const int q = a.q[t];
+    const T alpha = FP64 ? T(-q * g.kbd) : T(-q) * T(g.kb);
+    const T mass2 = FP64 ? T(g.mass2d) : T(g.mass2);
+    const double alphad = -q * g.kbd;
+    unsigned status = 0u;
+    double chi2 = 0.0;
+    int used = 0;
+    bool alive = active;
+    C pc[21];
+    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
+    alive = seed_fit<FP64>(a, s_surf, lays, n, t, st, pc, alpha, mass2, status, chi2, used, alive);
     if (active)
         for (int L = 0; L < 3; ++L) a.hit_idx[(size_t)L * n + t] = -1;
     // build layers
@@ -576,6 +593,407 @@ cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp
     } else {
         if (warp_coop) build_kernel<false, true><<<grid, b, 0, st>>>(g, a);
         else build_kernel<false, false><<<grid, b, 0, st>>>(g, a);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ combinatorial building
+// Sec. 2: building branches to explore several candidates per seed; Sec. 4.3:
+// a fixed number of slots per seed holds its candidates, the best kept.  Here
+// the slots of a seed are n_slots consecutive lanes of a warp, each carrying
+// one candidate in registers.  Per layer every lane predicts its candidate,
+// searches the window and lists its best children (hits below the chi2 cut,
+// ranked; then the candidate without a hit); the lanes of the seed merge their
+// lists with shuffles into the seed's new ranking (more hits first, then
+// smaller total chi2, then lower parent slot, then lower hit index); lane j
+// takes the j-th child, fetching its parent's predicted state from the
+// parent's lane by shuffles, and updates it with the child's hit.  A back
+// pointer (parent slot, hit) per layer and slot gives the hits of the best
+// candidate at the end.
+
+// pre-pass: the seed fit, one thread per seed
+__global__ void __launch_bounds__(128) ckf_seed_kernel(const Geom g, const CkfArgs c)
+{
+    const BuildArgs &a = c.b;
+    __shared__ Surf s_surf[MAX_SURF];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n) return;
+    const int n = a.n;
+    const int e = find_event(a.event_off, a.n_events, t);
+    const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
+    Track<float, ff> st;
+    st.x = from_f<ff>(a.seed_state[0 * n + t]);
+    st.y = from_f<ff>(a.seed_state[1 * n + t]);
+    st.z = from_f<ff>(a.seed_state[2 * n + t]);
+    st.ip = a.seed_state[3 * n + t];
+    st.phi = from_f<ff>(a.seed_state[4 * n + t]);
+    st.th = from_f<ff>(a.seed_state[5 * n + t]);
+    const int q = a.q[t];
+    float pc[21];
+    unsigned status = 0u;
+    double chi2 = 0.0;
+    int used = 0;
+    const bool alive =
+        seed_fit<false>(a, s_surf, lays, n, t, st, pc, float(-q) * g.kb, g.mass2, status, chi2, used, true);
+    const float w[11] = {st.x.hi, st.x.lo, st.y.hi, st.y.lo, st.z.hi, st.z.lo, st.phi.hi, st.phi.lo, st.th.hi,
+                         st.th.lo, st.ip};
+#pragma unroll
+    for (int k = 0; k < 11; ++k) c.seed_st[(size_t)k * n + t] = w[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) c.seed_cov[(size_t)k * n + t] = pc[k];
+    c.seed_chi2[t] = chi2;
+    c.seed_used[t] = used;
+    c.seed_status[t] = status;
+    c.seed_alive[t] = alive ? 1 : 0;
+}
+
+// prediction of a near-tangent crossing in FP64, out of line
+static __device__ __noinline__ MixedIO ckf_predict_fp64(MixedIO m, double alpha, double mass2, int ms_on,
+                                                       const Surf *sf)
+{
+    Track<double, double> sd;
+    sd.x = to_d(m.st.x);
+    sd.y = to_d(m.st.y);
+    sd.z = to_d(m.st.z);
+    sd.phi = to_d(m.st.phi);
+    sd.th = to_d(m.st.th);
+    sd.ip = m.st.ip;
+    double pd[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pd[i] = f2d(m.p[i]);
+    Jac<double> J;
+    if (!propagate(sd, alpha, *sf, J)) {
+        m.ok = 0;
+        return m;
+    }
+    transport<double>(pd, J);
+    if (ms_on) m.status |= ms_noise<double, double>(sd, *sf, J.cphi1, J.sphi1, mass2, pd);
+    auto f = [](double d) {
+        const float h = (float)d;
+        return ff{h, (float)(d - (double)h)};
+    };
+    m.st.x = f(sd.x);
+    m.st.y = f(sd.y);
+    m.st.z = f(sd.z);
+    m.st.phi = f(sd.phi);
+    m.st.th = f(sd.th);
+    m.st.ip = (float)sd.ip;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) m.p[i] = d2f(pd[i]);
+    m.ok = 1;
+    return m;
+}
+
+// A child in the seed's ranking.  nh < 0: no child.
+struct CkfKey {
+    int nh;
+    int parent;
+    int hit;  // original hit index; a child without a hit ranks after its parent's hits
+    double chi2;
+};
+constexpr int CKF_NO_HIT = 0x7fffffff;
+
+__device__ __forceinline__ bool ckf_before(const CkfKey &a, const CkfKey &b)
+{
+    if (a.nh != b.nh) return a.nh > b.nh;
+    if (a.chi2 != b.chi2) return a.chi2 < b.chi2;
+    if (a.parent != b.parent) return a.parent < b.parent;
+    return a.hit < b.hit;
+}
+
+__device__ __forceinline__ CkfKey ckf_shfl_xor(const CkfKey &k, int m)
+{
+    CkfKey o;
+    o.nh = __shfl_xor_sync(0xffffffffu, k.nh, m);
+    o.parent = __shfl_xor_sync(0xffffffffu, k.parent, m);
+    o.hit = __shfl_xor_sync(0xffffffffu, k.hit, m);
+    o.chi2 = __shfl_xor_sync(0xffffffffu, k.chi2, m);
+    return o;
+}
+
+__device__ __forceinline__ ff shfl_ff(ff v, int src)
+{
+    return ff{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128, 3) ckf_kernel(const Geom g, const CkfArgs c)
+{
+    const BuildArgs &a = c.b;
+    __shared__ Surf s_surf[MAX_SURF];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int slot = lane & (NS - 1);
+    const int base = lane & ~(NS - 1);
+    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) / NS;
+    const bool active = i0 < a.n;
+    const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real seed but write nothing
+    const int t = a.order ? a.order[i] : i;
+    const int n = a.n;
+    const size_t nslots = (size_t)n * NS;
+    const int e = find_event(a.event_off, a.n_events, t);
+    const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
+    const int q = a.q[t];
+    const float alpha = float(-q) * g.kb;
+    const double alphad = -q * g.kbd;
+    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
+    // the seed's candidate in slot 0; the other slots start empty
+    Track<float, ff> st;
+    st.x = ff{c.seed_st[0 * (size_t)n + t], c.seed_st[1 * (size_t)n + t]};
+    st.y = ff{c.seed_st[2 * (size_t)n + t], c.seed_st[3 * (size_t)n + t]};
+    st.z = ff{c.seed_st[4 * (size_t)n + t], c.seed_st[5 * (size_t)n + t]};
+    st.phi = ff{c.seed_st[6 * (size_t)n + t], c.seed_st[7 * (size_t)n + t]};
+    st.th = ff{c.seed_st[8 * (size_t)n + t], c.seed_st[9 * (size_t)n + t]};
+    st.ip = c.seed_st[10 * (size_t)n + t];
+    float pc[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) pc[k] = c.seed_cov[(size_t)k * n + t];
+    double chi2 = c.seed_chi2[t];
+    int nu = c.seed_used[t];
+    int nh = 3;
+    unsigned status = c.seed_status[t];
+    bool alive = slot == 0 && c.seed_alive[t] != 0;
+    bool stopped = false;
+    if (active && slot == 0)
+        for (int L = 0; L < 3; ++L) a.hit_idx[(size_t)L * n + t] = -1;
+    for (int L = 3; L < a.n_layers; ++L) {
+        const LayerDev ly = lays[L];
+        const Surf &sf = s_surf[ly.surface];
+        // 1. prediction (a candidate that cannot reach the layer stops, unchanged)
+        unsigned step = 0u;
+        bool search = alive && !stopped;
+        bool stop_now = false;
+        if (search) {
+            if (crossing_sine(st, alpha, sf) > 0.8f) {
+                MixedIO m;
+                mixed_pack(m, st, pc, chi2, 0u);
+                m = ckf_predict_fp64(m, alphad, g.mass2d, a.ms_on, &sf);
+                if (m.ok) {
+                    unsigned s2;
+                    double c2;
+                    mixed_unpack(m, st, pc, c2, s2);
+                    step |= s2;
+                } else {
+                    stop_now = true;
+                }
+            } else {
+                Jac<float> J;
+                if (!propagate(st, alpha, sf, J)) {
+                    stop_now = true;
+                } else {
+                    transport<float>(pc, J);
+                    if (a.ms_on) step |= ms_noise<float, float>(st, sf, J.cphi1, J.sphi1, g.mass2, pc);
+                }
+            }
+        }
+        if (stop_now) {
+            step |= KF_ST_NO_INTERSECT;
+            search = false;
+        }
+        const bool pass = alive && (stopped || stop_now);  // carried unchanged
+        // 2. window search: this candidate's best NS hits below the cut, ranked
+        double lc[NS];
+        int lh[NS], lp[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            lc[k] = 0.0;
+            lh[k] = CKF_NO_HIT;
+            lp[k] = -1;
+        }
+        int cnt = 0;
+        if (search) {
+            const Window w = make_window(st, pc, sf, kn.nsigma);
+            const bool shared = sf.var_rad == sf.var_rphi;
+            Ldl3 fs{0, 0, 0, 0, 0, 0};
+            const bool fs_ok = !shared || shared_factor(pc, sf, fs);
+            int ncand = 0;
+            bool capped = false;
+            for (int zb = w.z_lo; zb <= w.z_hi && !capped && fs_ok; ++zb) {
+                const int row = zb * KF_NPHI;
+                const int first = w.phi_lo, last = w.phi_lo + w.nphi - 1;
+                for (int part = 0; part < 2 && !capped; ++part) {
+                    int b0, b1;
+                    if (part == 0) {
+                        b0 = first;
+                        b1 = min(last, KF_NPHI - 1);
+                    } else {
+                        if (last < KF_NPHI) break;
+                        b0 = 0;
+                        b1 = last - KF_NPHI;
+                    }
+                    const int j0 = max(ly.offsets[row + b0], 0), j1 = min(ly.offsets[row + b1 + 1], ly.n_hits);
+                    for (int j = j0; j < j1; ++j) {
+                        if (ncand >= kn.max_cand) {
+                            capped = true;
+                            break;
+                        }
+                        ++ncand;
+                        const float4 h = ly.packed[j];
+                        const double c2 = cand_chi2(st, pc, sf, shared, fs, h);
+                        if (!(c2 >= 0.0 && c2 < (double)kn.chi2_cut)) continue;
+                        const double tot = chi2 + c2;
+                        const int hi = __float_as_int(h.w);
+                        // rank among this candidate's hits: total chi2, then hit index
+                        int pos = 0;
+#pragma unroll
+                        for (int k = 0; k < NS; ++k)
+                            if (k < cnt && (lc[k] < tot || (lc[k] == tot && lh[k] < hi))) ++pos;
+                        if (pos < NS) {
+#pragma unroll
+                            for (int k = NS - 1; k > 0; --k)
+                                if (k > pos) {
+                                    lc[k] = lc[k - 1];
+                                    lh[k] = lh[k - 1];
+                                    lp[k] = lp[k - 1];
+                                }
+#pragma unroll
+                            for (int k = 0; k < NS; ++k)
+                                if (k == pos) {
+                                    lc[k] = tot;
+                                    lh[k] = hi;
+                                    lp[k] = j;
+                                }
+                            cnt = min(cnt + 1, NS);
+                        }
+                    }
+                }
+            }
+            if (capped) step |= KF_ST_CAND_CAPPED;
+        }
+        // 3. the seed's new ranking: NS rounds of a shuffle minimum over its lanes
+        int head = 0;
+        CkfKey mine{-1, 0, CKF_NO_HIT, 0.0};
+        int my_ppos = -1;
+        for (int r = 0; r < NS; ++r) {
+            CkfKey k{-1, slot, CKF_NO_HIT, 0.0};
+            int ppos = -1;
+            if (pass) {
+                if (head == 0) k = CkfKey{nh, slot, CKF_NO_HIT, chi2};
+            } else if (search) {
+#pragma unroll
+                for (int m = 0; m < NS; ++m)
+                    if (m == head && m < cnt) {
+                        k = CkfKey{nh + 1, slot, lh[m], lc[m]};
+                        ppos = lp[m];
+                    }
+                if (head == cnt) k = CkfKey{nh, slot, CKF_NO_HIT, chi2};
+            }
+            CkfKey best = k;
+#pragma unroll
+            for (int m = 1; m < NS; m <<= 1) {
+                const CkfKey o = ckf_shfl_xor(best, m);
+                if (ckf_before(o, best)) best = o;
+            }
+            const int owner = base + (best.nh >= 0 ? best.parent : slot);
+            const int wpos = __shfl_sync(0xffffffffu, ppos, owner);
+            if (best.nh >= 0 && best.parent == slot) ++head;
+            if (slot == r) {
+                mine = best;
+                my_ppos = wpos;
+            }
+        }
+        // 4. take the child: the parent's predicted candidate, by shuffles
+        const int src = base + (mine.nh >= 0 ? mine.parent : slot);
+        const unsigned pstat = status | step;
+        Track<float, ff> ps;
+        ps.x = shfl_ff(st.x, src);
+        ps.y = shfl_ff(st.y, src);
+        ps.z = shfl_ff(st.z, src);
+        ps.phi = shfl_ff(st.phi, src);
+        ps.th = shfl_ff(st.th, src);
+        ps.ip = __shfl_sync(0xffffffffu, st.ip, src);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) pc[k] = __shfl_sync(0xffffffffu, pc[k], src);
+        st = ps;
+        chi2 = __shfl_sync(0xffffffffu, chi2, src);
+        nu = __shfl_sync(0xffffffffu, nu, src);
+        status = __shfl_sync(0xffffffffu, pstat, src);
+        const bool pstop = __shfl_sync(0xffffffffu, (int)(stopped || stop_now), src) != 0;
+        alive = active && mine.nh >= 0;
+        stopped = pstop;
+        if (alive && mine.hit != CKF_NO_HIT) {
+            const float4 h = ly.packed[my_ppos];
+            double c2u = 0.0;
+            if (!kf_update_mixed(st, pc, h.x, h.y, h.z, sf, c2u)) status |= KF_ST_CHOL_FAIL;
+            nu += 1;
+        }
+        if (alive) {
+            chi2 = mine.chi2;
+            nh = mine.nh;
+        }
+        if (active) {
+            c.bp_parent[(size_t)L * nslots + (size_t)i * NS + slot] = (int8_t)(alive ? mine.parent : -1);
+            c.bp_hit[(size_t)L * nslots + (size_t)i * NS + slot] = alive && mine.hit != CKF_NO_HIT ? mine.hit : -1;
+        }
+    }
+    __syncwarp();
+    if (!active || slot != 0) return;
+    // 5. the first candidate is the track
+    int s = 0;
+    for (int L = a.n_layers - 1; L >= 3; --L) {
+        const size_t o = (size_t)L * nslots + (size_t)i * NS + s;
+        a.hit_idx[(size_t)L * n + t] = c.bp_hit[o];
+        s = max((int)c.bp_parent[o], 0);
+    }
+    double sv[6] = {to_d(st.x), to_d(st.y), to_d(st.z), (double)st.ip, to_d(st.phi), to_d(st.th)};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (!isfinite(sv[k])) status |= KF_ST_NONFINITE;
+    if (a.o_state)
+        for (int k = 0; k < 6; ++k) a.o_state[(size_t)k * n + t] = sv[k];
+    if (a.o_cov)
+        for (int k = 0; k < 21; ++k) a.o_cov[(size_t)k * n + t] = (double)pc[k];
+    if (a.o_chi2) a.o_chi2[t] = chi2;
+    if (a.o_ndof) a.o_ndof[t] = 2 * nu - 5;
+    if (a.o_status) a.o_status[t] = status;
+}
+
+size_t ckf_scratch_bytes(int n, int n_layers, int n_slots)
+{
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t m = (size_t)n;
+    return al(11 * 4 * m) + al(21 * 4 * m) + al(8 * m) + al(4 * m) + al(4 * m) + al(m) +
+           al((size_t)n_layers * m * n_slots) + al(4 * (size_t)n_layers * m * n_slots) + 256;
+}
+
+void ckf_carve(CkfArgs &c, void *scratch, int n, int n_layers, int n_slots)
+{
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t m = (size_t)n;
+    char *p = static_cast<char *>(scratch);
+    c.seed_st = reinterpret_cast<float *>(p);
+    p += al(11 * 4 * m);
+    c.seed_cov = reinterpret_cast<float *>(p);
+    p += al(21 * 4 * m);
+    c.seed_chi2 = reinterpret_cast<double *>(p);
+    p += al(8 * m);
+    c.seed_used = reinterpret_cast<int32_t *>(p);
+    p += al(4 * m);
+    c.seed_status = reinterpret_cast<uint32_t *>(p);
+    p += al(4 * m);
+    c.seed_alive = reinterpret_cast<int8_t *>(p);
+    p += al(m);
+    c.bp_parent = reinterpret_cast<int8_t *>(p);
+    p += al((size_t)n_layers * m * n_slots);
+    c.bp_hit = reinterpret_cast<int32_t *>(p);
+}
+
+cudaError_t launch_ckf(const Geom &g, const CkfArgs &c, cudaStream_t st)
+{
+    const int n = c.b.n;
+    if (n <= 0) return cudaSuccess;
+    ckf_seed_kernel<<<(n + 127) / 128, 128, 0, st>>>(g, c);
+    const long long threads = (long long)n * c.n_slots;
+    const int grid = (int)((threads + 127) / 128);
+    switch (c.n_slots) {
+    case 1: ckf_kernel<1><<<grid, 128, 0, st>>>(g, c); break;
+    case 2: ckf_kernel<2><<<grid, 128, 0, st>>>(g, c); break;
+    case 4: ckf_kernel<4><<<grid, 128, 0, st>>>(g, c); break;
+    case 8: ckf_kernel<8><<<grid, 128, 0, st>>>(g, c); break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

@@ -83,6 +83,27 @@ struct BuildArgs {
     uint32_t *o_status;
 };
 cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp_coop, cudaStream_t st);
+
+// Combinatorial building: n_slots candidates per seed (mixed precision).  The
+// seed fit runs first, one thread per seed, into the seed_* arrays; then
+// n_slots lanes of a warp carry one seed's candidates through the layers,
+// leaving back pointers (parent slot, hit) per layer and slot.
+struct CkfArgs {
+    BuildArgs b;
+    int n_slots;
+    int pad_;
+    float *seed_st;        // [11][n]: x, y, z, phi, theta as float-float (hi, lo), then 1/pT
+    float *seed_cov;       // [21][n]
+    double *seed_chi2;     // [n]
+    int32_t *seed_used;    // [n]
+    uint32_t *seed_status; // [n]
+    int8_t *seed_alive;    // [n]
+    int8_t *bp_parent;     // [n_layers][n * n_slots]
+    int32_t *bp_hit;       // [n_layers][n * n_slots]
+};
+size_t ckf_scratch_bytes(int n, int n_layers, int n_slots);
+void ckf_carve(CkfArgs &c, void *scratch, int n, int n_layers, int n_slots);
+cudaError_t launch_ckf(const Geom &g, const CkfArgs &c, cudaStream_t st);
 size_t gather_scratch_bytes(int n);
 cudaError_t launch_gather(int n, int n_events, int n_layers, const LayerDev *layers, const int32_t *event_off,
                           const float *seed_hits, const int32_t *hit_idx, int32_t *off_out, uint8_t *layer_out,

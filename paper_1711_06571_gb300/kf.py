@@ -144,6 +144,10 @@ _SIGS = {
     "kf_bin_hits_batched": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    "kf_build_ckf": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params),
+                               C.POINTER(kf_build_params), C.c_int32, C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
+                               C.POINTER(C.c_int32), C.POINTER(kf_seeds), C.c_void_p, C.c_void_p,
+                               C.POINTER(kf_tracks_out), C.c_void_p]),
     "kf_bin_hits_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "kf_measure_peak": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
@@ -354,6 +358,20 @@ def kf_build_besthit(ctx, geom, fit, bp, n_events, n_layers, layers, event_offse
     _check(ctx, load().kf_build_besthit(ctx, C.byref(g), C.byref(f), C.byref(b), int(n_events), int(n_layers),
                                         layers, eo, C.byref(s), _ptr(seed_hits), _ptr(hit_idx_out), C.byref(o),
                                         _stream(stream)))
+
+
+def kf_build_ckf(ctx, geom, fit, bp, n_slots, n_events, n_layers, layers, event_offsets, seed_state, seed_q,
+                 seed_hits, hit_idx_out, out_state=None, out_cov=None, out_chi2=None, out_ndof=None, out_status=None,
+                 stream=None):
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    f = fit if fit is not None else fit_params()
+    b = bp if bp is not None else build_params()
+    eo = (C.c_int32 * (n_events + 1))(*[int(v) for v in event_offsets])
+    s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    _check(ctx, load().kf_build_ckf(ctx, C.byref(g), C.byref(f), C.byref(b), int(n_slots), int(n_events),
+                                    int(n_layers), layers, eo, C.byref(s), _ptr(seed_hits), _ptr(hit_idx_out),
+                                    C.byref(o), _stream(stream)))
 
 
 def kf_gather_hits(ctx, n_events, n_layers, layers, event_offsets, seed_hits, hit_idx, offsets_out, layer_out,

@@ -118,7 +118,7 @@ def seeds_from_seed_hits(ctx, geom, seed_hits_np, device="cuda", stream=None):
 
 
 def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, nsigma=3.0, chi2_cut=30.0,
-                max_cand=32):
+                max_cand=32, n_slots=0):
     """Bin every event's layers, seed, and run best-hit building of all events in one
     launch; returns numpy idx (n, n_layers) and fitted tracks (track-major)."""
     g = kf.make_geometry(geom)
@@ -132,10 +132,15 @@ def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, 
     n = int(eoff[-1])
     idx = torch.empty((n_layers, n), dtype=torch.int32, device="cuda")
     out = alloc_fit_out(n)
-    kf.kf_build_besthit(ctx, g, kf.fit_params(precision=precision), kf.build_params(nsigma, chi2_cut, max_cand,
-                                                                                       warp_coop),
-                        len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"], out["chi2"],
-                        out["ndof"], out["status"])
+    if n_slots:  # combinatorial building with n_slots candidates per seed
+        kf.kf_build_ckf(ctx, g, kf.fit_params(precision=precision), kf.build_params(nsigma, chi2_cut, max_cand),
+                        n_slots, len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
+                        out["chi2"], out["ndof"], out["status"])
+    else:
+        kf.kf_build_besthit(ctx, g, kf.fit_params(precision=precision), kf.build_params(nsigma, chi2_cut, max_cand,
+                                                                                           warp_coop),
+                            len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
+                            out["chi2"], out["ndof"], out["status"])
     torch.cuda.synchronize()
     return dict(idx=idx.t().cpu().numpy(), state=out["state"].t().cpu().numpy(),
                 cov=unpack_cov(out["cov"].cpu().numpy()), chi2=out["chi2"].cpu().numpy(),

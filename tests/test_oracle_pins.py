@@ -569,3 +569,84 @@ def test_besthit_finds_true_hits(oracle_mod):
     assert fake < 0.03, fake
     # seed layers carry the given seed hits
     np.testing.assert_array_equal(out["idx"][:, :3], ev["seed_idx"])
+
+
+# ---------------------------------------------------------------------- combinatorial building (Sec. 2, 4.3)
+
+def test_ckf_with_one_slot_is_besthit(oracle_mod):
+    """One candidate per seed: the ranking keeps the smallest-chi2 hit below the
+    cut, else the candidate without a hit -- best-hit building, to the bit."""
+    g = synth.geometry("barrel17")
+    ev = _binned_event(oracle_mod, g, 600, 31)
+    bh = oracle_mod.build_besthit(g, ev)
+    ck = oracle_mod.build_ckf(g, ev, n_slots=1)
+    for k in ("idx", "state", "cov", "chi2", "ndof", "status"):
+        np.testing.assert_array_equal(ck[k], bh[k])
+
+
+def _small_event(oracle_mod, n_signal, seed):
+    """Three seed layers and three build layers of the 10-cylinder barrel, a few
+    hits a layer (signal + noise)."""
+    g = synth.geometry("barrel10")
+    ev = synth.gen_event(g, n_signal, synth.BASE_SEED + seed, noise_frac=0.5)
+    ev["layers"] = ev["layers"][:6]
+    g = dict(g, surfaces=g["surfaces"][:6])
+    for ly in ev["layers"]:
+        ly["perm"], ly["offsets"] = oracle_mod.bin_layer(ly["x"], ly["y"], ly["z"], g["surfaces"][ly["surf"]]["half_or_rin"])
+    return g, ev
+
+
+@pytest.mark.parametrize("seed", [41, 42, 43])
+def test_ckf_equals_exhaustive_search_without_pruning(oracle_mod, seed):
+    """With more slots than paths, a window wider than the layer and scattering off,
+    nothing is pruned: the first candidate must be the best of all hit choices
+    (one hit or none per build layer), found by fitting every path and keeping
+    those whose every hit passes the chi2 cut -- more hits first, then smaller
+    total chi2."""
+    import itertools
+    g, ev = _small_event(oracle_mod, 3, seed)
+    nl = len(ev["layers"])
+    cut = 30.0
+    ck = oracle_mod.build_ckf(g, ev, n_slots=1024, nsigma=1e4, chi2_cut=cut, max_cand=1024, ms_on=False)
+    checked = 0
+    for t in range(ev["n"]):
+        sh = ev["seed_hits"][t]
+        seed_state, q = oracle_mod.seed(sh[0], sh[1], sh[2], g["bz"])
+        choices = [[-1] + list(range(len(ev["layers"][L]["x"]))) for L in range(3, nl)]
+        best = None
+        for path in itertools.product(*choices):
+            lay = [0, 1, 2] + [3 + k for k, h in enumerate(path) if h >= 0]
+            hx = [sh[0, 0], sh[1, 0], sh[2, 0]] + [ev["layers"][3 + k]["x"][h] for k, h in enumerate(path) if h >= 0]
+            hy = [sh[0, 1], sh[1, 1], sh[2, 1]] + [ev["layers"][3 + k]["y"][h] for k, h in enumerate(path) if h >= 0]
+            hz = [sh[0, 2], sh[1, 2], sh[2, 2]] + [ev["layers"][3 + k]["z"][h] for k, h in enumerate(path) if h >= 0]
+            surf = [ev["layers"][L]["surf"] for L in lay]
+            r = oracle_mod.fit_one(g, surf, hx, hy, hz, seed_state, q, ms_on=False)
+            if r["status"] & 7 or r["n_used"] != len(lay):
+                continue
+            if np.any(r["chi2_each"][3:] >= cut):
+                continue
+            key = (-len(lay), r["chi2"])
+            if best is None or key < best[0]:
+                best = (key, path, r)
+        assert best is not None
+        (negnh, chi2), path, r = best
+        np.testing.assert_array_equal(ck["idx"][t, 3:], np.array(path))
+        assert ck["chi2"][t] == pytest.approx(chi2, rel=1e-9)
+        np.testing.assert_allclose(ck["state"][t], r["state"], rtol=1e-9, atol=1e-9)
+        checked += 1
+    assert checked == ev["n"]
+
+
+def test_ckf_more_slots_recover_inefficiency(oracle_mod):
+    """Keeping several candidates per seed recovers true hits that best-hit loses
+    to a noise hit with a smaller chi2 (the branching of Sec. 2)."""
+    g = synth.geometry("barrel17")
+    ev = _binned_event(oracle_mod, g, 2000, 32)
+    where = ev["truth_where"][:, 3:]
+    has = where >= 0
+    effs = []
+    for ns in (1, 4):
+        ck = oracle_mod.build_ckf(g, ev, n_slots=ns)
+        effs.append(np.mean(ck["idx"][:, 3:][has] == where[has]))
+        np.testing.assert_array_equal(ck["idx"][:, :3], ev["seed_idx"])
+    assert effs[1] > effs[0], effs
