@@ -39,7 +39,7 @@ WORKLOAD = ("KF fit of 1,000,000 tracks x 17 barrel layers (R 4-100 cm), Bz 3.8 
 # DRAM bytes (read + write) of one fit-kernel launch on this workload, from an
 # ncu capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # set to None whenever the kernel changes until it is captured again
-FIT_KERNEL_DRAM_BYTES = 2.319057e9 + 0.969327e9
+FIT_KERNEL_DRAM_BYTES = None
 FP64_FLOP_SEED_PHASE = 1897.0
 FP64_FLOP_PER_FP32_UPDATE = 44.0
 FP32_FLOP_PER_FP32_UPDATE = 900.0
@@ -547,7 +547,7 @@ def main():
     ach64 = fp64_flop / (fit_avg * 1e-3) / 1e12
     roofline = dict(bound="alu", pipe="fp64", achieved=ach64, peak=peak64 / 1e12, unit="TFLOP/s",
                     frac=ach64 / (peak64 / 1e12),
-                    traffic=FIT_KERNEL_DRAM_BYTES if n == N_TRACKS else None,
+                    traffic=FIT_KERNEL_DRAM_BYTES if n == N_TRACKS and FIT_KERNEL_DRAM_BYTES else None,
                     peak_source="kf_measure_peak FP64 FMA chains (measured in this run); nominal 152 SMs x 2 "
                                 "DFMA/clock x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s",
                     fp32=dict(achieved=fp32_flop / (fit_avg * 1e-3) / 1e12, peak=peak32 / 1e12, unit="TFLOP/s",

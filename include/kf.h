@@ -180,6 +180,31 @@ int kf_make_seeds(kf_ctx *ctx, const kf_geometry *geom, int32_t n, const kf_trac
 int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n, const kf_seeds *seeds,
            const kf_track_hits *hits, const kf_tracks_out *out, void *stream);
 
+/* Outward-inward refit (the final fit of Sec. 2 run a second time, from the
+ * last hit back to the first, so that the estimate at the first hit uses
+ * every hit).  Each track is run backwards by reversing its direction of
+ * motion -- phi -> phi + pi, theta -> pi - theta, q -> -q, the same helix
+ * traversed the other way -- and the hits the forward fit used (the first
+ * (ndof + 5) / 2 of the track), in reverse order, are fitted as by kf_fit
+ * (FP64 for the first updates), starting at the last used hit from the forward
+ * fit's state there with the forward covariance times cov_scale (100 is
+ * usual: the forward information then counts once more with weight 1/100,
+ * and the filter stays on the fitted trajectory near a track's apex, where a
+ * fresh 1e4 covariance makes the result depend on rounding); the result at the
+ * first hit is turned back to the forward direction.
+ *   hits: device CSR as for kf_fit (forward path order).
+ *   fwd_state, fwd_cov: device [6][n] and [21][n] FP64, the forward fit's state
+ *     and covariance at each track's last used hit (kf_fit's out.state and
+ *     out.cov); q: device [n], the charges used by that fit; fwd_ndof: device
+ *     [n], its ndof.  cov_scale > 0.
+ *   out: device, state and covariance at the first hit (forward direction),
+ *     chi2 and ndof of the backward pass, status.
+ * Blocks until offsets[n] is read; the rest runs on the stream (kf_fit's
+ * schedule and precision from params). */
+int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
+                    const kf_track_hits *hits, const double *fwd_state, const double *fwd_cov, const int8_t *q,
+                    const int32_t *fwd_ndof, double cov_scale, const kf_tracks_out *out, void *stream);
+
 /* End-to-end fit from host memory: copies the hits to the device, estimates
  * the seeds (kf_make_seeds), fits (kf_fit) and copies the results back.  The
  * tracks are split into n_chunks ranges processed alternately on two internal

@@ -147,6 +147,10 @@ def lib():
             L.or_ckf_tracks.argtypes = [C.POINTER(FitCfg), C.POINTER(CkfCfg), C.POINTER(Surf), C.c_int,
                                         C.POINTER(Layer), C.c_int, C.c_int, _F, _I32, _I32, _D, _D, _D, _I32,
                                         _U32, C.c_void_p]
+            L.or_refit_tracks.restype = None
+            L.or_refit_tracks.argtypes = [C.POINTER(FitCfg), C.POINTER(Surf), C.c_int, C.c_int, _I32, C.c_void_p,
+                                          _F, _F, _F, _D, _D, C.c_double, C.POINTER(C.c_int8), _I32, _D, _D, _D,
+                                          _I32, _U32]
             _lib = L
     return _lib
 
@@ -436,4 +440,40 @@ def build_ckf(geom, event, n_slots=4, nsigma=3.0, chi2_cut=30.0, max_cand=32, se
 
     _run_ranges(run, t0, t1, threads)
     del keep
+    return out
+
+
+def refit_inward(geom, hits, fwd_state, fwd_cov, q, fwd_ndof, cov_scale=100.0, seed_cov=1e4, ms_on=True, t0=0,
+                 t1=None, threads=1):
+    """Outward-inward refit: the hits each forward fit used ((ndof + 5) / 2 of them) fitted
+    again from the last back to the first, starting from the forward state at the last used
+    hit with the forward covariance times cov_scale (fwd_state (n, 6), fwd_cov (n, 6, 6),
+    q (n,), fwd_ndof (n,)).  Returns the state (n, 6) and cov (n, 6, 6) at the first hit,
+    chi2, ndof, status."""
+    cfg = fit_cfg(geom, seed_cov, ms_on)
+    sarr = surfaces(geom)
+    off = np.ascontiguousarray(hits["offsets"], dtype=np.int32)
+    n = len(off) - 1
+    if t1 is None:
+        t1 = n
+    layer = np.ascontiguousarray(hits["layer"], dtype=np.uint8)
+    x, y, z = (np.ascontiguousarray(hits[k], dtype=np.float32) for k in ("x", "y", "z"))
+    fwd = np.ascontiguousarray(fwd_state, dtype=np.float64).reshape(n, 6)
+    fcv = np.ascontiguousarray(fwd_cov, dtype=np.float64).reshape(n, 36)
+    qi = np.ascontiguousarray(q, dtype=np.int8)
+    nd = np.ascontiguousarray(fwd_ndof, dtype=np.int32)
+    out = dict(state=np.zeros((n, 6)), cov=np.zeros((n, 6, 6)), chi2=np.zeros(n), ndof=np.zeros(n, np.int32),
+               status=np.zeros(n, np.uint32))
+    L = lib()
+
+    def run(a, b):
+        L.or_refit_tracks(C.byref(cfg), sarr, int(a), int(b), _p(off, C.c_int32),
+                          layer.ctypes.data if len(layer) else None, _p(x, C.c_float), _p(y, C.c_float),
+                          _p(z, C.c_float), _p(fwd, C.c_double), _p(fcv, C.c_double), float(cov_scale),
+                          _p(qi, C.c_int8), _p(nd, C.c_int32),
+                          _p(out["state"], C.c_double),
+                          _p(out["cov"], C.c_double), _p(out["chi2"], C.c_double), _p(out["ndof"], C.c_int32),
+                          _p(out["status"], C.c_uint32))
+
+    _run_ranges(run, t0, t1, threads)
     return out

@@ -271,7 +271,7 @@ int kf_make_seeds(kf_ctx *ctx, const kf_geometry *geom, int32_t n, const kf_trac
 
 static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
                     const kf_seeds *seeds, const kf_track_hits *hits, const kf_tracks_out *out, void *stream,
-                    const Tuned *force)
+                    const Tuned *force, const double *p0 = nullptr, double p0_scale = 1.0)
 {
     if (!ctx) return KF_EINVAL;
     if (n < 0 || !seeds || !hits || !out) return fail(ctx, KF_EINVAL, "n >= 0, seeds, hits and out are required");
@@ -315,6 +315,8 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     a.o_chi2 = out->chi2;
     a.o_ndof = out->ndof;
     a.o_status = out->status;
+    a.p0 = p0;
+    a.p0_scale = p0_scale;
     const bool fp64 = P.precision == KF_PREC_FP64;
     // processing order (both schedules): tracks bucketed by hit count and seed 1/pT
     const size_t nhist = order_scratch_ints();
@@ -387,6 +389,80 @@ int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, in
            const kf_track_hits *hits, const kf_tracks_out *out, void *stream)
 {
     return fit_impl(ctx, geom, params, n, seeds, hits, out, stream, nullptr);
+}
+
+int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
+                    const kf_track_hits *hits, const double *fwd_state, const double *fwd_cov, const int8_t *q,
+                    const int32_t *fwd_ndof, double cov_scale, const kf_tracks_out *out, void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (n < 0 || !hits || !out) return fail(ctx, KF_EINVAL, "n >= 0, hits and out are required");
+    kf_fit_params P;
+    int rc = check_fit_params(ctx, params, P);
+    if (rc) return rc;
+    Geom G;
+    if ((rc = to_geom(ctx, geom, G))) return rc;
+    if ((rc = set_dev(ctx))) return rc;
+    if (n == 0) return KF_OK;
+    NEED_DEV(hits->offsets, "hits.offsets");
+    NEED_DEV(hits->layer, "hits.layer");
+    NEED_DEV(hits->x, "hits.x");
+    NEED_DEV(hits->y, "hits.y");
+    NEED_DEV(hits->z, "hits.z");
+    NEED_DEV(fwd_state, "fwd_state");
+    NEED_DEV(q, "q");
+    NEED_DEV(fwd_ndof, "fwd_ndof");
+    NEED_DEV(fwd_cov, "fwd_cov");
+    if (!(cov_scale > 0)) return fail(ctx, KF_EINVAL, "cov_scale must be > 0");
+    OPT_DEV(out->state, "out.state");
+    OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->chi2, "out.chi2");
+    OPT_DEV(out->ndof, "out.ndof");
+    OPT_DEV(out->status, "out.status");
+    int32_t nh = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&nh, hits->offsets + n, sizeof nh, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading offsets[n]");
+    if (nh < 0) return fail(ctx, KF_EINVAL, "offsets[n] < 0");
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_l = 0, o_x = o_l + al((size_t)nh), o_y = o_x + al(4 * (size_t)nh), o_z = o_y + al(4 * (size_t)nh),
+                 o_s = o_z + al(4 * (size_t)nh), o_q = o_s + al(24 * (size_t)n), o_c = o_q + al((size_t)n),
+                 o_r = o_c + al(4 * (size_t)n), o_b = o_r + al(4 * ((size_t)n + 1)),
+                 o_v = o_b + al(4 * ((size_t)n / 1024 + 2)), total = o_v + al(168 * (size_t)n);
+    // the reversed copies sit in a scratch buffer of their own: kf_fit takes the
+    // stream's workspace for its order pass
+    void *buf = nullptr;
+    if (cudaMallocAsync(&buf, total, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KF_ENOMEM, "refit scratch of %zu bytes", total);
+    }
+    char *b = static_cast<char *>(buf);
+    uint8_t *rl = reinterpret_cast<uint8_t *>(b + o_l);
+    float *rx = reinterpret_cast<float *>(b + o_x), *ry = reinterpret_cast<float *>(b + o_y),
+          *rz = reinterpret_cast<float *>(b + o_z), *seed = reinterpret_cast<float *>(b + o_s);
+    int8_t *rq = reinterpret_cast<int8_t *>(b + o_q);
+    int32_t *cnt = reinterpret_cast<int32_t *>(b + o_c), *roff = reinterpret_cast<int32_t *>(b + o_r),
+            *bsum = reinterpret_cast<int32_t *>(b + o_b);
+    double *rcov = reinterpret_cast<double *>(b + o_v);
+    e = launch_used_counts(n, hits->offsets, fwd_ndof, cnt, st);
+    if (e == cudaSuccess) e = launch_scan_counts(n, cnt, roff, bsum, st);
+    if (e == cudaSuccess)
+        e = launch_reverse(n, hits->offsets, roff, hits->layer, hits->x, hits->y, hits->z, fwd_state, fwd_cov, q, rl,
+                           rx, ry, rz, seed, rcov, rq, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(buf, st);
+        return cuda_fail(ctx, e, "reversing the tracks");
+    }
+    const kf_seeds S{seed, rq};
+    const kf_track_hits H{roff, rl, rx, ry, rz};
+    rc = fit_impl(ctx, geom, &P, n, &S, &H, out, stream, nullptr, rcov, cov_scale);
+    if (rc == KF_OK) {
+        e = launch_unreverse(n, out->state, out->cov, st);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "turning the results back");
+    }
+    cudaFreeAsync(buf, st);
+    return rc;
 }
 
 static bool is_host_ptr(const void *p)

@@ -1089,6 +1089,16 @@ __global__ void gather_fill_kernel(int n, int n_events, int n_layers, const Laye
 
 size_t gather_scratch_bytes(int n) { return ((size_t)n + (size_t)(n / 1024 + 2)) * sizeof(int32_t) + 256; }
 
+cudaError_t launch_scan_counts(int n, const int32_t *cnt, int32_t *off_out, int32_t *bsum, cudaStream_t st)
+{
+    if (n <= 0) return cudaMemsetAsync(off_out, 0, sizeof(int32_t), st);
+    const int nb = (n + 1023) / 1024;
+    block_scan_kernel<<<nb, 1024, 0, st>>>(n, cnt, off_out, bsum);
+    bsum_scan_kernel<<<1, 32, 0, st>>>(nb, bsum);
+    add_bsum_kernel<<<nb, 1024, 0, st>>>(n, off_out, bsum, nb);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(int n, int n_events, int n_layers, const LayerDev *layers, const int32_t *event_off,
                           const float *seed_hits, const int32_t *hit_idx, int32_t *off_out, uint8_t *layer_out,
                           float *x_out, float *y_out, float *z_out, void *scratch, cudaStream_t st)

@@ -10,6 +10,8 @@
 
 namespace kfd {
 
+constexpr double PI_D_FIT = 3.14159265358979323846;
+
 template <bool B, class X, class Y> struct sel { using type = X; };
 template <class X, class Y> struct sel<false, X, Y> { using type = Y; };
 
@@ -207,6 +209,40 @@ static __device__ __noinline__ MixedIO fp64_step_out_of_line(MixedIO m, int k, d
     return m;
 }
 
+// A near-tangent crossing inside the FP64 phase (the covariance already FP64):
+// the propagation in FP64 too, out of line.  A track fitted inwards meets its
+// near-tangent crossings first, while the seed covariance is still large.
+struct MixedIOD {
+    Track<float, ff> st;
+    double p[21];
+    double chi2;
+    unsigned status;
+    int ok;
+};
+
+static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int k, double alpha, double mass2,
+                                                                 int ms_on, const Surf *sf, float hx, float hy,
+                                                                 float hz)
+{
+    Track<double, double> sd;
+    sd.x = to_d(m.st.x);
+    sd.y = to_d(m.st.y);
+    sd.z = to_d(m.st.z);
+    sd.phi = to_d(m.st.phi);
+    sd.ip = m.st.ip;
+    sd.th = to_d(m.st.th);
+    m.ok = fit_step<true, double>(sd, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
+    if (m.ok) {
+        m.st.x = ff_from_d(sd.x);
+        m.st.y = ff_from_d(sd.y);
+        m.st.z = ff_from_d(sd.z);
+        m.st.phi = ff_from_d(sd.phi);
+        m.st.ip = (float)sd.ip;
+        m.st.th = ff_from_d(sd.th);
+    }
+    return m;
+}
+
 template <class C>
 __device__ __forceinline__ void store_cov(double *o_cov, int n, int t, const C p[21])
 {
@@ -238,10 +274,15 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
     int used = 0, k = 0;
     bool alive = true;
     double pd[21];
+    if (a.p0) {
 #pragma unroll
-    for (int i = 0; i < 21; ++i) pd[i] = 0.0;
+        for (int i = 0; i < 21; ++i) pd[i] = a.p0_scale * a.p0[(size_t)i * n + t];
+    } else {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
+        for (int i = 0; i < 21; ++i) pd[i] = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
+    }
     // phase 1: the first n64 updates with an FP64 covariance, Joseph form, and
     // at least until the third seed hit (the seed-hit rule) has been used: a
     // disk/barrel overlap can put two of the first hits a fraction of a mm
@@ -258,7 +299,10 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         T cphi, sphi;
         sincos_pos(st.phi, sphi, cphi);
         if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
-        if (kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)) {
+        // the structured update needs the diagonal seed covariance; a given one takes the general form
+        const bool ok0 = a.p0 ? kf_update<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)
+                              : kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
+        if (ok0) {
             ++used;
             k = 1;
         } else {
@@ -268,8 +312,32 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
     }
     for (; alive && k < n1; ++k) {
         const int h = o0 + k;
-        if (!fit_step<true, double>(st, pd, k, alpha, mass2, a.ms_on, surf[a.layer[h]], a.hx[h], a.hy[h], a.hz[h],
-                                    chi2, status)) {
+        const Surf &sf = surf[a.layer[h]];
+        bool ok;
+        if constexpr (!FP64) {
+            if (grazing_crossing(st, alpha, sf)) {
+                MixedIOD m;
+                m.st = st;
+#pragma unroll
+                for (int i = 0; i < 21; ++i) m.p[i] = pd[i];
+                m.chi2 = chi2;
+                m.status = status;
+                m = fp64_step_pd_out_of_line(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
+                                             a.hz[h]);
+                st = m.st;
+#pragma unroll
+                for (int i = 0; i < 21; ++i) pd[i] = m.p[i];
+                chi2 = m.chi2;
+                status = m.status;
+                ok = m.ok != 0;
+            } else {
+                ok = fit_step<true, double>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
+                                            status);
+            }
+        } else {
+            ok = fit_step<true, double>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2, status);
+        }
+        if (!ok) {
             alive = false;
             break;
         }
@@ -355,6 +423,108 @@ __global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const Geom g, con
             fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
         }
     }
+}
+
+// ------------------------------------------------------------------ outward-inward refit
+// The track is run backwards by reversing its direction of motion, the same
+// helix traversed the other way: phi -> phi + pi, theta -> pi - theta, q -> -q
+// (1/pT and the position unchanged; the theta row and column of the
+// covariance change sign); the reversed list of the hits the forward fit used
+// is then fitted from the forward state with the inflated forward covariance,
+// and the result at the first hit is turned back.
+
+// hits the forward fit used: the first (ndof + 5) / 2 of the track
+__global__ void used_counts_kernel(int n, const int32_t *__restrict__ off, const int32_t *__restrict__ ndof,
+                                   int32_t *__restrict__ cnt)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int nh = off[t + 1] - off[t];
+    cnt[t] = min(max((ndof[t] + 5) / 2, 0), nh);
+}
+
+__global__ void reverse_hits_kernel(int n, const int32_t *__restrict__ off, const int32_t *__restrict__ roff,
+                                    const uint8_t *__restrict__ layer, const float *__restrict__ x,
+                                    const float *__restrict__ y, const float *__restrict__ z, uint8_t *__restrict__ rl,
+                                    float *__restrict__ rx, float *__restrict__ ry, float *__restrict__ rz)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int o = off[t], ro = roff[t], m = roff[t + 1] - ro;  // m <= the track's hit count
+    for (int k = 0; k < m; ++k) {
+        const int s = o + m - 1 - k;
+        rl[ro + k] = layer[s];
+        rx[ro + k] = x[s];
+        ry[ro + k] = y[s];
+        rz[ro + k] = z[s];
+    }
+}
+
+__device__ __forceinline__ double reverse_phi(double p)
+{
+    const double r = p + PI_D_FIT;
+    return r > PI_D_FIT ? r - 2.0 * PI_D_FIT : r;
+}
+
+__global__ void reverse_seed_kernel(int n, const double *__restrict__ fwd, const double *__restrict__ fwd_cov,
+                                    const int8_t *__restrict__ q, float *__restrict__ seed, double *__restrict__ rcov,
+                                    int8_t *__restrict__ rq)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            const double v = fwd_cov[(size_t)pk(i, j) * n + t];
+            rcov[(size_t)pk(i, j) * n + t] = (i == 5) != (j == 5) ? -v : v;
+        }
+    seed[0 * (size_t)n + t] = (float)fwd[0 * (size_t)n + t];
+    seed[1 * (size_t)n + t] = (float)fwd[1 * (size_t)n + t];
+    seed[2 * (size_t)n + t] = (float)fwd[2 * (size_t)n + t];
+    seed[3 * (size_t)n + t] = (float)fwd[3 * (size_t)n + t];
+    seed[4 * (size_t)n + t] = (float)reverse_phi(fwd[4 * (size_t)n + t]);
+    seed[5 * (size_t)n + t] = (float)(PI_D_FIT - fwd[5 * (size_t)n + t]);
+    rq[t] = (int8_t)(-q[t]);
+}
+
+__global__ void unreverse_kernel(int n, double *__restrict__ st, double *__restrict__ cov)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    if (st) {
+        const double p = st[4 * (size_t)n + t] - PI_D_FIT;
+        st[4 * (size_t)n + t] = p <= -PI_D_FIT ? p + 2.0 * PI_D_FIT : p;
+        st[5 * (size_t)n + t] = PI_D_FIT - st[5 * (size_t)n + t];
+    }
+    if (cov)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) cov[(size_t)pk(5, j) * n + t] = -cov[(size_t)pk(5, j) * n + t];
+}
+
+cudaError_t launch_used_counts(int n, const int32_t *off, const int32_t *fwd_ndof, int32_t *cnt, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    used_counts_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, off, fwd_ndof, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reverse(int n, const int32_t *off, const int32_t *roff, const uint8_t *layer, const float *x,
+                           const float *y, const float *z, const double *fwd, const double *fwd_cov, const int8_t *q,
+                           uint8_t *rl, float *rx, float *ry, float *rz, float *seed, double *rcov, int8_t *rq,
+                           cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    reverse_hits_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, off, roff, layer, x, y, z, rl, rx, ry, rz);
+    reverse_seed_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, fwd, fwd_cov, q, seed, rcov, rq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unreverse(int n, double *state, double *cov, cudaStream_t st)
+{
+    if (n <= 0 || (!state && !cov)) return cudaSuccess;
+    unreverse_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, state, cov);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cudaStream_t st)

@@ -31,6 +31,9 @@ struct FitArgs {
     int32_t *queue;        // work counter, zeroed before the launch
     int chunk;             // tracks per thread per queue grab (a block takes blockDim * chunk)
     int pad2_;
+    // initial covariance: p0_scale * p0 ([21][n] FP64) instead of seed_cov * I when p0 is set
+    const double *p0;
+    double p0_scale;
 };
 
 // kf_fit.cu
@@ -42,6 +45,17 @@ int persistent_blocks_per_sm(bool fp64, int block);
 size_t order_scratch_ints();
 cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, int32_t *hist, int32_t *order,
                          cudaStream_t st);
+
+// outward-inward refit (kf_fit.cu): cnt[t] = hits the forward fit used, then
+// (after an exclusive scan of cnt into roff) those hits reversed into roff's CSR
+cudaError_t launch_used_counts(int n, const int32_t *off, const int32_t *fwd_ndof, int32_t *cnt, cudaStream_t st);
+cudaError_t launch_reverse(int n, const int32_t *off, const int32_t *roff, const uint8_t *layer, const float *x,
+                           const float *y, const float *z, const double *fwd, const double *fwd_cov, const int8_t *q,
+                           uint8_t *rl, float *rx, float *ry, float *rz, float *seed, double *rcov, int8_t *rq,
+                           cudaStream_t st);
+// exclusive scan of n counts into off_out[0..n] (kf_build.cu); bsum: n / 1024 + 2 ints
+cudaError_t launch_scan_counts(int n, const int32_t *cnt, int32_t *off_out, int32_t *bsum, cudaStream_t st);
+cudaError_t launch_unreverse(int n, double *state, double *cov, cudaStream_t st);
 
 // kf_bin.cu
 size_t bin_scratch_bytes(int n_hits);

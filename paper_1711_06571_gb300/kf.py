@@ -130,6 +130,9 @@ _SIGS = {
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "kf_fit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
                          C.POINTER(kf_seeds), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out), C.c_void_p]),
+    "kf_refit_inward": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
+                                  C.POINTER(kf_track_hits), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_double, C.POINTER(kf_tracks_out), C.c_void_p]),
     "kf_fit_host": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
                               C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out), C.c_int32]),
     "kf_autotune_fit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
@@ -269,6 +272,17 @@ def kf_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, ou
     o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
     _check(ctx, load().kf_fit(ctx, C.byref(g), C.byref(p), int(n), C.byref(s), C.byref(h), C.byref(o),
                               _stream(stream)))
+
+
+def kf_refit_inward(ctx, geom, params, n, offsets, layer, x, y, z, fwd_state, fwd_cov, q, fwd_ndof, cov_scale=100.0,
+                    out_state=None, out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None):
+    g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
+    p = params if params is not None else fit_params()
+    h = kf_track_hits(_ptr(offsets), _ptr(layer), _ptr(x), _ptr(y), _ptr(z))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    _check(ctx, load().kf_refit_inward(ctx, C.byref(g), C.byref(p), int(n), C.byref(h), _ptr(fwd_state),
+                                       _ptr(fwd_cov), _ptr(q), _ptr(fwd_ndof), float(cov_scale), C.byref(o),
+                                       _stream(stream)))
 
 
 def _hptr(t):

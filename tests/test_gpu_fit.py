@@ -182,3 +182,45 @@ def test_fit_parity_million_tracks_sampled(ctx, oracle_mod):
     # every track: finite, status clean except the documented ones
     bad = (gpu["status"] & ST_BAD) != 0
     assert bad.mean() < 1e-3
+
+
+def _gpu_fit_and_refit(ctx, g, tk, precision):
+    gg = kf.make_geometry(g)
+    dh = run.hits_to_device(tk)
+    seeds = run.make_seeds(ctx, gg, dh)
+    fw = run.alloc_fit_out(dh["n"])
+    run.fit(ctx, gg, dh, seeds, fw, precision=precision)
+    bw = run.alloc_fit_out(dh["n"])
+    kf.kf_refit_inward(ctx, gg, kf.fit_params(precision=precision), dh["n"], dh["offsets"], dh["layer"], dh["x"],
+                       dh["y"], dh["z"], fw["state"], fw["cov"], seeds[1], fw["ndof"], 100.0, bw["state"],
+                       bw["cov"], bw["chi2"], bw["ndof"], bw["status"])
+    torch.cuda.synchronize()
+    return dict(state=bw["state"].t().cpu().numpy(), cov=run.unpack_cov(bw["cov"].cpu().numpy()),
+                chi2=bw["chi2"].cpu().numpy(), ndof=bw["ndof"].cpu().numpy(),
+                status=bw["status"].cpu().numpy().astype(np.uint32), q=seeds[1].cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", [kf.KF_PREC_MIXED, kf.KF_PREC_FP64])
+@pytest.mark.parametrize("name", ["barrel10", "barrel17"])
+def test_refit_inward_parity(ctx, oracle_mod, name, precision):
+    """Outward-inward refit: the state and covariance at the first hit, the chi2
+    and ndof of the backward pass, against the oracle's refit (each side seeded
+    with its own forward fit)."""
+    g = synth.geometry(name)
+    tk = synth.gen_tracks(g, 3000, synth.BASE_SEED + 12)
+    fw = oracle_mod.fit(g, tk)
+    orc = oracle_mod.refit_inward(g, tk, fw["state"], fw["cov"], fw["q"], fw["ndof"])
+    orc["q"] = fw["q"]
+    gpu = _gpu_fit_and_refit(ctx, g, tk, precision)
+    diff = np.nonzero((gpu["status"] & ST_BAD) != (orc["status"] & ST_BAD))[0]
+    assert len(diff) == 0, [(int(t), int(gpu["status"][t]), int(orc["status"][t]), int(gpu["ndof"][t]),
+                             int(orc["ndof"][t]), int(fw["ndof"][t]), int(fw["status"][t]),
+                             tk["offsets"][t + 1] - tk["offsets"][t], fw["state"][t].tolist()) for t in diff[:4]]
+    np.testing.assert_array_equal(gpu["ndof"], orc["ndof"])
+    ok = ((orc["status"] & ST_BAD) == 0) & (gpu["q"] == orc["q"])
+    res = parity.compare_fits(gpu, orc, np.zeros(tk["n"], int), ok)
+    print(f"refit {name} prec={precision}:", parity.summary(res))
+    assert ok.mean() > 0.99
+    assert res["max_pull"].max() <= parity.TOL_PARAM_SIGMA
+    assert res["chi2rel"].max() <= parity.TOL_CHI2_REL
+    assert res["dcov"].max() <= parity.TOL_COV_NORM

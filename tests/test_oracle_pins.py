@@ -650,3 +650,54 @@ def test_ckf_more_slots_recover_inefficiency(oracle_mod):
         effs.append(np.mean(ck["idx"][:, 3:][has] == where[has]))
         np.testing.assert_array_equal(ck["idx"][:, :3], ev["seed_idx"])
     assert effs[1] > effs[0], effs
+
+
+# ---------------------------------------------------------------------- outward-inward refit
+
+def test_refit_inward_noise_free_recovers_truth_at_first_hit(oracle_mod):
+    """Noise-free tracks (no smearing, no scattering): the backward fit ends on the
+    first hit with the true state there."""
+    g = synth.geometry("barrel10")
+    tk = synth.gen_tracks(g, 200, 33, ms_on=False, smear=False, keep_truth=True)
+    fw = oracle_mod.fit(g, tk, ms_on=False)
+    bw = oracle_mod.refit_inward(g, tk, fw["state"], fw["cov"], fw["q"], fw["ndof"], ms_on=False)
+    first = tk["offsets"][:-1]
+    tru = tk["truth"][first]
+    assert np.all(bw["status"] == 0)
+    sig = np.sqrt(np.diagonal(bw["cov"], axis1=1, axis2=2))
+    d = bw["state"] - tru
+    d[:, 3] = fw["q"] * bw["state"][:, 3] - tk["truth_q"] * tru[:, 3]
+    d[:, 4] = (d[:, 4] + np.pi) % (2 * np.pi) - np.pi
+    assert np.max(np.abs(d) / sig) < 0.01
+    assert np.max(bw["chi2"]) < 1e-3
+    np.testing.assert_array_equal(bw["ndof"], fw["ndof"])
+
+
+def test_refit_inward_statistics_at_first_hit(oracle_mod):
+    """Smeared hits, no scattering: the backward estimate at the first hit against
+    the true state there.  Pulls of the five surface parameters have unit width and
+    the full five-parameter chi2 (which uses the correlations, so a wrong sign in
+    the reversed covariance shows) has mean 5."""
+    import sys
+    sys.path.insert(0, HERE)
+    import parity
+    g = synth.geometry("barrel10")
+    tk = synth.gen_tracks(g, 4000, 34, ms_on=False, keep_truth=True)
+    fw = oracle_mod.fit(g, tk, ms_on=False)
+    bw = oracle_mod.refit_inward(g, tk, fw["state"], fw["cov"], fw["q"], fw["ndof"], ms_on=False)
+    ok = (fw["status"] == 0) & (bw["status"] == 0) & (fw["q"] == tk["truth_q"])
+    first = tk["offsets"][:-1]
+    tru = tk["truth"][first][ok]
+    st, C6 = bw["state"][ok], bw["cov"][ok]
+    T = parity.local_frame(tru, np.zeros(len(tru), int))
+    d = st - tru
+    d[:, 4] = (d[:, 4] + np.pi) % (2 * np.pi) - np.pi
+    dl = np.einsum("nij,nj->ni", T, d)
+    C5 = np.einsum("nai,nij,nbj->nab", T, C6, T)
+    pulls = dl / np.sqrt(np.diagonal(C5, axis1=1, axis2=2))
+    chi2 = np.einsum("ni,ni->n", dl, np.linalg.solve(C5, dl[:, :, None])[:, :, 0])
+    m = len(tru)
+    assert m > 0.9 * tk["n"]
+    np.testing.assert_allclose(pulls.std(axis=0), 1.0, atol=0.06)
+    np.testing.assert_allclose(pulls.mean(axis=0), 0.0, atol=0.06)
+    assert abs(chi2.mean() - 5.0) < 5 * np.sqrt(10.0 / m)
