@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--tracks", type=int, default=N_TRACKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
-    ap.add_argument("--part", default="all", choices=["all", "build", "serving", "uneven"],
+    ap.add_argument("--part", default="all", choices=["all", "build", "serving", "uneven", "layout"],
                     help="build / serving: only that measurement, printed as its own JSON line")
     ap.add_argument("--ref-sample", type=int, default=0,
                     help="--impl reference: tracks of the workload the oracle fits per step "
@@ -322,6 +322,36 @@ def uneven_bench(ctx, steps, warmup, n_tracks=2_000_000):
                 persistent_speedup=ms_grid / ms_pers, steps_measured=steps)
 
 
+def layout_study(ctx, sizes=(32 * 1024, 256 * 1024, 2 * 1024 * 1024, 8 * 1024 * 1024), reps=20):
+    """Sec. 4.3's layout study on GB300: the covariance transport P' = J P J^T of n
+    matrices per launch (one per thread, FP32, operands in registers), in the AOS,
+    SOA and Matriplex-like BLOCK layouts; time per launch and the bytes it moves."""
+    import torch
+    from paper_1711_06571_gb300 import kf
+    stream = torch.cuda.current_stream()
+    out = []
+    for n in sizes:
+        J = torch.randn(n * 36, device="cuda")
+        P = torch.randn(n * 21, device="cuda")
+        Po = torch.empty(n * 21, device="cuda")
+        row = dict(n=n, bytes_per_launch=n * (36 + 21 + 21) * 4)
+        for name, layout in (("aos", kf.KF_LAYOUT_AOS), ("soa", kf.KF_LAYOUT_SOA), ("block", kf.KF_LAYOUT_BLOCK)):
+            for _ in range(3):
+                kf.kf_layout_transport(ctx, layout, n, J, P, Po)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                kf.kf_layout_transport(ctx, layout, n, J, P, Po)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            row[name] = dict(ms=ms, ns_per_matrix=ms * 1e6 / n, gb_s=row["bytes_per_launch"] / (ms * 1e-3) / 1e9)
+        out.append(row)
+        del J, P, Po
+    return dict(workload="P' = J P J^T, FP32, one matrix per thread; J 36 + P 21 floats in, 21 out", rows=out)
+
+
 SERVING_WORKLOAD = ("serving loop: Poisson arrivals, event sizes log-uniform 500-50,000 tracks (16-event pool at the "
                     "log-uniform quantiles), 17 barrel layers, 20% noise hits per layer, best-hit build + final "
                     "fit per event, 40 GB device-memory budget")
@@ -485,6 +515,8 @@ def main():
                 r = build_bench(ctx, geom, args.steps, args.warmup)
             elif args.part == "uneven":
                 r = uneven_bench(ctx, args.steps, args.warmup)
+            elif args.part == "layout":
+                r = layout_study(ctx)
             else:
                 rates = None if args.serving_rates == "auto" else [float(v) for v in args.serving_rates.split(",")]
                 r = serving_sweep(ctx, geom, rates, memory=args.serving_memory, zero_copy=not args.serving_copy)

@@ -486,6 +486,23 @@ void kf_server_destroy(kf_server *s);
 
 /* ---------------------------------------------------------------- measurement */
 
+/* Layout study (Sec. 4.3: the paper timed batched 6x6 products on a GPU for
+ * several memory layouts).  One launch of the covariance transport
+ * P' = J P J^T for n matrices, one per thread, operands in registers, FP32,
+ * with J (36 entries, row-major), P and P' (21 packed lower-triangle entries)
+ * stored in the given layout:
+ *   KF_LAYOUT_AOS    element k of matrix t at t * K + k;
+ *   KF_LAYOUT_SOA    at k * n + t (the layout of this library's kernels);
+ *   KF_LAYOUT_BLOCK  Matriplex-like blocks of 32: ((t / 32) * K + k) * 32 + t % 32
+ *                    (n a multiple of 32).
+ * J, P, P_out: device arrays of n * 36, n * 21, n * 21 floats.  Asynchronous
+ * on the stream; time it with events around the call. */
+#define KF_LAYOUT_AOS 0
+#define KF_LAYOUT_SOA 1
+#define KF_LAYOUT_BLOCK 2
+int kf_layout_transport(kf_ctx *ctx, int32_t layout, int32_t n, const float *J, const float *P, float *P_out,
+                        void *stream);
+
 /* Peak arithmetic rate of this GPU, measured (no counterpart in the paper; it
  * gives the roofline denominators of the fit): a grid of several blocks per SM
  * runs eight independent fused multiply-add chains per thread in FP64

@@ -664,6 +664,24 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     return KF_OK;
 }
 
+int kf_layout_transport(kf_ctx *ctx, int32_t layout, int32_t n, const float *J, const float *P, float *P_out,
+                        void *stream)
+{
+    if (!ctx) return KF_EINVAL;
+    if (layout != KF_LAYOUT_AOS && layout != KF_LAYOUT_SOA && layout != KF_LAYOUT_BLOCK)
+        return fail(ctx, KF_EINVAL, "layout must be KF_LAYOUT_AOS, KF_LAYOUT_SOA or KF_LAYOUT_BLOCK");
+    if (n < 0 || (layout == KF_LAYOUT_BLOCK && n % 32))
+        return fail(ctx, KF_EINVAL, "n >= 0 (a multiple of 32 for KF_LAYOUT_BLOCK)");
+    int rc = set_dev(ctx);
+    if (rc) return rc;
+    if (n == 0) return KF_OK;
+    NEED_DEV(J, "J");
+    NEED_DEV(P, "P");
+    NEED_DEV(P_out, "P_out");
+    cudaError_t e = launch_transport_layout(layout, n, J, P, P_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "layout transport kernel");
+}
+
 int kf_measure_peak(kf_ctx *ctx, int which, double *flops_per_s)
 {
     if (!ctx) return KF_EINVAL;

@@ -123,6 +123,9 @@ cudaError_t launch_gather(int n, int n_events, int n_layers, const LayerDev *lay
                           const float *seed_hits, const int32_t *hit_idx, int32_t *off_out, uint8_t *layer_out,
                           float *x_out, float *y_out, float *z_out, void *scratch, cudaStream_t st);
 
+// kf_layout.cu
+cudaError_t launch_transport_layout(int layout, int n, const float *J, const float *P, float *Po, cudaStream_t st);
+
 // kf_peak.cu
 cudaError_t measure_peak(int which, int sm_count, void *scratch, double *flops_per_s);
 

@@ -154,6 +154,8 @@ _SIGS = {
     "kf_bin_hits_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "kf_measure_peak": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "kf_layout_transport": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     "kf_gather_hits": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(kf_binned_layer),
                                  C.POINTER(C.c_int32), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -394,6 +396,15 @@ def kf_gather_hits(ctx, n_events, n_layers, layers, event_offsets, seed_hits, hi
     _check(ctx, load().kf_gather_hits(ctx, int(n_events), int(n_layers), layers, eo, _ptr(seed_hits),
                                       _ptr(hit_idx), _ptr(offsets_out), _ptr(layer_out), _ptr(x_out), _ptr(y_out),
                                       _ptr(z_out), _stream(stream)))
+
+
+KF_LAYOUT_AOS = 0
+KF_LAYOUT_SOA = 1
+KF_LAYOUT_BLOCK = 2
+
+
+def kf_layout_transport(ctx, layout, n, J, P, P_out, stream=None):
+    _check(ctx, load().kf_layout_transport(ctx, int(layout), int(n), _ptr(J), _ptr(P), _ptr(P_out), _stream(stream)))
 
 
 def kf_measure_peak(ctx, which: int) -> float:

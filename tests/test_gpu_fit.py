@@ -224,3 +224,50 @@ def test_refit_inward_parity(ctx, oracle_mod, name, precision):
     assert res["max_pull"].max() <= parity.TOL_PARAM_SIGMA
     assert res["chi2rel"].max() <= parity.TOL_CHI2_REL
     assert res["dcov"].max() <= parity.TOL_COV_NORM
+
+
+def _to_layout(a, layout):
+    """(n, K) matrices -> the flat array of a layout (see kf_layout_transport)."""
+    n, K = a.shape
+    if layout == kf.KF_LAYOUT_AOS:
+        return np.ascontiguousarray(a).reshape(-1)
+    if layout == kf.KF_LAYOUT_SOA:
+        return np.ascontiguousarray(a.T).reshape(-1)
+    return np.ascontiguousarray(a.reshape(n // 32, 32, K).transpose(0, 2, 1)).reshape(-1)
+
+
+def _from_layout(f, n, K, layout):
+    if layout == kf.KF_LAYOUT_AOS:
+        return f.reshape(n, K)
+    if layout == kf.KF_LAYOUT_SOA:
+        return f.reshape(K, n).T
+    return f.reshape(n // 32, K, 32).transpose(0, 2, 1).reshape(n, K)
+
+
+def test_layout_transport_matches_oracle(ctx, oracle_mod):
+    """The layout study's kernel computes J P J^T in every layout; checked against
+    the oracle's dense FP64 transport."""
+    rng = np.random.default_rng(5)
+    n = 4096
+    J = rng.normal(size=(n, 36)).astype(np.float32)
+    A = rng.normal(size=(n, 6, 6))
+    P6 = A @ A.transpose(0, 2, 1)
+    tril = np.tril_indices(6)
+    P = P6[:, tril[0], tril[1]].astype(np.float32)
+    ref = np.zeros((n, 21))
+    for t in range(0, n, 97):
+        Pn = oracle_mod.transport(J[t].astype(np.float64), P6[t].astype(np.float32).astype(np.float64).reshape(36))
+        ref[t] = Pn.reshape(6, 6)[tril]
+    outs = []
+    for layout in (kf.KF_LAYOUT_AOS, kf.KF_LAYOUT_SOA, kf.KF_LAYOUT_BLOCK):
+        dJ = torch.from_numpy(_to_layout(J, layout)).cuda()
+        dP = torch.from_numpy(_to_layout(P, layout)).cuda()
+        dO = torch.empty(n * 21, dtype=torch.float32, device="cuda")
+        kf.kf_layout_transport(ctx, layout, n, dJ, dP, dO)
+        torch.cuda.synchronize()
+        outs.append(_from_layout(dO.cpu().numpy(), n, 21, layout))
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    sel = np.arange(0, n, 97)
+    scale = np.abs(ref[sel]).max(axis=1, keepdims=True)
+    assert np.max(np.abs(outs[0][sel] - ref[sel]) / scale) < 1e-5
