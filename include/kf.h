@@ -80,7 +80,10 @@ typedef struct kf_ctx kf_ctx;
  * kind 1: disk z = pos, half_or_rin <= r <= r_out.
  * x_x0: thickness in radiation lengths at normal incidence.
  * sig_n: hit resolution along the surface normal; sig_rphi: along phi-hat;
- * sig_3: along z (barrel) or r (disk), all in cm. */
+ * sig_3: along z (barrel) or r (disk), all in cm.
+ * dr: barrel, radial half-extent of the layer's modules (a non-ideal layer whose
+ * hits lie within pos +- dr, Sec. 4.1); 0 for an ideal cylinder.  Read by the
+ * building window under measurement model 1. */
 typedef struct {
     int32_t kind;
     int32_t pad_;
@@ -91,6 +94,7 @@ typedef struct {
     double sig_n;
     double sig_rphi;
     double sig_3;
+    double dr;
 } kf_surface;
 
 /* Detector and field.  surfaces: host array of n_surfaces (<= KF_MAX_SURFACES). */

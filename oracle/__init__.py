@@ -50,12 +50,12 @@ def build_lib(force: bool = False) -> str:
 class Surf(C.Structure):
     _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("pos", C.c_double),
                 ("half_or_rin", C.c_double), ("r_out", C.c_double), ("x_x0", C.c_double),
-                ("sig_n", C.c_double), ("sig_rphi", C.c_double), ("sig_3", C.c_double)]
+                ("sig_n", C.c_double), ("sig_rphi", C.c_double), ("sig_3", C.c_double), ("dr", C.c_double)]
 
 
 class FitCfg(C.Structure):
     _fields_ = [("bz", C.c_double), ("mass", C.c_double), ("seed_cov", C.c_double),
-                ("ms_on", C.c_int32), ("pad_", C.c_int32)]
+                ("ms_on", C.c_int32), ("meas_model", C.c_int32)]
 
 
 class BuildCfg(C.Structure):
@@ -147,6 +147,8 @@ def lib():
             L.or_ckf_tracks.argtypes = [C.POINTER(FitCfg), C.POINTER(CkfCfg), C.POINTER(Surf), C.c_int,
                                         C.POINTER(Layer), C.c_int, C.c_int, _F, _I32, _I32, _D, _D, _D, _I32,
                                         _U32, C.c_void_p]
+            L.or_update2d.restype = C.c_int
+            L.or_update2d.argtypes = [_D, _D, _D, C.POINTER(Surf), _D]
             L.or_refit_tracks.restype = None
             L.or_refit_tracks.argtypes = [C.POINTER(FitCfg), C.POINTER(Surf), C.c_int, C.c_int, _I32, C.c_void_p,
                                           _F, _F, _F, _D, _D, C.c_double, C.POINTER(C.c_int8), _I32, _D, _D, _D,
@@ -171,11 +173,13 @@ def surfaces(geom) -> "C.Array":
         arr[i].sig_n = float(s["sig_n"])
         arr[i].sig_rphi = float(s["sig_rphi"])
         arr[i].sig_3 = float(s["sig_3"])
+        arr[i].dr = float(s.get("dr", 0.0))
     return arr
 
 
-def fit_cfg(geom, seed_cov=1e4, ms_on=True) -> FitCfg:
-    return FitCfg(bz=float(geom["bz"]), mass=float(geom["mass"]), seed_cov=float(seed_cov), ms_on=int(bool(ms_on)))
+def fit_cfg(geom, seed_cov=1e4, ms_on=True, meas_model=0) -> FitCfg:
+    return FitCfg(bz=float(geom["bz"]), mass=float(geom["mass"]), seed_cov=float(seed_cov), ms_on=int(bool(ms_on)),
+                  meas_model=int(meas_model))
 
 
 # ---------------------------------------------------------------- single-step helpers (pins)
@@ -238,6 +242,17 @@ def update(st, P, hit, R):
     return rc, st, P, chi2.value
 
 
+def update2d(st, P, hit, surf):
+    """Measurement-model-1 update (2-D, tangent plane at the hit azimuth)."""
+    st = np.ascontiguousarray(st, dtype=np.float64).copy()
+    P = np.ascontiguousarray(P, dtype=np.float64).reshape(36).copy()
+    hit = np.ascontiguousarray(hit, dtype=np.float64)
+    chi2 = np.zeros(1)
+    sarr = surfaces({"surfaces": [surf]})
+    rc = lib().or_update2d(_p(st, C.c_double), _p(P, C.c_double), _p(hit, C.c_double), sarr, _p(chi2, C.c_double))
+    return rc, st, P.reshape(6, 6), float(chi2[0])
+
+
 def transport(J, P):
     J = np.ascontiguousarray(J, dtype=np.float64)
     P = np.ascontiguousarray(P, dtype=np.float64).copy()
@@ -286,10 +301,11 @@ def fit_one(geom, layer, hx, hy, hz, seed_state, q, seed_cov=1e4, ms_on=True, li
 
 # ---------------------------------------------------------------- batched entry points
 
-def fit(geom, hits, seeds=None, q=None, seed_cov=1e4, ms_on=True, t0=0, t1=None, threads=1):
+def fit(geom, hits, seeds=None, q=None, seed_cov=1e4, ms_on=True, t0=0, t1=None, threads=1, meas_model=0):
     """Fit every track of a CSR hit set.  hits: dict offsets (n+1,), layer, x, y, z.
+    meas_model 1: barrel hits on their own radius, 2-D update (non-ideal geometry).
     Returns dict with seed, q, state (n,6), cov (n,6,6), chi2, ndof, status."""
-    cfg = fit_cfg(geom, seed_cov, ms_on)
+    cfg = fit_cfg(geom, seed_cov, ms_on, meas_model)
     sarr = surfaces(geom)
     off = np.ascontiguousarray(hits["offsets"], dtype=np.int32)
     n = len(off) - 1
@@ -349,10 +365,11 @@ def bin_layer(x, y, z, half_len):
 
 
 def build_besthit(geom, event, nsigma=3.0, chi2_cut=30.0, max_cand=32, seed_cov=1e4, ms_on=True, t0=0, t1=None,
-          record=False, threads=1):
+          record=False, threads=1, meas_model=0):
     """Best-hit building of one event.  event: dict with 'layers' (list of dicts x, y, z, perm, offsets,
-    surf), 'seed_hits' (n,3,3) float32, 'seed_idx' (n,3) int32."""
-    fc = fit_cfg(geom, seed_cov, ms_on)
+    surf), 'seed_hits' (n,3,3) float32, 'seed_idx' (n,3) int32.  meas_model 1: two-step
+    propagation (layer average cylinder, then each candidate's own) and 2-D updates."""
+    fc = fit_cfg(geom, seed_cov, ms_on, meas_model)
     bc = BuildCfg(nsigma=float(nsigma), chi2_cut=float(chi2_cut), max_cand=int(min(max_cand, 1024)))
     sarr = surfaces(geom)
     lays = event["layers"]
@@ -444,13 +461,13 @@ def build_ckf(geom, event, n_slots=4, nsigma=3.0, chi2_cut=30.0, max_cand=32, se
 
 
 def refit_inward(geom, hits, fwd_state, fwd_cov, q, fwd_ndof, cov_scale=100.0, seed_cov=1e4, ms_on=True, t0=0,
-                 t1=None, threads=1):
+                 t1=None, threads=1, meas_model=0):
     """Outward-inward refit: the hits each forward fit used ((ndof + 5) / 2 of them) fitted
     again from the last back to the first, starting from the forward state at the last used
     hit with the forward covariance times cov_scale (fwd_state (n, 6), fwd_cov (n, 6, 6),
     q (n,), fwd_ndof (n,)).  Returns the state (n, 6) and cov (n, 6, 6) at the first hit,
     chi2, ndof, status."""
-    cfg = fit_cfg(geom, seed_cov, ms_on)
+    cfg = fit_cfg(geom, seed_cov, ms_on, meas_model)
     sarr = surfaces(geom)
     off = np.ascontiguousarray(hits["offsets"], dtype=np.int32)
     n = len(off) - 1

@@ -57,6 +57,7 @@ typedef struct {
     double sig_n;
     double sig_rphi;
     double sig_3;
+    double dr; /* barrel: radial half-extent of the layer's modules (0: a cylinder) */
 } or_surf;
 
 /* ------------------------------------------------------------------ */
@@ -573,8 +574,97 @@ typedef struct {
     double mass;
     double seed_cov; /* seed covariance = seed_cov * I6 */
     int32_t ms_on;   /* add multiple-scattering noise */
-    int32_t pad_;
+    int32_t meas_model; /* 0: 3-D hit on the layer surface; 1: on the hit's own radius, 2-D (Sec. 4.1) */
 } or_fit_cfg;
+
+/* ------------------------------------------------------------------ */
+/* measurement model 1 (Sec. 4.1, non-ideal geometry): a barrel hit need  */
+/* not lie on its layer's average cylinder; the state is carried to the   */
+/* cylinder through the hit and updated on the plane tangent to it there, */
+/* with the two coordinates measured on that plane: r-phi and z.          */
+/* ------------------------------------------------------------------ */
+
+/* the cylinder through a barrel hit: the layer surface with the hit's radius */
+static or_surf hit_cylinder(const or_surf *sf, const double hit[3])
+{
+    or_surf h = *sf;
+    h.pos = sqrt(hit[0] * hit[0] + hit[1] * hit[1]);
+    return h;
+}
+
+/* 2-D update on the tangent plane at the hit azimuth: H (2x6) has rows
+ * (-sin a, cos a, 0, 0, 0, 0) and (0, 0, 1, 0, 0, 0) with a the hit azimuth,
+ * R = diag(sig_rphi^2, sig_3^2), r = H (m - x).  Joseph form, symmetrised.
+ * Returns 0 or OR_ST_CHOL_FAIL. */
+int or_update2d(double st[6], double P[36], const double hit[3], const or_surf *sf, double *chi2)
+{
+    const double rh = sqrt(hit[0] * hit[0] + hit[1] * hit[1]);
+    const double ca = hit[0] / rh, sa = hit[1] / rh;
+    double H[12] = {0}, R2[4] = {sf->sig_rphi * sf->sig_rphi, 0.0, 0.0, sf->sig_3 * sf->sig_3};
+    double r[2], HP[12], S[4], Si[4], det, K[12], M[36], MP[36], Pn[36];
+    int i, j, k;
+    H[0 * 6 + 0] = -sa;
+    H[0 * 6 + 1] = ca;
+    H[1 * 6 + 2] = 1.0;
+    r[0] = -sa * (hit[0] - st[0]) + ca * (hit[1] - st[1]);
+    r[1] = hit[2] - st[2];
+    for (i = 0; i < 2; ++i)
+        for (j = 0; j < 6; ++j) {
+            double v = 0.0;
+            for (k = 0; k < 6; ++k) v += H[i * 6 + k] * P[k * 6 + j];
+            HP[i * 6 + j] = v;
+        }
+    for (i = 0; i < 2; ++i)
+        for (j = 0; j < 2; ++j) {
+            double v = R2[i * 2 + j];
+            for (k = 0; k < 6; ++k) v += HP[i * 6 + k] * H[j * 6 + k];
+            S[i * 2 + j] = v;
+        }
+    det = S[0] * S[3] - S[1] * S[2];
+    if (!(S[0] > 0.0) || !(det > 0.0)) return (int)OR_ST_CHOL_FAIL;
+    Si[0] = S[3] / det;
+    Si[1] = -S[1] / det;
+    Si[2] = -S[2] / det;
+    Si[3] = S[0] / det;
+    *chi2 = r[0] * (Si[0] * r[0] + Si[1] * r[1]) + r[1] * (Si[2] * r[0] + Si[3] * r[1]);
+    /* K = P H^T S^-1 (6x2) */
+    for (i = 0; i < 6; ++i)
+        for (j = 0; j < 2; ++j) {
+            double v = 0.0;
+            for (k = 0; k < 2; ++k) v += HP[k * 6 + i] * Si[k * 2 + j];
+            K[i * 2 + j] = v;
+        }
+    for (i = 0; i < 6; ++i) st[i] += K[i * 2 + 0] * r[0] + K[i * 2 + 1] * r[1];
+    st[4] = wrap_phi(st[4]);
+    /* Joseph: (I - K H) P (I - K H)^T + K R K^T */
+    for (i = 0; i < 6; ++i)
+        for (j = 0; j < 6; ++j) M[i * 6 + j] = (i == j ? 1.0 : 0.0) - (K[i * 2 + 0] * H[0 * 6 + j] + K[i * 2 + 1] * H[1 * 6 + j]);
+    for (i = 0; i < 6; ++i)
+        for (j = 0; j < 6; ++j) {
+            double v = 0.0;
+            for (k = 0; k < 6; ++k) v += M[i * 6 + k] * P[k * 6 + j];
+            MP[i * 6 + j] = v;
+        }
+    for (i = 0; i < 6; ++i)
+        for (j = 0; j < 6; ++j) {
+            double v = 0.0;
+            for (k = 0; k < 6; ++k) v += MP[i * 6 + k] * M[j * 6 + k];
+            v += K[i * 2 + 0] * R2[0] * K[j * 2 + 0] + K[i * 2 + 1] * R2[3] * K[j * 2 + 1];
+            Pn[i * 6 + j] = v;
+        }
+    for (i = 0; i < 6; ++i)
+        for (j = 0; j < 6; ++j) P[i * 6 + j] = 0.5 * (Pn[i * 6 + j] + Pn[j * 6 + i]);
+    return 0;
+}
+
+/* chi2 of a hit under model 1 without updating */
+static int or_chi2_2d(const double st[6], const double P[36], const double hit[3], const or_surf *sf, double *chi2)
+{
+    double s2[6], P2[36];
+    memcpy(s2, st, sizeof s2);
+    memcpy(P2, P, sizeof P2);
+    return or_update2d(s2, P2, hit, sf, chi2);
+}
 
 /* Fit one track over its hits in path order.  The seed is placed at hit 1
  * with covariance seed_cov * I; hit 1 is used with no propagation; every
@@ -603,8 +693,10 @@ static unsigned or_fit_from(const or_fit_cfg *cfg, const or_surf *surfs, int nh,
     *chi2_sum = 0.0;
     *n_used = 0;
     for (k = 0; k < nh; ++k) {
-        const or_surf *sf = &surfs[layer[k]];
         double hit[3] = {(double)hx[k], (double)hy[k], (double)hz[k]};
+        const int m1 = cfg->meas_model == 1 && surfs[layer[k]].kind == 0;
+        const or_surf hcyl = hit_cylinder(&surfs[layer[k]], hit);
+        const or_surf *sf = m1 ? &hcyl : &surfs[layer[k]];
         double Rm[9], chi2 = 0.0;
         int rc;
         if (k > 0) {
@@ -636,8 +728,12 @@ static unsigned or_fit_from(const or_fit_cfg *cfg, const or_surf *surfs, int nh,
             or_transport(J, P);
         }
         if (cfg->ms_on) status |= (unsigned)or_ms_noise(st, cfg->mass, sf, P);
-        or_meas_cov(sf, hit, Rm);
-        rc = or_update(st, P, hit, Rm, &chi2);
+        if (m1) {
+            rc = or_update2d(st, P, hit, sf, &chi2);
+        } else {
+            or_meas_cov(sf, hit, Rm);
+            rc = or_update(st, P, hit, Rm, &chi2);
+        }
         if (rc) {
             status |= (unsigned)rc;
             break;
@@ -806,7 +902,10 @@ static int floor_clamp(double v, int lo, int hi)
  * hit in the window's bins (z ascending, phi ascending with wrap, binned
  * order; at most max_cand), keep the smallest chi2 below the cut (ties: lower
  * original index) and update with it.  idx receives the chosen original hit
- * index per layer (-1: none). */
+ * index per layer (-1: none).  Under measurement model 1 (Sec. 4.1, non-ideal
+ * geometry) the propagation takes two steps: to the layer's average cylinder
+ * (noise and window there), then from there to each candidate hit's own
+ * cylinder, where its chi2 is taken and the update made (2-D, tangent plane). */
 unsigned or_build_one(const or_fit_cfg *fc, const or_build_cfg *bc, const or_surf *surfs, int nlay,
                       const or_layer *lays, const float seed_hits[9], const int32_t seed_idx[3], int32_t *idx,
                       double st[6], double P[36], double *chi2_sum, int *ndof, or_step_rec *rec)
@@ -859,6 +958,19 @@ unsigned or_build_one(const or_fit_cfg *fc, const or_build_cfg *bc, const or_sur
         sphi2 = (yp * yp * P[0 * 6 + 0] + xp * xp * P[1 * 6 + 1] - 2.0 * xp * yp * P[0 * 6 + 1]) / (r2 * r2);
         dphi = bc->nsigma * sqrt(sphi2 + (sf->sig_rphi / R) * (sf->sig_rphi / R));
         dz = bc->nsigma * sqrt(P[2 * 6 + 2] + sf->sig_3 * sf->sig_3);
+        if (fc->meas_model == 1 && sf->dr > 0.0) {
+            /* hits lie within +-dr of the average radius: the window widens by the
+             * azimuth and z the track sweeps over that radial distance */
+            const double ca = fabs(cos(st[4] - phip)), sa = fabs(sin(st[4] - phip));
+            const double cot = cos(st[5]) / sin(st[5]);
+            if (ca > 1e-3) {
+                dphi += sf->dr * sa / (ca * R);
+                dz += sf->dr * fabs(cot) / ca;
+            } else {
+                dphi = OR_PI;
+                dz = 2.0 * Lz;
+            }
+        }
         phi_lo = (int)floor(((phip - dphi + OR_PI) * 1024.0) / (2.0 * OR_PI));
         phi_hi = (int)floor(((phip + dphi + OR_PI) * 1024.0) / (2.0 * OR_PI));
         nphi = phi_hi - phi_lo + 1;
@@ -886,12 +998,21 @@ unsigned or_build_one(const or_fit_cfg *fc, const or_build_cfg *bc, const or_sur
             double hit[3] = {(double)ly->x[h], (double)ly->y[h], (double)ly->z[h]};
             double Rm[9], S[9], r[3], c2 = -1.0;
             int a, b;
-            or_meas_cov(sf, hit, Rm);
-            for (a = 0; a < 3; ++a) {
-                r[a] = hit[a] - st[a];
-                for (b = 0; b < 3; ++b) S[a * 3 + b] = P[a * 6 + b] + Rm[a * 3 + b];
+            if (fc->meas_model == 1) {
+                /* second step: from the layer's average cylinder to the hit's own */
+                const or_surf hc = hit_cylinder(sf, hit);
+                double s2[6], P2[36], J2[36];
+                memcpy(P2, P, sizeof P2);
+                if (or_propagate(st, q, fc->bz, &hc, s2, J2) || (or_transport(J2, P2), or_chi2_2d(s2, P2, hit, &hc, &c2)))
+                    c2 = -1.0;
+            } else {
+                or_meas_cov(sf, hit, Rm);
+                for (a = 0; a < 3; ++a) {
+                    r[a] = hit[a] - st[a];
+                    for (b = 0; b < 3; ++b) S[a * 3 + b] = P[a * 6 + b] + Rm[a * 3 + b];
+                }
+                if (or_chi2(S, r, &c2)) c2 = -1.0;
             }
-            if (or_chi2(S, r, &c2)) c2 = -1.0;
             cchi[k] = c2;
             if (c2 < 0.0) continue;
             if (best < 0 || c2 < bchi || (c2 == bchi && h < best)) {
@@ -917,8 +1038,21 @@ unsigned or_build_one(const or_fit_cfg *fc, const or_build_cfg *bc, const or_sur
         if (best >= 0 && bchi < bc->chi2_cut) {
             double hit[3] = {(double)ly->x[best], (double)ly->y[best], (double)ly->z[best]};
             double Rm[9], c2;
-            or_meas_cov(sf, hit, Rm);
-            if (or_update(st, P, hit, Rm, &c2)) {
+            int urc;
+            if (fc->meas_model == 1) {
+                const or_surf hc = hit_cylinder(sf, hit);
+                double s2[6], J2[36];
+                urc = or_propagate(st, q, fc->bz, &hc, s2, J2);
+                if (!urc) {
+                    memcpy(st, s2, sizeof s2);
+                    or_transport(J2, P);
+                    urc = or_update2d(st, P, hit, &hc, &c2);
+                }
+            } else {
+                or_meas_cov(sf, hit, Rm);
+                urc = or_update(st, P, hit, Rm, &c2);
+            }
+            if (urc) {
                 status |= OR_ST_CHOL_FAIL;
                 break;
             }

@@ -52,7 +52,7 @@ class KfError(RuntimeError):
 class kf_surface(C.Structure):
     _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("pos", C.c_double), ("half_or_rin", C.c_double),
                 ("r_out", C.c_double), ("x_x0", C.c_double), ("sig_n", C.c_double), ("sig_rphi", C.c_double),
-                ("sig_3", C.c_double)]
+                ("sig_3", C.c_double), ("dr", C.c_double)]
 
 
 class kf_geometry(C.Structure):
@@ -224,6 +224,7 @@ def make_geometry(geom: dict):
         arr[i].sig_n = float(s["sig_n"])
         arr[i].sig_rphi = float(s["sig_rphi"])
         arr[i].sig_3 = float(s["sig_3"])
+        arr[i].dr = float(s.get("dr", 0.0))
     g = kf_geometry(bz=float(geom["bz"]), mass=float(geom["mass"]), n_surfaces=len(surfs),
                     surfaces=C.cast(arr, C.POINTER(kf_surface)))
     g._keep = arr

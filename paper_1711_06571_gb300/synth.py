@@ -50,11 +50,21 @@ def geometry(name: str, x_x0: float = X_X0, bz: float = BZ) -> dict:
     barrel10: 10 cylinders at R = 4, 8, ..., 40 cm (1,000-track fit).
     barrel17: 17 cylinders at R = 4 + 6 i, i = 0..16 (fit at scale, best-hit building, serving).
     lids:     barrel17 plus 2 x 12 disks at |z| = 30 + 240 j / 11, j = 0..11, r in [|z|/7 + 5, 100].
+    barrel17s: barrel17 whose layers are rings of modules at alternating radii R - 0.25 and
+              R + 0.25 cm (sectors about 10 cm wide in r-phi): a non-ideal geometry where hits
+              do not lie on the layer's average cylinder (Sec. 4.1).  The surfaces carry the
+              average radius; "stagger" and "n_mod" describe the modules for the generator.
     """
     if name == "barrel10":
         surfs = [_barrel(4.0 * (i + 1), x_x0) for i in range(10)]
     elif name == "barrel17":
         surfs = [_barrel(4.0 + 6.0 * i, x_x0) for i in range(17)]
+    elif name == "barrel17s":
+        surfs = [_barrel(4.0 + 6.0 * i, x_x0) for i in range(17)]
+        for sf in surfs:
+            sf["stagger"] = 0.25
+            sf["dr"] = 0.25  # the layer's radial half-extent, as a reconstruction sees it
+            sf["n_mod"] = max(4, 2 * int(round(math.pi * sf["pos"] / 10.0)))  # even: radii alternate
     elif name == "lids":
         surfs = [_barrel(4.0 + 6.0 * i, x_x0) for i in range(17)]
         for sgn in (1.0, -1.0):
@@ -137,6 +147,15 @@ def _disk_s(tr, idx, Z):
     return torch.where(s > 1e-9, s, torch.full_like(s, math.inf))
 
 
+def _xy_after(tr, idx, c, s):
+    """Transverse position of tracks idx after a transverse path s."""
+    x, y, phi = tr.x[idx], tr.y[idx], tr.phi[idx]
+    xc = x - torch.sin(phi) / c
+    yc = y + torch.cos(phi) / c
+    phi1 = phi + c * s
+    return xc + torch.sin(phi1) / c, yc - torch.cos(phi1) / c
+
+
 def _radius_after(tr, idx, c, s):
     x, y, phi = tr.x[idx], tr.y[idx], tr.phi[idx]
     xc = x - torch.sin(phi) / c
@@ -200,8 +219,18 @@ def gen_tracks(geom: dict, n: int, seed: int, eta_max: float = 1.0, pt_min: floa
             break
         c = tr.curv(bz)[idx]
         if barrel_only:
-            R = surfs[barrels[step]]["pos"]
+            sf = surfs[barrels[step]]
+            R = sf["pos"]
             s = _barrel_s(tr, idx, c, torch.full_like(c, R))
+            if sf.get("stagger", 0.0) > 0.0:
+                # the module the track meets: its sector from the azimuth at the average
+                # radius, its radius R -+ stagger alternating with the sector
+                fin = torch.isfinite(s)
+                xa, ya = _xy_after(tr, idx, c, torch.where(fin, s, torch.zeros_like(s)))
+                sec = torch.floor((torch.atan2(ya, xa) + math.pi) * (sf["n_mod"] / (2.0 * math.pi)))
+                sec = torch.remainder(sec, sf["n_mod"])
+                Rm = R + sf["stagger"] * torch.where(torch.remainder(sec, 2) == 1, 1.0, -1.0).to(torch.float64)
+                s = torch.where(fin, _barrel_s(tr, idx, c, Rm), s)
             surf_id = torch.full_like(idx, barrels[step])
         else:
             # smallest positive path over every surface whose crossing lies on the surface

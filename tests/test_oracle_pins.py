@@ -701,3 +701,106 @@ def test_refit_inward_statistics_at_first_hit(oracle_mod):
     np.testing.assert_allclose(pulls.std(axis=0), 1.0, atol=0.06)
     np.testing.assert_allclose(pulls.mean(axis=0), 0.0, atol=0.06)
     assert abs(chi2.mean() - 5.0) < 5 * np.sqrt(10.0 / m)
+
+
+# ---------------------------------------------------------------------- measurement model 1 (Sec. 4.1)
+
+def test_update2d_equals_information_form(oracle_mod):
+    """The 2-D update on the tangent plane at the hit azimuth equals the
+    information form with H = [(-sin a, cos a, 0, ...), (0, 0, 1, ...)]."""
+    rng = np.random.default_rng(15)
+    surf = _barrel(30.0)
+    for _ in range(20):
+        A = rng.normal(size=(6, 6))
+        P = A @ A.T * 0.01 + np.eye(6) * 1e-3
+        x = rng.normal(size=6)
+        x[4] = 0.3
+        a = rng.uniform(-math.pi, math.pi)
+        m = np.array([30.0 * math.cos(a), 30.0 * math.sin(a), rng.normal()])
+        H = np.zeros((2, 6))
+        H[0, 0], H[0, 1], H[1, 2] = -math.sin(a), math.cos(a), 1.0
+        R = np.diag([surf["sig_rphi"] ** 2, surf["sig_3"] ** 2])
+        rc, xo, Po, chi2 = oracle_mod.update2d(x, P, m, surf)
+        r = H[:, :3] @ (m - x[:3])
+        Pi = np.linalg.inv(np.linalg.inv(P) + H.T @ np.linalg.inv(R) @ H)
+        xi = x + Pi @ H.T @ np.linalg.solve(R, r)
+        assert rc == 0
+        np.testing.assert_allclose(Po, Pi, rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(xo, xi, rtol=1e-8, atol=1e-11)
+        assert chi2 == pytest.approx(r @ np.linalg.solve(H @ P @ H.T + R, r), rel=1e-10)
+
+
+def _local_pulls(st, C, tru, q, tq):
+    a = np.arctan2(tru[:, 1], tru[:, 0])
+    ep = np.stack([-np.sin(a), np.cos(a)], 1)
+    drphi = np.sum((st[:, :2] - tru[:, :2]) * ep, 1)
+    srphi = np.sqrt(np.einsum("ni,nij,nj->n", ep, C[:, :2, :2], ep))
+    return {
+        "rphi": drphi / srphi,
+        "z": (st[:, 2] - tru[:, 2]) / np.sqrt(C[:, 2, 2]),
+        "q/pT": (q * st[:, 3] - tq * tru[:, 3]) / np.sqrt(C[:, 3, 3]),
+        "phi": ((st[:, 4] - tru[:, 4] + np.pi) % (2 * np.pi) - np.pi) / np.sqrt(C[:, 4, 4]),
+        "theta": (st[:, 5] - tru[:, 5]) / np.sqrt(C[:, 5, 5]),
+    }
+
+
+def test_model1_noise_free_staggered_modules(oracle_mod):
+    """Modules at R -+ 0.25 cm: hits off the layer's average cylinder.  Model 1
+    (each hit on its own cylinder, 2-D update) recovers the true state of
+    noise-free tracks; model 0 (hits on the average cylinder) cannot."""
+    g = synth.geometry("barrel17s")
+    tk = synth.gen_tracks(g, 300, 35, ms_on=False, smear=False, keep_truth=True)
+    last = tk["offsets"][1:] - 1
+    tru = tk["truth"][last]
+    r1 = oracle_mod.fit(g, tk, ms_on=False, meas_model=1)
+    assert np.all(r1["status"] == 0)
+    for k, p in _local_pulls(r1["state"], r1["cov"], tru, r1["q"], tk["truth_q"]).items():
+        assert np.max(np.abs(p)) < 0.01, k
+    assert np.max(r1["chi2"]) < 1e-3
+    r0 = oracle_mod.fit(g, tk, ms_on=False, meas_model=0)
+    assert np.median(r0["chi2"] / r0["ndof"]) > 10.0
+
+
+def test_model1_statistics_staggered_modules(oracle_mod):
+    """Model 1 on the staggered geometry with scattering and smearing: pulls of
+    the five surface parameters ~ N(0, 1), and chi2 / ndof as under model 1 on
+    the ideal geometry (compared as the mean over tracks without the top 1%: on
+    17 layers a few low-pT tracks carry most of the chi2 tail)."""
+    g = synth.geometry("barrel17s")
+    tk = synth.gen_tracks(g, 20000, synth.BASE_SEED + 36, keep_truth=True)
+    r = oracle_mod.fit(g, tk, meas_model=1, threads=4)
+    ok = ((r["status"] & 7) == 0) & (r["q"] == tk["truth_q"])
+    last = tk["offsets"][1:] - 1
+    tru = tk["truth"][last][ok]
+    for k, p in _local_pulls(r["state"][ok], r["cov"][ok], tru, r["q"][ok], tk["truth_q"][ok]).items():
+        assert abs(p.mean()) < 0.04, (k, p.mean())
+        assert abs(p.std() - 1.0) < 0.05, (k, p.std())
+    g0 = synth.geometry("barrel17")
+    tk0 = synth.gen_tracks(g0, 20000, synth.BASE_SEED + 36)
+    r0 = oracle_mod.fit(g0, tk0, threads=4, meas_model=1)
+    ok0 = (r0["status"] & 7) == 0
+
+    def trimmed(rr, m):
+        x = np.sort(rr["chi2"][m] / rr["ndof"][m])
+        return x[: int(0.99 * len(x))].mean()
+
+    t1, t0 = trimmed(r, ok), trimmed(r0, ok0)
+    assert abs(t1 - t0) < 0.01, (t1, t0)
+    assert 0.9 < t1 < 1.05
+
+
+def test_besthit_two_step_on_staggered_modules(oracle_mod):
+    """Best-hit building on the staggered geometry: with two-step propagation
+    (average cylinder for the window, then each candidate's own cylinder) it keeps
+    the true hits as well as on the ideal geometry; taking the hits as lying on
+    the average cylinder (model 0) loses most of them."""
+    effs = {}
+    for name, model in (("barrel17", 0), ("barrel17s", 1), ("barrel17s", 0)):
+        g = synth.geometry(name)
+        ev = _binned_event(oracle_mod, g, 2000, 37)
+        out = oracle_mod.build_besthit(g, ev, meas_model=model)
+        where = ev["truth_where"][:, 3:]
+        has = where >= 0
+        effs[(name, model)] = np.mean(out["idx"][:, 3:][has] == where[has])
+    assert effs[("barrel17s", 1)] > effs[("barrel17", 0)] - 0.02, effs
+    assert effs[("barrel17s", 0)] < 0.5, effs
