@@ -68,6 +68,19 @@ extern "C" {
 #define KF_SCHED_PERSISTENT 1 /* tracks bucketed by hit count, persistent kernel
                                  with an atomic work queue, replayed as a CUDA graph */
 
+/* measurement model (kf_fit_params.meas_model), Sec. 4.1 */
+#define KF_MEAS_LAYER 0  /* the hit lies on its layer's surface: 3-D update there */
+#define KF_MEAS_HIT_2D 1 /* non-ideal barrel: a barrel hit lies on the cylinder through
+                            it (its module sits up to dr off the layer radius); the
+                            track is carried to that cylinder and updated with the
+                            two coordinates measured on the plane tangent to it at the
+                            hit (r-phi and z; disk hits keep KF_MEAS_LAYER).  Best-hit
+                            building takes two steps per layer: to the layer's average
+                            cylinder (scattering noise and the window, widened by dr,
+                            there), then to each candidate's cylinder to score it.
+                            Grid schedule and per-thread scoring only; the persistent
+                            schedule, the autotuner and kf_build_ckf refuse it. */
+
 #define KF_MAX_SURFACES 64
 #define KF_NPHI 1024
 #define KF_NZ 64
@@ -83,7 +96,7 @@ typedef struct kf_ctx kf_ctx;
  * sig_3: along z (barrel) or r (disk), all in cm.
  * dr: barrel, radial half-extent of the layer's modules (a non-ideal layer whose
  * hits lie within pos +- dr, Sec. 4.1); 0 for an ideal cylinder.  Read by the
- * building window under measurement model 1. */
+ * building window under KF_MEAS_HIT_2D. */
 typedef struct {
     int32_t kind;
     int32_t pad_;
@@ -112,6 +125,8 @@ typedef struct {
     double seed_cov;        /* seed covariance = seed_cov * I6, default 1e4 */
     int32_t ms_on;          /* 1: add multiple-scattering noise at every surface */
     int32_t schedule;       /* KF_SCHED_GRID | KF_SCHED_PERSISTENT */
+    int32_t meas_model;     /* KF_MEAS_LAYER (default) | KF_MEAS_HIT_2D */
+    int32_t pad_;
 } kf_fit_params;
 
 /* Seeds: device SoA. state [6][n] FP32 (x, y, z, 1/pT, phi, theta at the

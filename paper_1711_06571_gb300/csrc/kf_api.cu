@@ -108,11 +108,14 @@ int to_geom(kf_ctx *ctx, const kf_geometry *g, Geom &G)
             return fail(ctx, KF_EINVAL, "surface %d: resolutions must be > 0 and x/X0 >= 0", i);
         if (s.kind == 0 && !(s.pos > 0 && s.half_or_rin > 0))
             return fail(ctx, KF_EINVAL, "surface %d: barrel needs R > 0 and half length > 0", i);
+        if (!(s.dr >= 0) || (s.kind == 0 && !(s.dr < s.pos)))
+            return fail(ctx, KF_EINVAL, "surface %d: dr must be >= 0 and below the radius", i);
         Surf &d = G.s[i];
         d.kind = s.kind;
         d.posd = s.pos;
         d.pos = (float)s.pos;
         d.pos2 = (float)(s.pos * s.pos);
+        d.pos2lo = (float)(s.pos * s.pos - (double)d.pos2);
         d.halfd = s.half_or_rin;
         d.half = (float)s.half_or_rin;
         d.rout = (float)s.r_out;
@@ -126,6 +129,7 @@ int to_geom(kf_ctx *ctx, const kf_geometry *g, Geom &G)
         d.var_rad = (float)d.var_radd;
         d.var_rphi = (float)d.var_rphid;
         d.var_zz = (float)d.var_zzd;
+        d.dr = s.kind == 0 ? (float)s.dr : 0.f;
     }
     return KF_OK;
 }
@@ -170,6 +174,8 @@ int check_fit_params(kf_ctx *ctx, const kf_fit_params *p, kf_fit_params &q)
     q.seed_cov = 1e4;
     q.ms_on = 1;
     q.schedule = KF_SCHED_GRID;
+    q.meas_model = KF_MEAS_LAYER;
+    q.pad_ = 0;
     if (!p) return KF_OK;
     q = *p;
     if (q.precision != KF_PREC_MIXED && q.precision != KF_PREC_FP64)
@@ -178,6 +184,10 @@ int check_fit_params(kf_ctx *ctx, const kf_fit_params *p, kf_fit_params &q)
     if (!(q.seed_cov > 0)) return fail(ctx, KF_EINVAL, "seed_cov must be > 0");
     if (q.schedule != KF_SCHED_GRID && q.schedule != KF_SCHED_PERSISTENT)
         return fail(ctx, KF_EINVAL, "schedule must be KF_SCHED_GRID or KF_SCHED_PERSISTENT");
+    if (q.meas_model != KF_MEAS_LAYER && q.meas_model != KF_MEAS_HIT_2D)
+        return fail(ctx, KF_EINVAL, "meas_model must be KF_MEAS_LAYER or KF_MEAS_HIT_2D");
+    if (q.meas_model == KF_MEAS_HIT_2D && q.schedule != KF_SCHED_GRID)
+        return fail(ctx, KF_EINVAL, "meas_model KF_MEAS_HIT_2D runs on the grid schedule");
     return KF_OK;
 }
 
@@ -303,6 +313,7 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     a.n64 = P.n_fp64_updates;
     a.seed_cov = P.seed_cov;
     a.ms_on = P.ms_on;
+    a.meas_model = P.meas_model;
     a.seed_state = seeds->state;
     a.q = seeds->q;
     a.off = hits->offsets;
@@ -571,6 +582,8 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             a.n64 = P.n_fp64_updates;
             a.seed_cov = P.seed_cov;
             a.ms_on = P.ms_on;
+            a.meas_model = P.meas_model;
+    a.meas_model = P.meas_model;
             a.seed_state = d_seed;
             a.q = d_q;
             a.off = d_off;
@@ -616,6 +629,8 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     if (rc) return rc;
     if ((rc = set_dev(ctx))) return rc;
     if (n <= 0) return fail(ctx, KF_EINVAL, "autotune needs n > 0");
+    if (P.meas_model != KF_MEAS_LAYER)
+        return fail(ctx, KF_EINVAL, "the persistent schedule runs measurement model KF_MEAS_LAYER only");
     const bool fp64 = P.precision == KF_PREC_FP64;
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
@@ -872,6 +887,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     a.n64 = P.n_fp64_updates;
     a.seed_cov = P.seed_cov;
     a.ms_on = P.ms_on;
+    a.meas_model = P.meas_model;
     a.max_cand = B.max_cand;
     a.nsigma = (float)B.nsigma;
     a.chi2_cut = (float)B.chi2_cut;
@@ -902,6 +918,8 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
     if (rc) return rc;
     if (P.precision != KF_PREC_MIXED)
         return fail(ctx, KF_EINVAL, "combinatorial building runs the mixed precision policy only");
+    if (P.meas_model != KF_MEAS_LAYER)
+        return fail(ctx, KF_EINVAL, "combinatorial building runs measurement model KF_MEAS_LAYER only");
     if (n_slots != 1 && n_slots != 2 && n_slots != 4 && n_slots != 8)
         return fail(ctx, KF_EINVAL, "n_slots must be 1, 2, 4 or 8");
     Geom G;
@@ -946,6 +964,7 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
     a.n64 = P.n_fp64_updates;
     a.seed_cov = P.seed_cov;
     a.ms_on = P.ms_on;
+    a.meas_model = P.meas_model;
     a.max_cand = B.max_cand;
     a.nsigma = (float)B.nsigma;
     a.chi2_cut = (float)B.chi2_cut;

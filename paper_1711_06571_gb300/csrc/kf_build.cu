@@ -41,16 +41,35 @@ struct Window {
     int z_lo, z_hi;
 };
 
+//
+// dr > 0 (model 1, hits within +-dr of the layer radius): the window widens by
+// the azimuth and z the track sweeps over dr, dr tan(a) / R and dr |cot theta| /
+// cos(a) with a the angle between the track and the radial direction; the whole
+// layer when the track runs nearly along the layer (cos(a) <= 1e-3).
 template <class T, class P>
-__device__ __forceinline__ Window make_window(const Track<T, P> &st, const float p[21], const Surf &sf, float nsig)
+__device__ __forceinline__ Window make_window(const Track<T, P> &st, const float p[21], const Surf &sf, float nsig,
+                                              float dr = 0.f)
 {
     const float X = (float)lead(st.x), Y = (float)lead(st.y), Z = (float)lead(st.z);
     const float r2 = X * X + Y * Y;
     const float phip = atan2f(Y, X);
     const float sphi2 = (Y * Y * p[pk(0, 0)] + X * X * p[pk(1, 1)] - 2.f * X * Y * p[pk(1, 0)]) / (r2 * r2);
     const float R = sf.pos;
-    const float dphi = nsig * sqrtf(fmaxf(sphi2, 0.f) + sf.var_rphi / (R * R));
-    const float dz = nsig * sqrtf(fmaxf(p[pk(2, 2)], 0.f) + sf.var_zz);
+    float dphi = nsig * sqrtf(fmaxf(sphi2, 0.f) + sf.var_rphi / (R * R));
+    float dz = nsig * sqrtf(fmaxf(p[pk(2, 2)], 0.f) + sf.var_zz);
+    if (dr > 0.f) {
+        float sd, cd, sth, cth;
+        sincosf((float)lead(st.phi) - phip, &sd, &cd);
+        sincosf((float)lead(st.th), &sth, &cth);
+        const float ca = fabsf(cd), sa = fabsf(sd);
+        if (ca > 1e-3f) {
+            dphi += dr * sa / (ca * R);
+            dz += dr * fabsf(cth / sth) / ca;
+        } else {
+            dphi = PI_F;
+            dz = 2.f * sf.half;
+        }
+    }
     const float kphi = 1024.f / (2.f * PI_F);
     Window w;
     if (!(dphi < PI_F) || !(fabsf(phip) <= 2.f * PI_F)) {
@@ -89,6 +108,23 @@ __device__ __forceinline__ double cand_chi2(const Track<T, P> &st, const float p
     return ldl3_chi2(g, (double)r0, (double)r1, (double)r2);
 }
 
+// chi2 of one candidate under model 1: the predicted state (on the layer's
+// average cylinder) carried on to the cylinder through the hit, with the
+// position block of its covariance, and the 2-D chi2 there; -1 when the hit's
+// cylinder is out of reach or S is not positive definite.
+template <class T, class P, class C>
+__device__ __forceinline__ double cand_chi2_m1(const Track<T, P> &st, const C pc[21], const Surf &sf, T alpha,
+                                               float4 h)
+{
+    const Surf hs = hit_surface(sf, h.x, h.y);
+    Track<T, P> s2 = st;
+    Jac<T> J;
+    if (!propagate(s2, alpha, hs, J)) return -1.0;
+    C q[6];
+    transport_pos<C>(pc, JacAs<C>::get(J), q);
+    return kf_chi2_2d(s2, q, h.x, h.y, h.z, hs);
+}
+
 template <bool FP64> struct sel_t;
 template <> struct sel_t<true> { using T = double; using P = double; };
 template <> struct sel_t<false> { using T = float; using P = ff; };
@@ -101,10 +137,12 @@ struct StepOut {
 
 // Per-thread scoring: walk the window's rows (z ascending, phi from the low edge
 // with wrap, binned order), at most max_cand candidates.
-template <class T, class P>
-__device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[21], const Surf &sf,
-                                          const LayerDev &ly, const Window &w, bool shared, const Ldl3 &fs,
-                                          int max_cand, int &best, double &bchi, float4 &bhit, bool &capped)
+// M1: each candidate scored by cand_chi2_m1 (pc, alpha) instead of cand_chi2.
+template <bool M1, class T, class P, class C>
+__device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[21], const C pc[21], T alpha,
+                                          const Surf &sf, const LayerDev &ly, const Window &w, bool shared,
+                                          const Ldl3 &fs, int max_cand, int &best, double &bchi, float4 &bhit,
+                                          bool &capped)
 {
     int ncand = 0;
     for (int zb = w.z_lo; zb <= w.z_hi && !capped; ++zb) {
@@ -128,7 +166,9 @@ __device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[
                 }
                 ++ncand;
                 const float4 h = ly.packed[j];
-                const double c2 = cand_chi2(st, pw, sf, shared, fs, h);
+                double c2;
+                if constexpr (M1) c2 = cand_chi2_m1(st, pc, sf, alpha, h);
+                else c2 = cand_chi2(st, pw, sf, shared, fs, h);
                 const int hi = __float_as_int(h.w);
                 if (c2 >= 0.0 && (best < 0 || c2 < bchi || (c2 == bchi && hi < best))) {
                     best = hi;
@@ -161,7 +201,13 @@ struct StepKnobs {
 // One build layer for one track with per-thread scoring: propagate, transport,
 // scattering noise, window, candidates, update.  JOSEPH selects the covariance
 // update form (the FP64 steps).
-template <bool JOSEPH, class T, class P, class C>
+//
+// M1 (measurement model 1, Sec. 4.1, barrel layers): two propagation steps, to
+// the layer's average cylinder (scattering noise and the window, widened by
+// the layer's dr, there), then from there to each candidate's own cylinder,
+// where it is scored in 2-D; the chosen hit is reached the same way and the
+// 2-D update made on its cylinder.
+template <bool JOSEPH, bool M1, class T, class P, class C>
 __device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], T alpha, T mass2, const StepKnobs &a,
                                                      const Surf &sf, const LayerDev &ly, double &chi2,
                                                      unsigned &status, bool &alive)
@@ -178,6 +224,33 @@ __device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], 
     float pw[21];
 #pragma unroll
     for (int i = 0; i < 21; ++i) pw[i] = (float)pc[i];
+    int best = -1;
+    double bchi = 0.0;
+    float4 bhit = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (M1) {
+        if (sf.kind == 0) {
+            const Window w = make_window(st, pw, sf, a.nsigma, sf.dr);
+            const Ldl3 none{0, 0, 0, 0, 0, 0};
+            score_own<true>(st, pw, pc, alpha, sf, ly, w, false, none, a.max_cand, best, bchi, bhit, o.capped);
+            if (best >= 0 && bchi < (double)a.chi2_cut) {
+                const Surf hs = hit_surface(sf, bhit.x, bhit.y);
+                Jac<T> J;
+                bool ok = propagate(st, alpha, hs, J);
+                if (ok) {
+                    transport<C>(pc, JacAs<C>::get(J));
+                    if constexpr (JOSEPH) ok = kf_update2d<true>(st, pc, bhit.x, bhit.y, bhit.z, hs, chi2);
+                    else ok = kf_update2d_mixed(st, pc, bhit.x, bhit.y, bhit.z, hs, chi2);
+                }
+                if (ok) {
+                    o.chosen = best;
+                } else {
+                    status |= KF_ST_CHOL_FAIL;
+                    alive = false;
+                }
+            }
+            return o;
+        }
+    }
     const Window w = make_window(st, pw, sf, a.nsigma);
     const bool shared = sf.var_rad == sf.var_rphi;
     Ldl3 fs{0, 0, 0, 0, 0, 0};
@@ -186,10 +259,7 @@ __device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], 
         alive = false;
         return o;
     }
-    int best = -1;
-    double bchi = 0.0;
-    float4 bhit = make_float4(0.f, 0.f, 0.f, 0.f);
-    score_own(st, pw, sf, ly, w, shared, fs, a.max_cand, best, bchi, bhit, o.capped);
+    score_own<false>(st, pw, pc, alpha, sf, ly, w, shared, fs, a.max_cand, best, bchi, bhit, o.capped);
     if (best >= 0 && bchi < (double)a.chi2_cut) {
         bool ok;
         if constexpr (JOSEPH) {
@@ -211,6 +281,7 @@ __device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], 
 }
 
 // FP64 layer step for a mixed-path track at a near-tangent crossing
+template <bool M1>
 __device__ __forceinline__ StepOut layer_step_fp64(Track<float, ff> &st, float pc[21], double alpha, double mass2,
                                                    const StepKnobs &a, const Surf &sf, const LayerDev &ly,
                                                    double &chi2, unsigned &status, bool &alive)
@@ -225,7 +296,7 @@ __device__ __forceinline__ StepOut layer_step_fp64(Track<float, ff> &st, float p
     double pd[21];
 #pragma unroll
     for (int i = 0; i < 21; ++i) pd[i] = pc[i];
-    const StepOut o = layer_step_thread<true>(sd, pd, alpha, mass2, a, sf, ly, chi2, status, alive);
+    const StepOut o = layer_step_thread<true, M1>(sd, pd, alpha, mass2, a, sf, ly, chi2, status, alive);
     if (alive) {
         auto f = [](double d) {
             float h = (float)d;
@@ -250,11 +321,12 @@ struct Fp64LayerIO {
     StepOut o;
     int alive;
 };
+template <bool M1>
 static __device__ __noinline__ Fp64LayerIO layer_step_fp64_out_of_line(Fp64LayerIO io, double alpha, double mass2,
                                                                        StepKnobs kn, const Surf *sf, LayerDev ly)
 {
     bool alive = io.alive != 0;
-    io.o = layer_step_fp64(io.m.st, io.m.p, alpha, mass2, kn, *sf, ly, io.m.chi2, io.m.status, alive);
+    io.o = layer_step_fp64<M1>(io.m.st, io.m.p, alpha, mass2, kn, *sf, ly, io.m.chi2, io.m.status, alive);
     io.alive = alive;
     return io;
 }
@@ -383,7 +455,8 @@ __device__ __forceinline__ void score_coop(const Track<T, P> &st, bool do_step, 
 // event): the first n64 updates with an FP64 covariance (the structured update
 // at the first hit, Joseph form after), the rest in the layer covariance type.
 // Returns whether the track is still alive.
-template <bool FP64>
+// M1: barrel seed hits on their own cylinders with the 2-D update.
+template <bool FP64, bool M1 = false>
 __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf, const LayerDev *lays, int n, int t,
                                          Track<typename sel_t<FP64>::T, typename sel_t<FP64>::P> &st,
                                          typename sel_t<FP64>::T pc[21], typename sel_t<FP64>::T alpha,
@@ -404,6 +477,16 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         const Surf &sf = s_surf[lays[k].surface];
         const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
                     hz = a.seed_hits[(3 * k + 2) * n + t];
+        if constexpr (M1) {
+            if (sf.kind == 0) {
+                const Surf h = hit_surface(sf, hx, hy);
+                alive = fit_step_on<true, double, true>(st, pd, k, alpha, mass2, a.ms_on, h, hx, hy, hz, chi2,
+                                                        status);
+                if (!alive) break;
+                ++used;
+                continue;
+            }
+        }
         T cphi, sphi;
         if (k > 0) {
             Jac<T> J;
@@ -435,6 +518,15 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         const Surf &sf = s_surf[lays[k].surface];
         const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
                     hz = a.seed_hits[(3 * k + 2) * n + t];
+        if constexpr (M1) {
+            if (sf.kind == 0) {
+                const Surf h = hit_surface(sf, hx, hy);
+                alive = fit_step_on<false, C, true>(st, pc, k, alpha, mass2, a.ms_on, h, hx, hy, hz, chi2, status);
+                if (!alive) break;
+                ++used;
+                continue;
+            }
+        }
         T cphi, sphi;
         if (k > 0) {
             Jac<T> J;
@@ -460,9 +552,10 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
     return alive;
 }
 
-template <bool FP64, bool COOP>
+template <bool FP64, bool COOP, bool M1>
 // three blocks per SM (at most 168 registers a thread): 12 warps to hide the
-// FP64 and memory latencies of the layer steps
+// FP64 and memory latencies of the layer steps.  M1: measurement model 1
+// (per-thread scoring).
 __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const BuildArgs a)
 {
     using T = typename sel_t<FP64>::T;
@@ -495,7 +588,7 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
     bool alive = active;
     C pc[21];
     const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
-    alive = seed_fit<FP64>(a, s_surf, lays, n, t, st, pc, alpha, mass2, status, chi2, used, alive);
+    alive = seed_fit<FP64, M1>(a, s_surf, lays, n, t, st, pc, alpha, mass2, status, chi2, used, alive);
     if (active)
         for (int L = 0; L < 3; ++L) a.hit_idx[(size_t)L * n + t] = -1;
     // build layers
@@ -505,12 +598,15 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
         StepOut so{-1, false};
         bool near_tangent = false;
         if constexpr (!FP64) near_tangent = alive && crossing_sine(st, alpha, sf) > 0.8f;
+        // model 1: the first update after the seed hits is strongly informative
+        // (six seed coordinates for five parameters) and runs in FP64 as well
+        if constexpr (!FP64 && M1) near_tangent = near_tangent || (alive && a.n64 > 0 && used < 4);
         if (near_tangent) {
             if constexpr (!FP64) {
                 Fp64LayerIO io;
                 mixed_pack(io.m, st, pc, chi2, status);
                 io.alive = alive;
-                io = layer_step_fp64_out_of_line(io, alphad, g.mass2d, kn, &sf, ly);
+                io = layer_step_fp64_out_of_line<M1>(io, alphad, g.mass2d, kn, &sf, ly);
                 mixed_unpack(io.m, st, pc, chi2, status);
                 alive = io.alive != 0;
                 so = io.o;
@@ -518,10 +614,10 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
         }
         // the cooperative path needs the S factor shared by a layer's candidates; the
         // condition is the same for every lane (all events share the geometry)
-        const bool coop = COOP && sf.var_rad == sf.var_rphi;
+        const bool coop = COOP && !M1 && sf.var_rad == sf.var_rphi;
         if (!coop) {
             if (alive && !near_tangent)
-                so = layer_step_thread<false>(st, pc, alpha, mass2, kn, sf, ly, chi2, status, alive);
+                so = layer_step_thread<false, M1>(st, pc, alpha, mass2, kn, sf, ly, chi2, status, alive);
         } else {
             // every lane of the warp takes part in the shuffles, stepping or not
             bool do_step = alive && !near_tangent;
@@ -587,12 +683,15 @@ cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp
 {
     if (a.n <= 0) return cudaSuccess;
     const int b = 128, grid = (a.n + b - 1) / b;
-    if (fp64) {
-        if (warp_coop) build_kernel<true, true><<<grid, b, 0, st>>>(g, a);
-        else build_kernel<true, false><<<grid, b, 0, st>>>(g, a);
+    if (a.meas_model == 1) {  // per-thread scoring
+        if (fp64) build_kernel<true, false, true><<<grid, b, 0, st>>>(g, a);
+        else build_kernel<false, false, true><<<grid, b, 0, st>>>(g, a);
+    } else if (fp64) {
+        if (warp_coop) build_kernel<true, true, false><<<grid, b, 0, st>>>(g, a);
+        else build_kernel<true, false, false><<<grid, b, 0, st>>>(g, a);
     } else {
-        if (warp_coop) build_kernel<false, true><<<grid, b, 0, st>>>(g, a);
-        else build_kernel<false, false><<<grid, b, 0, st>>>(g, a);
+        if (warp_coop) build_kernel<false, true, false><<<grid, b, 0, st>>>(g, a);
+        else build_kernel<false, false, false><<<grid, b, 0, st>>>(g, a);
     }
     return cudaGetLastError();
 }

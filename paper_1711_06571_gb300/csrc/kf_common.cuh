@@ -21,11 +21,13 @@ constexpr float PI_F = 3.14159265358979323846f;
 struct Surf {
     int kind;   // 0 barrel, 1 disk
     int pad_;
-    float pos, pos2, half, rout;
+    float pos, pos2, half, rout;  // pos2 + pos2lo: pos^2 as a float-float (barrel)
     float x_x0;
     float var_rad;   // variance along r-hat (barrel: sig_n^2, disk: sig_3^2)
     float var_rphi;  // along phi-hat
     float var_zz;    // along z (barrel: sig_3^2, disk: sig_n^2)
+    float dr;        // barrel: radial half-extent of the layer's modules (model 1 window)
+    float pos2lo;
     double posd, halfd, x_x0d, var_radd, var_rphid, var_zzd;
 };
 
@@ -113,14 +115,14 @@ __device__ __forceinline__ void sincos_pos(ff a, float &s, float &c)
 __device__ __forceinline__ void sincos_pos(double a, double &s, double &c) { sincos(a, &s, &c); }
 
 // x^2 + y^2 - R^2 for a point held in extended precision
-__device__ __forceinline__ float radial_excess(ff x, ff y, float R2)
+__device__ __forceinline__ float radial_excess(ff x, ff y, float R2, float R2lo)
 {
     float p1 = __fmul_rn(x.hi, x.hi), e1 = fmaf(x.hi, x.hi, -p1);
     float p2 = __fmul_rn(y.hi, y.hi), e2 = fmaf(y.hi, y.hi, -p2);
     float s, e, s2, e3;
     two_sum(p1, p2, s, e);
     two_sum(s, -R2, s2, e3);
-    float lo = e + e3 + e1 + e2 + 2.0f * (x.hi * x.lo + y.hi * y.lo);
+    float lo = e + e3 - R2lo + e1 + e2 + 2.0f * (x.hi * x.lo + y.hi * y.lo);
     return s2 + lo;
 }
 __device__ __forceinline__ double radial_excess(double x, double y, double R2) { return x * x + y * y - R2; }

@@ -121,34 +121,20 @@ struct FitTypes {
     using P = typename sel<FP64, double, ff>::type;
 };
 
-// one surface crossing + update; returns false when the track ends here
-template <bool JOSEPH, class C, class T, class P>
+// one hit on layer surface sf.  M1 (measurement model 1, Sec. 4.1): a barrel
+// hit is reached on the cylinder through it and measured in 2-D there.
+template <bool JOSEPH, class C, bool M1 = false, class T, class P>
 __device__ __forceinline__ bool fit_step(Track<T, P> &st, C p[21], int k, T alpha, T mass2, int ms_on,
                                          const Surf &sf, float hx, float hy, float hz, double &chi2,
                                          unsigned &status)
 {
-    T cphi, sphi;
-    if (k > 0) {
-        Jac<T> J;
-        if (!propagate(st, alpha, sf, J)) {
-            status |= KF_ST_NO_INTERSECT;
-            return false;
+    if constexpr (M1) {
+        if (sf.kind == 0) {
+            const Surf h = hit_surface(sf, hx, hy);
+            return fit_step_on<JOSEPH, C, true>(st, p, k, alpha, mass2, ms_on, h, hx, hy, hz, chi2, status);
         }
-        transport<C>(p, JacAs<C>::get(J));
-        cphi = J.cphi1;
-        sphi = J.sphi1;
-    } else {
-        sincos_pos(st.phi, sphi, cphi);
     }
-    if (ms_on) status |= ms_noise<T, C>(st, sf, cphi, sphi, mass2, p);
-    bool ok;
-    if constexpr (JOSEPH) ok = kf_update<true>(st, p, hx, hy, hz, sf, chi2);
-    else ok = kf_update_mixed(st, p, hx, hy, hz, sf, chi2);
-    if (!ok) {
-        status |= KF_ST_CHOL_FAIL;
-        return false;
-    }
-    return true;
+    return fit_step_on<JOSEPH, C, false>(st, p, k, alpha, mass2, ms_on, sf, hx, hy, hz, chi2, status);
 }
 
 // Sine of the crossing angle above which a mixed-path step runs in FP64:
@@ -166,6 +152,15 @@ __device__ __forceinline__ bool grazing_crossing(const Track<float, ff> &st, flo
     sincos_pos(st.th, sth, cth);
     return fabsf(cth) < 0.6f;
 }
+// the same test on the surface the hit is measured on
+template <bool M1>
+__device__ __forceinline__ bool grazing_crossing(const Track<float, ff> &st, float alpha, const Surf &sf, float hx,
+                                                 float hy)
+{
+    if constexpr (M1)
+        if (sf.kind == 0) return grazing_crossing(st, alpha, hit_surface(sf, hx, hy));
+    return grazing_crossing(st, alpha, sf);
+}
 
 __device__ __forceinline__ ff ff_from_d(double d)
 {
@@ -174,6 +169,7 @@ __device__ __forceinline__ ff ff_from_d(double d)
 }
 
 // one full step in FP64 for a mixed-path track (state float-float, P float)
+template <bool M1>
 __device__ __forceinline__ bool fp64_step(Track<float, ff> &st, float pf[21], int k, double alpha, double mass2,
                                        int ms_on, const Surf &sf, float hx, float hy, float hz, double &chi2,
                                        unsigned &status)
@@ -188,7 +184,7 @@ __device__ __forceinline__ bool fp64_step(Track<float, ff> &st, float pf[21], in
     double pd[21];
 #pragma unroll
     for (int i = 0; i < 21; ++i) pd[i] = f2d(pf[i]);
-    if (!fit_step<true, double>(sd, pd, k, alpha, mass2, ms_on, sf, hx, hy, hz, chi2, status)) return false;
+    if (!fit_step<true, double, M1>(sd, pd, k, alpha, mass2, ms_on, sf, hx, hy, hz, chi2, status)) return false;
     st.x = ff_from_d(sd.x);
     st.y = ff_from_d(sd.y);
     st.z = ff_from_d(sd.z);
@@ -201,11 +197,12 @@ __device__ __forceinline__ bool fp64_step(Track<float, ff> &st, float pf[21], in
 }
 
 // fp64_step out of line (a near-tangent crossing is about 2% of the steps)
+template <bool M1>
 static __device__ __noinline__ MixedIO fp64_step_out_of_line(MixedIO m, int k, double alpha, double mass2,
                                                              int ms_on, const Surf *sf, float hx, float hy,
                                                              float hz)
 {
-    m.ok = fp64_step(m.st, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
+    m.ok = fp64_step<M1>(m.st, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
     return m;
 }
 
@@ -220,6 +217,7 @@ struct MixedIOD {
     int ok;
 };
 
+template <bool M1>
 static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int k, double alpha, double mass2,
                                                                  int ms_on, const Surf *sf, float hx, float hy,
                                                                  float hz)
@@ -231,7 +229,7 @@ static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int
     sd.phi = to_d(m.st.phi);
     sd.ip = m.st.ip;
     sd.th = to_d(m.st.th);
-    m.ok = fit_step<true, double>(sd, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
+    m.ok = fit_step<true, double, M1>(sd, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
     if (m.ok) {
         m.st.x = ff_from_d(sd.x);
         m.st.y = ff_from_d(sd.y);
@@ -251,7 +249,7 @@ __device__ __forceinline__ void store_cov(double *o_cov, int n, int t, const C p
     for (int i = 0; i < 21; ++i) o_cov[(size_t)i * n + t] = (double)p[i];
 }
 
-template <bool FP64>
+template <bool FP64, bool M1 = false>
 __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *surf, float kb, float mass2f,
                                           double kbd, double mass2d)
 {
@@ -291,6 +289,10 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
     if (a.n64 > 0 && nh >= 3) {
         const int s2 = seed_hit_last(a.hx + o0, a.hy + o0, nh);
         n1 = max(n1, s2 + 1);
+        // model 1: the three seed hits measure six coordinates for five track
+        // parameters (the first hit's radial position stays at the seed prior),
+        // so the next update is still a strongly informative one: FP64 too
+        if (M1) n1 = max(n1, s2 + 2);
     }
     n1 = min(n1, nh);
     if (n1 > 0) {
@@ -298,10 +300,18 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         const Surf &sf = surf[a.layer[o0]];
         T cphi, sphi;
         sincos_pos(st.phi, sphi, cphi);
-        if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
-        // the structured update needs the diagonal seed covariance; a given one takes the general form
-        const bool ok0 = a.p0 ? kf_update<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)
-                              : kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
+        bool ok0;
+        if (M1 && sf.kind == 0) {
+            // model 1: the seed sits at the hit; the 2-D update on the hit's cylinder
+            const Surf h = hit_surface(sf, a.hx[o0], a.hy[o0]);
+            if (a.ms_on) status |= ms_noise<T, double>(st, h, cphi, sphi, mass2, pd);
+            ok0 = kf_update2d<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], h, chi2);
+        } else {
+            if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
+            // the structured update needs the diagonal seed covariance; a given one takes the general form
+            ok0 = a.p0 ? kf_update<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)
+                       : kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
+        }
         if (ok0) {
             ++used;
             k = 1;
@@ -315,14 +325,14 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         const Surf &sf = surf[a.layer[h]];
         bool ok;
         if constexpr (!FP64) {
-            if (grazing_crossing(st, alpha, sf)) {
+            if (grazing_crossing<M1>(st, alpha, sf, a.hx[h], a.hy[h])) {
                 MixedIOD m;
                 m.st = st;
 #pragma unroll
                 for (int i = 0; i < 21; ++i) m.p[i] = pd[i];
                 m.chi2 = chi2;
                 m.status = status;
-                m = fp64_step_pd_out_of_line(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
+                m = fp64_step_pd_out_of_line<M1>(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
                                              a.hz[h]);
                 st = m.st;
 #pragma unroll
@@ -331,11 +341,12 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
                 status = m.status;
                 ok = m.ok != 0;
             } else {
-                ok = fit_step<true, double>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
-                                            status);
+                ok = fit_step<true, double, M1>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h],
+                                                chi2, status);
             }
         } else {
-            ok = fit_step<true, double>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2, status);
+            ok = fit_step<true, double, M1>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
+                                            status);
         }
         if (!ok) {
             alive = false;
@@ -352,18 +363,18 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
             const int h = o0 + k;
             const Surf &sf = surf[a.layer[h]];
             bool near_tangent = false;
-            if constexpr (!FP64) near_tangent = grazing_crossing(st, alpha, sf);
+            if constexpr (!FP64) near_tangent = grazing_crossing<M1>(st, alpha, sf, a.hx[h], a.hy[h]);
             if (near_tangent) {
                 // near-tangent crossing: the whole step in FP64 (Joseph form)
                 if constexpr (!FP64) {
                     MixedIO m;
                     mixed_pack(m, st, pf, chi2, status);
-                    m = fp64_step_out_of_line(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
+                    m = fp64_step_out_of_line<M1>(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
                                               a.hz[h]);
                     if (!mixed_unpack(m, st, pf, chi2, status)) break;
                 }
-            } else if (!fit_step<false, T>(st, pf, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
-                                           status)) {
+            } else if (!fit_step<false, T, M1>(st, pf, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h],
+                                               chi2, status)) {
                 break;
             }
             ++used;
@@ -385,7 +396,7 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
     if (a.o_status) a.o_status[t] = status;
 }
 
-template <bool FP64>
+template <bool FP64, bool M1>
 __global__ void __launch_bounds__(128) fit_kernel(const Geom g, const FitArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
@@ -393,7 +404,7 @@ __global__ void __launch_bounds__(128) fit_kernel(const Geom g, const FitArgs a)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.count) return;
     const int t = a.t_begin + (a.order ? a.order[i] : i);
-    fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
+    fit_track<FP64, M1>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
 }
 
 // Persistent form: a grid sized to the machine; each block takes
@@ -533,10 +544,13 @@ cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cu
     (void)block;
     const int b = 128;
     const int grid = (a.count + b - 1) / b;
-    if (fp64)
-        fit_kernel<true><<<grid, b, 0, st>>>(g, a);
-    else
-        fit_kernel<false><<<grid, b, 0, st>>>(g, a);
+    if (a.meas_model == 1) {
+        if (fp64) fit_kernel<true, true><<<grid, b, 0, st>>>(g, a);
+        else fit_kernel<false, true><<<grid, b, 0, st>>>(g, a);
+    } else {
+        if (fp64) fit_kernel<true, false><<<grid, b, 0, st>>>(g, a);
+        else fit_kernel<false, false><<<grid, b, 0, st>>>(g, a);
+    }
     return cudaGetLastError();
 }
 
@@ -555,6 +569,7 @@ static cudaError_t launch_pers(const Geom &g, const FitArgs &a, int block, int g
 cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, int block, int grid, cudaStream_t st)
 {
     if (a.count <= 0) return cudaSuccess;
+    if (a.meas_model != 0) return cudaErrorInvalidValue;  // model 1 runs on the grid schedule
     return fp64 ? launch_pers<true>(g, a, block, grid, st) : launch_pers<false>(g, a, block, grid, st);
 }
 

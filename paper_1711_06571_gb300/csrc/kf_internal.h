@@ -30,7 +30,7 @@ struct FitArgs {
     const int32_t *order;  // processing order (tracks sorted by hit count), or null
     int32_t *queue;        // work counter, zeroed before the launch
     int chunk;             // tracks per thread per queue grab (a block takes blockDim * chunk)
-    int pad2_;
+    int meas_model;        // 0: 3-D hit on the layer; 1: barrel hits on their own cylinder, 2-D (grid schedule)
     // initial covariance: p0_scale * p0 ([21][n] FP64) instead of seed_cov * I when p0 is set
     const double *p0;
     double p0_scale;
@@ -95,6 +95,8 @@ struct BuildArgs {
     double *o_state, *o_cov, *o_chi2;
     int32_t *o_ndof;
     uint32_t *o_status;
+    int meas_model;  // as FitArgs::meas_model (per-thread scoring only)
+    int pad_;
 };
 cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp_coop, cudaStream_t st);
 

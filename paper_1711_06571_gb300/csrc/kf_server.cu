@@ -580,6 +580,7 @@ int kf_server::launch(Batch &b)
         a.n64 = p.fit.n_fp64_updates;
         a.seed_cov = p.fit.seed_cov;
         a.ms_on = p.fit.ms_on;
+        a.meas_model = p.fit.meas_model;
         a.max_cand = p.build.max_cand;
         a.nsigma = (float)p.build.nsigma;
         a.chi2_cut = (float)p.build.chi2_cut;
@@ -615,6 +616,7 @@ int kf_server::launch(Batch &b)
         a.n64 = p.fit.n_fp64_updates;
         a.seed_cov = p.fit.seed_cov;
         a.ms_on = p.fit.ms_on;
+        a.meas_model = p.fit.meas_model;
         a.seed_state = fseed;
         a.q = fq;
         a.off = goff;
@@ -822,8 +824,9 @@ int kf_server_create(kf_ctx *ctx, const kf_geometry *geom, const kf_server_param
     if (P.max_batch_events <= 0) P.max_batch_events = 16;
     if (P.max_batches > 16 || P.max_batch_events > 64 || !(P.batch_window_ms >= 0 && P.batch_window_ms <= 1e5))
         return ctx_fail(ctx, KF_EINVAL, "max_batches <= 16, max_batch_events <= 64, 0 <= batch_window_ms <= 1e5");
-    kf_fit_params F;
-    int rc = ctx_fit_params(ctx, P.fit.seed_cov == 0 ? nullptr : &P.fit, F);
+    kf_fit_params F, Fin = P.fit;
+    Fin.schedule = KF_SCHED_GRID;  // the server's fits run on the grid schedule
+    int rc = ctx_fit_params(ctx, P.fit.seed_cov == 0 ? nullptr : &Fin, F);
     if (rc) return rc;
     P.fit = F;
     if (P.build.nsigma == 0) P.build = kf_build_params{3.0, 30.0, 32, 0};

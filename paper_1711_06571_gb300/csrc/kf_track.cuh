@@ -60,6 +60,13 @@ __device__ __forceinline__ double sub_lead(double Z, double z) { return Z - z; }
 __device__ __forceinline__ ff set_exact(float Z, ff) { return {Z, 0.f}; }
 __device__ __forceinline__ double set_exact(double Z, double) { return Z; }
 
+// x^2 + y^2 - R^2 for barrel surface sf
+__device__ __forceinline__ float surf_excess(ff x, ff y, const Surf &sf) { return radial_excess(x, y, sf.pos2, sf.pos2lo); }
+__device__ __forceinline__ double surf_excess(double x, double y, const Surf &sf)
+{
+    return radial_excess(x, y, sf.posd * sf.posd);
+}
+
 constexpr float MAX_PATH = 1.0e6f;  // longer transverse paths count as no intersection
 
 // Propagate st along its helix to surface sf (Sec. 3 uniform field, Sec. 4.1
@@ -81,7 +88,7 @@ __device__ __forceinline__ bool propagate(Track<T, P> &st, T alpha, const Surf &
     const T X = lead(st.x), Y = lead(st.y);
     if (sf.kind == 0) {
         const T R = spos<T>(sf);
-        const T g0 = radial_excess(st.x, st.y, R * R);
+        const T g0 = surf_excess(st.x, st.y, sf);
         const T pt = X * cphi + Y * sphi, pn = -X * sphi + Y * cphi;
         const bool inside = g0 < T(0);
         if (inside) {
@@ -179,7 +186,7 @@ __device__ __forceinline__ T crossing_sine(const Track<T, P> &st, T alpha, const
     sincos_pos(st.phi, sphi, cphi);
     const T X = lead(st.x), Y = lead(st.y);
     const T R = spos<T>(sf);
-    const T g0 = radial_excess(st.x, st.y, R * R);
+    const T g0 = surf_excess(st.x, st.y, sf);
     const T pn = -X * sphi + Y * cphi;
     T sg = c > T(0) ? T(1) : (c < T(0) ? T(-1) : T(0));
     return (fabs(c) * (-g0) - T(2) * sg * pn) / (T(2) * R);
@@ -237,6 +244,52 @@ __device__ __forceinline__ void transport(T p[21], const Jac<T> &J)
             if (j != 3 && j != 5) v += a[i] * u[j];
             if (i != 3 && i != 5 && j != 3 && j != 5) v += gam * u[i] * u[j];
             p[pk(i, j)] = v;
+        }
+    }
+}
+
+// The position block of J P J^T alone (packed entries 0..5: (0,0) (1,0) (1,1)
+// (2,0) (2,1) (2,2)), by the same arithmetic as transport: what a hit's chi2
+// needs when the state is only carried to the hit to score it.
+template <class T>
+__device__ __forceinline__ void transport_pos(const T p[21], const Jac<T> &J, T q[6])
+{
+    T y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        T v = T(0);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) v += p[pk(i, j)] * J.w[j];
+        y[i] = v;
+    }
+    T gam = T(0);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gam += J.w[i] * y[i];
+    T a[3];
+    a[0] = y[0] + J.ax3 * y[3] + J.ax4 * y[4];
+    a[1] = y[1] + J.ay3 * y[3] + J.ay4 * y[4];
+    a[2] = y[2] + J.az5 * y[5];
+    T B[3][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        T p3 = p[pk(3, j)], p4 = p[pk(4, j)], p5 = p[pk(5, j)];
+        B[0][j] = p[pk(0, j)] + J.ax3 * p3 + J.ax4 * p4;
+        B[1][j] = p[pk(1, j)] + J.ay3 * p3 + J.ay4 * p4;
+        B[2][j] = p[pk(2, j)] + J.az5 * p5;
+    }
+    const T u[3] = {J.u0, J.u1, J.u2};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            T v;
+            if (j == 0) v = B[i][0] + J.ax3 * B[i][3] + J.ax4 * B[i][4];
+            else if (j == 1) v = B[i][1] + J.ay3 * B[i][3] + J.ay4 * B[i][4];
+            else v = B[i][2] + J.az5 * B[i][5];
+            v += u[i] * a[j];
+            v += a[i] * u[j];
+            v += gam * u[i] * u[j];
+            q[pk(i, j)] = v;
         }
     }
 }
@@ -509,6 +562,160 @@ __device__ __forceinline__ bool kf_update_mixed_factored(Track<float, Pp> &st, f
     return true;
 }
 
+// ---------------------------------------------------------------- measurement model 1
+// Sec. 4.1, non-ideal geometry: a barrel hit need not lie on its layer's average
+// cylinder.  The state is carried to the cylinder through the hit and updated on
+// the plane tangent to it there, with the two coordinates measured on that plane:
+// H has rows t = (-sin a, cos a, 0, ..) and (0, 0, 1, ..), a the hit azimuth;
+// R = diag(sig_rphi^2, sig_z^2); chi2 and S^-1 from a 2x2 LDL^T in FP64.
+
+// the cylinder through a barrel hit: R^2 = hx^2 + hy^2 (exact in FP64 to the
+// last bit of the sum), carried as a float-float for the FP32 propagation
+__device__ __forceinline__ Surf hit_surface(const Surf &sf, float hx, float hy)
+{
+    Surf h = sf;
+    const double r2 = fma((double)hx, (double)hx, (double)hy * (double)hy);
+    h.pos2 = (float)r2;
+    h.pos2lo = (float)(r2 - (double)h.pos2);
+    h.pos = sqrtf(h.pos2);
+    h.posd = sqrt(r2);
+    return h;
+}
+
+// the surface a hit is measured on: its own cylinder under model 1 (barrel), the layer otherwise
+template <bool M1>
+__device__ __forceinline__ Surf meas_surface(const Surf &sf, float hx, float hy)
+{
+    if (M1 && sf.kind == 0) return hit_surface(sf, hx, hy);
+    return sf;
+}
+
+template <bool JOSEPH, class C, class T, class Pp>
+__device__ __forceinline__ bool kf_update2d(Track<T, Pp> &st, C p[21], float hx, float hy, float hz, const Surf &sf,
+                                            double &chi2)
+{
+    const auto r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);
+    const bool d = sizeof(C) == 8;
+    const C rh = sqrt(C(hx) * C(hx) + C(hy) * C(hy));
+    const C ca = C(hx) / rh, sa = C(hy) / rh;
+    const C vt = d ? C(sf.var_rphid) : C(sf.var_rphi), vz = d ? C(sf.var_zzd) : C(sf.var_zz);
+    // G = P H^T (6x2)
+    C G[6][2];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        G[i][0] = -sa * p[pk(i, 0)] + ca * p[pk(i, 1)];
+        G[i][1] = p[pk(i, 2)];
+    }
+    const C s11 = -sa * G[0][0] + ca * G[1][0] + vt, s21 = G[2][0], s22 = p[pk(2, 2)] + vz;
+    const double e11 = wide(s11), e21 = wide(s21), e22 = wide(s22);
+    if (!(e11 > 0.0)) return false;
+    const double i1 = rcp_d(e11), l21 = e21 * i1, d2 = fma(-l21, e21, e22);
+    if (!(d2 > 0.0)) return false;
+    const double i2 = rcp_d(d2);
+    const double rt = -wide(sa) * wide(C(r0)) + wide(ca) * wide(C(r1)), rz = wide(C(r2));
+    const double z2 = fma(-l21, rt, rz);
+    chi2 += fma(z2 * i2, z2, rt * i1 * rt);
+    // S^-1 = L^-T D^-1 L^-1
+    const C a11 = to_t(fma(l21 * l21, i2, i1), C(0)), a21 = to_t(-l21 * i2, C(0)), a22 = to_t(i2, C(0));
+    C K[6][2];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        K[i][0] = G[i][0] * a11 + G[i][1] * a21;
+        K[i][1] = G[i][0] * a21 + G[i][1] * a22;
+    }
+    const C ct = to_t(rt, C(0)), cz = to_t(rz, C(0));
+    C dd[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dd[i] = K[i][0] * ct + K[i][1] * cz;
+    add_inc(st.x, dd[0]);
+    add_inc(st.y, dd[1]);
+    add_inc(st.z, dd[2]);
+    add_inc(st.ip, dd[3]);
+    add_inc(st.phi, dd[4]);
+    st.phi = wrap(st.phi);
+    add_inc(st.th, dd[5]);
+    if (JOSEPH) {
+        // P - K G^T + (K S - G) K^T
+        C W[6][2];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            W[i][0] = K[i][0] * s11 + K[i][1] * s21 - G[i][0];
+            W[i][1] = K[i][0] * s21 + K[i][1] * s22 - G[i][1];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j)
+                p[pk(i, j)] = p[pk(i, j)] - (K[i][0] * G[j][0] + K[i][1] * G[j][1]) +
+                              (W[i][0] * K[j][0] + W[i][1] * K[j][1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) p[pk(i, j)] -= K[i][0] * G[j][0] + K[i][1] * G[j][1];
+    }
+    return true;
+}
+
+// chi2 of a hit under model 1 without the update (the S of kf_update2d), or -1
+// when S is not positive definite
+template <class C, class T, class Pp>
+__device__ __forceinline__ double kf_chi2_2d(const Track<T, Pp> &st, const C p[21], float hx, float hy, float hz,
+                                             const Surf &sf)
+{
+    const auto r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);
+    const bool d = sizeof(C) == 8;
+    const C rh = sqrt(C(hx) * C(hx) + C(hy) * C(hy));
+    const C ca = C(hx) / rh, sa = C(hy) / rh;
+    const C vt = d ? C(sf.var_rphid) : C(sf.var_rphi), vz = d ? C(sf.var_zzd) : C(sf.var_zz);
+    const C g0 = -sa * p[pk(0, 0)] + ca * p[pk(1, 0)], g1 = -sa * p[pk(1, 0)] + ca * p[pk(1, 1)];
+    const double e11 = wide(C(-sa * g0 + ca * g1 + vt));
+    const double e21 = wide(C(-sa * p[pk(2, 0)] + ca * p[pk(2, 1)])), e22 = wide(C(p[pk(2, 2)] + vz));
+    if (!(e11 > 0.0)) return -1.0;
+    const double i1 = rcp_d(e11), l21 = e21 * i1, d2 = fma(-l21, e21, e22);
+    if (!(d2 > 0.0)) return -1.0;
+    const double rt = -wide(sa) * wide(C(r0)) + wide(ca) * wide(C(r1)), rz = wide(C(r2));
+    const double z2 = fma(-l21, rt, rz);
+    return fma(z2 * rcp_d(d2), z2, rt * i1 * rt);
+}
+
+// the FP64 Joseph 2-D update of an FP32 covariance, out of line
+static __device__ __noinline__ MixedIO kf_update2d_fp64_of_f32(MixedIO m, float hx, float hy, float hz,
+                                                               const Surf *sf)
+{
+    double pd[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pd[i] = f2d(m.p[i]);
+    m.ok = kf_update2d<true>(m.st, pd, hx, hy, hz, *sf, m.chi2);
+#pragma unroll
+    for (int i = 0; i < 21; ++i) m.p[i] = d2f(pd[i]);
+    return m;
+}
+
+// model-1 update on the mixed path: FP64 Joseph when the prior on the measured
+// directions exceeds the hit variance by UPDATE_FP64_RATIO (as kf_update_mixed)
+template <class Pp>
+__device__ __forceinline__ bool kf_update2d_mixed(Track<float, Pp> &st, float p[21], float hx, float hy, float hz,
+                                                  const Surf &sf, double &chi2)
+{
+    const bool informative = p[pk(0, 0)] + p[pk(1, 1)] > UPDATE_FP64_RATIO * sf.var_rphi ||
+                             p[pk(2, 2)] > UPDATE_FP64_RATIO * sf.var_zz;
+    if (informative) {
+        MixedIO m;
+        unsigned status = 0u;
+        mixed_pack(m, st, p, chi2, status);
+        m = kf_update2d_fp64_of_f32(m, hx, hy, hz, &sf);
+        return mixed_unpack(m, st, p, chi2, status);
+    }
+    return kf_update2d<false>(st, p, hx, hy, hz, sf, chi2);
+}
+template <class Pp>
+__device__ __forceinline__ bool kf_update2d_mixed(Track<double, Pp> &st, double p[21], float hx, float hy, float hz,
+                                                  const Surf &sf, double &chi2)
+{
+    return kf_update2d<false>(st, p, hx, hy, hz, sf, chi2);
+}
+
 // The first update, at the seed: the prior is seed_cov * I plus scattering
 // noise on phi and theta only, so the position block is seed_cov * I and the
 // position-angle blocks are zero.  The Joseph update then leaves the angle rows
@@ -549,6 +756,43 @@ __device__ __forceinline__ bool kf_seed_update(Track<T, Pp> &st, double p[21], f
 #pragma unroll
         for (int j = 0; j <= i; ++j)
             p[pk(i, j)] = p[pk(i, j)] - K[i][j] * c + (W[i][0] * K[j][0] + W[i][1] * K[j][1] + W[i][2] * K[j][2]);
+    return true;
+}
+
+// one surface crossing + update on surface sf; returns false when the track
+// ends here.  TWO_D: the 2-D update on the plane tangent to sf at the hit
+// (model 1, sf the hit's own cylinder).
+template <bool JOSEPH, class C, bool TWO_D, class T, class P>
+__device__ __forceinline__ bool fit_step_on(Track<T, P> &st, C p[21], int k, T alpha, T mass2, int ms_on,
+                                            const Surf &sf, float hx, float hy, float hz, double &chi2,
+                                            unsigned &status)
+{
+    T cphi, sphi;
+    if (k > 0) {
+        Jac<T> J;
+        if (!propagate(st, alpha, sf, J)) {
+            status |= KF_ST_NO_INTERSECT;
+            return false;
+        }
+        transport<C>(p, JacAs<C>::get(J));
+        cphi = J.cphi1;
+        sphi = J.sphi1;
+    } else {
+        sincos_pos(st.phi, sphi, cphi);
+    }
+    if (ms_on) status |= ms_noise<T, C>(st, sf, cphi, sphi, mass2, p);
+    bool ok;
+    if constexpr (TWO_D) {
+        if constexpr (JOSEPH) ok = kf_update2d<true>(st, p, hx, hy, hz, sf, chi2);
+        else ok = kf_update2d_mixed(st, p, hx, hy, hz, sf, chi2);
+    } else {
+        if constexpr (JOSEPH) ok = kf_update<true>(st, p, hx, hy, hz, sf, chi2);
+        else ok = kf_update_mixed(st, p, hx, hy, hz, sf, chi2);
+    }
+    if (!ok) {
+        status |= KF_ST_CHOL_FAIL;
+        return false;
+    }
     return true;
 }
 

@@ -37,6 +37,8 @@ KF_PREC_MIXED = 0
 KF_PREC_FP64 = 1
 KF_SCHED_GRID = 0
 KF_SCHED_PERSISTENT = 1
+KF_MEAS_LAYER = 0
+KF_MEAS_HIT_2D = 1
 KF_MAX_SURFACES = 64
 KF_NPHI = 1024
 KF_NZ = 64
@@ -62,7 +64,7 @@ class kf_geometry(C.Structure):
 
 class kf_fit_params(C.Structure):
     _fields_ = [("precision", C.c_int32), ("n_fp64_updates", C.c_int32), ("seed_cov", C.c_double),
-                ("ms_on", C.c_int32), ("schedule", C.c_int32)]
+                ("ms_on", C.c_int32), ("schedule", C.c_int32), ("meas_model", C.c_int32), ("pad_", C.c_int32)]
 
 
 class kf_seeds(C.Structure):
@@ -231,9 +233,10 @@ def make_geometry(geom: dict):
     return g
 
 
-def fit_params(precision=KF_PREC_MIXED, n_fp64_updates=3, seed_cov=1e4, ms_on=True, schedule=KF_SCHED_GRID):
+def fit_params(precision=KF_PREC_MIXED, n_fp64_updates=3, seed_cov=1e4, ms_on=True, schedule=KF_SCHED_GRID,
+               meas_model=KF_MEAS_LAYER):
     return kf_fit_params(precision=int(precision), n_fp64_updates=int(n_fp64_updates), seed_cov=float(seed_cov),
-                         ms_on=int(bool(ms_on)), schedule=int(schedule))
+                         ms_on=int(bool(ms_on)), schedule=int(schedule), meas_model=int(meas_model))
 
 
 # ---------------------------------------------------------------- entry points (same names as kf.h)

@@ -52,8 +52,9 @@ def make_seeds(ctx, geom, dh, stream=None):
 
 
 def fit(ctx, geom, dh, seeds, out, precision=kf.KF_PREC_MIXED, n_fp64=3, ms_on=True,
-        schedule=kf.KF_SCHED_GRID, stream=None):
-    p = kf.fit_params(precision=precision, n_fp64_updates=n_fp64, ms_on=ms_on, schedule=schedule)
+        schedule=kf.KF_SCHED_GRID, stream=None, meas_model=kf.KF_MEAS_LAYER):
+    p = kf.fit_params(precision=precision, n_fp64_updates=n_fp64, ms_on=ms_on, schedule=schedule,
+                      meas_model=meas_model)
     kf.kf_fit(ctx, geom, p, dh["n"], seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
               out["state"], out["cov"], out["chi2"], out["ndof"], out["status"], stream=stream)
 
@@ -71,13 +72,15 @@ def unpack_cov(cov21: np.ndarray) -> np.ndarray:
     return C
 
 
-def fit_numpy(ctx, geom, tk, precision=kf.KF_PREC_MIXED, n_fp64=3, ms_on=True, schedule=kf.KF_SCHED_GRID):
+def fit_numpy(ctx, geom, tk, precision=kf.KF_PREC_MIXED, n_fp64=3, ms_on=True, schedule=kf.KF_SCHED_GRID,
+              meas_model=kf.KF_MEAS_LAYER):
     """End to end on numpy CSR hits: seeds + fit on the GPU; numpy results (track-major)."""
     g = kf.make_geometry(geom)
     dh = hits_to_device(tk)
     seeds = make_seeds(ctx, g, dh)
     out = alloc_fit_out(dh["n"])
-    fit(ctx, g, dh, seeds, out, precision=precision, n_fp64=n_fp64, ms_on=ms_on, schedule=schedule)
+    fit(ctx, g, dh, seeds, out, precision=precision, n_fp64=n_fp64, ms_on=ms_on, schedule=schedule,
+        meas_model=meas_model)
     torch.cuda.synchronize()
     return dict(seed=seeds[0].t().double().cpu().numpy(), q=seeds[1].cpu().numpy(),
                 state=out["state"].t().cpu().numpy(), cov=unpack_cov(out["cov"].cpu().numpy()),
@@ -118,7 +121,7 @@ def seeds_from_seed_hits(ctx, geom, seed_hits_np, device="cuda", stream=None):
 
 
 def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, nsigma=3.0, chi2_cut=30.0,
-                max_cand=32, n_slots=0):
+                max_cand=32, n_slots=0, meas_model=kf.KF_MEAS_LAYER):
     """Bin every event's layers, seed, and run best-hit building of all events in one
     launch; returns numpy idx (n, n_layers) and fitted tracks (track-major)."""
     g = kf.make_geometry(geom)
@@ -133,12 +136,13 @@ def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, 
     idx = torch.empty((n_layers, n), dtype=torch.int32, device="cuda")
     out = alloc_fit_out(n)
     if n_slots:  # combinatorial building with n_slots candidates per seed
-        kf.kf_build_ckf(ctx, g, kf.fit_params(precision=precision), kf.build_params(nsigma, chi2_cut, max_cand),
+        kf.kf_build_ckf(ctx, g, kf.fit_params(precision=precision, meas_model=meas_model),
+                        kf.build_params(nsigma, chi2_cut, max_cand),
                         n_slots, len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
                         out["chi2"], out["ndof"], out["status"])
     else:
-        kf.kf_build_besthit(ctx, g, kf.fit_params(precision=precision), kf.build_params(nsigma, chi2_cut, max_cand,
-                                                                                           warp_coop),
+        kf.kf_build_besthit(ctx, g, kf.fit_params(precision=precision, meas_model=meas_model),
+                            kf.build_params(nsigma, chi2_cut, max_cand, warp_coop),
                             len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
                             out["chi2"], out["ndof"], out["status"])
     torch.cuda.synchronize()

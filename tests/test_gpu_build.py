@@ -242,6 +242,46 @@ def test_build_parity(ctx, oracle_mod, warp_coop, precision):
     assert tot_allowed <= 2e-3 * tot_steps
 
 
+@pytest.mark.parametrize("precision", [kf.KF_PREC_MIXED, kf.KF_PREC_FP64])
+def test_build_parity_hit_2d_staggered(ctx, oracle_mod, precision):
+    """Best-hit building under measurement model 1 (Sec. 4.1) on the staggered
+    barrel: two propagation steps per layer (the average cylinder, then each
+    candidate's own), windows widened by the layers' dr, 2-D scoring and updates."""
+    g = synth.geometry("barrel17s")
+    events = [synth.gen_event(g, 3000, synth.BASE_SEED + 31 + i) for i in range(2)]
+    gpu = run.build_numpy(ctx, g, events, precision=precision, meas_model=kf.KF_MEAS_HIT_2D)
+    t0 = 0
+    tot_steps = tot_allowed = 0
+    effs = []
+    for ev in events:
+        n = ev["n"]
+        orc = oracle_mod.build_besthit(g, _binned_oracle_event(oracle_mod, g, ev), record=True, meas_model=1)
+        gidx = gpu["idx"][t0:t0 + n]
+        steps, allowed, bad = classify_build(oracle_mod, g, ev, orc, gidx)
+        assert not bad, bad[:5]
+        tot_steps += steps
+        tot_allowed += allowed
+        same = np.all(gidx[:, 3:] == orc["idx"][:, 3:], axis=1) & ((orc["status"] & 7) == 0)
+        g_slice = {k: gpu[k][t0:t0 + n] for k in ("state", "cov", "chi2", "ndof", "status", "q")}
+        res = parity.compare_fits(g_slice, _with_oracle_q(oracle_mod, g, ev, orc), np.zeros(n, int), same)
+        print(f"model-1 build prec={precision}: {same.mean():.4f} identical tracks,", parity.summary(res))
+        ids = np.nonzero(same)[0]
+        for j in np.argsort(res["max_pull"])[-3:]:
+            t = ids[j]
+            print("  worst", int(t), res["pull"][j].round(5).tolist(), "ndof", int(orc["ndof"][t]),
+                  "oracle", orc["state"][t].tolist(), "gpu", g_slice["state"][t].tolist())
+        assert res["max_pull"].max() <= parity.TOL_PARAM_SIGMA
+        assert res["chi2rel"].max() <= parity.TOL_CHI2_REL
+        where = ev["truth_where"][:, 3:]
+        has = where >= 0
+        effs.append(np.mean(gidx[:, 3:][has] == where[has]))
+        t0 += n
+    print(f"model-1 build prec={precision}: {tot_allowed} allowed differences in {tot_steps} steps; "
+          f"true-hit efficiency {np.mean(effs):.4f}")
+    assert tot_allowed <= 2e-3 * tot_steps
+    assert np.mean(effs) > 0.85
+
+
 def _with_oracle_q(oracle_mod, g, ev, orc):
     q = np.array([oracle_mod.seed(ev["seed_hits"][t, 0], ev["seed_hits"][t, 1], ev["seed_hits"][t, 2], g["bz"])[1]
                   for t in range(ev["n"])], np.int8)
@@ -355,6 +395,8 @@ def test_ckf_rejects_bad_arguments(ctx):
         run.build_numpy(ctx, g, [ev], n_slots=3)
     with pytest.raises(kf.KfError):
         run.build_numpy(ctx, g, [ev], n_slots=4, precision=kf.KF_PREC_FP64)
+    with pytest.raises(kf.KfError):  # measurement model 1 runs on the best-hit path only
+        run.build_numpy(ctx, g, [ev], n_slots=2, meas_model=kf.KF_MEAS_HIT_2D)
 
 
 def test_gather_and_final_fit(ctx, oracle_mod):

@@ -102,6 +102,26 @@ def test_fit_parity_cylinder_with_lids(ctx, oracle_mod):
         _check_fit(tk, orc, gpu, g, label=f"lids prec={prec}", noise=noise)
 
 
+@pytest.mark.parametrize("precision", [kf.KF_PREC_MIXED, kf.KF_PREC_FP64])
+def test_fit_parity_hit_2d_staggered(ctx, oracle_mod, precision):
+    """Measurement model 1 (Sec. 4.1) on the staggered 17-layer barrel: every
+    barrel hit reached on the cylinder through it and updated in 2-D there."""
+    g = synth.geometry("barrel17s")
+    tk = synth.gen_tracks(g, 3000, synth.BASE_SEED + 21)
+    orc = oracle_mod.fit(g, tk, meas_model=1)
+    gpu = run.fit_numpy(ctx, g, tk, precision=precision, meas_model=kf.KF_MEAS_HIT_2D)
+    _check_fit(tk, orc, gpu, g, label=f"barrel17s model 1 prec={precision}")
+
+
+def test_hit_2d_rejected_where_unsupported(ctx):
+    g = synth.geometry("barrel17s")
+    tk = synth.gen_tracks(g, 100, synth.BASE_SEED + 22)
+    with pytest.raises(kf.KfError):
+        run.fit_numpy(ctx, g, tk, schedule=kf.KF_SCHED_PERSISTENT, meas_model=kf.KF_MEAS_HIT_2D)
+    with pytest.raises(kf.KfError):
+        run.fit_numpy(ctx, g, tk, meas_model=2)
+
+
 def test_persistent_schedule_matches_grid(ctx):
     g = synth.geometry("lids")
     tk = synth.gen_tracks(g, 20000, synth.BASE_SEED + 5, eta_max=2.5, min_hits=4)
@@ -184,14 +204,14 @@ def test_fit_parity_million_tracks_sampled(ctx, oracle_mod):
     assert bad.mean() < 1e-3
 
 
-def _gpu_fit_and_refit(ctx, g, tk, precision):
+def _gpu_fit_and_refit(ctx, g, tk, precision, meas_model=kf.KF_MEAS_LAYER):
     gg = kf.make_geometry(g)
     dh = run.hits_to_device(tk)
     seeds = run.make_seeds(ctx, gg, dh)
     fw = run.alloc_fit_out(dh["n"])
-    run.fit(ctx, gg, dh, seeds, fw, precision=precision)
+    run.fit(ctx, gg, dh, seeds, fw, precision=precision, meas_model=meas_model)
     bw = run.alloc_fit_out(dh["n"])
-    kf.kf_refit_inward(ctx, gg, kf.fit_params(precision=precision), dh["n"], dh["offsets"], dh["layer"], dh["x"],
+    kf.kf_refit_inward(ctx, gg, kf.fit_params(precision=precision, meas_model=meas_model), dh["n"], dh["offsets"], dh["layer"], dh["x"],
                        dh["y"], dh["z"], fw["state"], fw["cov"], seeds[1], fw["ndof"], 100.0, bw["state"],
                        bw["cov"], bw["chi2"], bw["ndof"], bw["status"])
     torch.cuda.synchronize()
@@ -201,17 +221,19 @@ def _gpu_fit_and_refit(ctx, g, tk, precision):
 
 
 @pytest.mark.parametrize("precision", [kf.KF_PREC_MIXED, kf.KF_PREC_FP64])
-@pytest.mark.parametrize("name", ["barrel10", "barrel17"])
+@pytest.mark.parametrize("name", ["barrel10", "barrel17", "barrel17s"])
 def test_refit_inward_parity(ctx, oracle_mod, name, precision):
     """Outward-inward refit: the state and covariance at the first hit, the chi2
     and ndof of the backward pass, against the oracle's refit (each side seeded
-    with its own forward fit)."""
+    with its own forward fit).  The staggered barrel runs measurement model 1
+    both ways."""
     g = synth.geometry(name)
+    model = 1 if name == "barrel17s" else 0
     tk = synth.gen_tracks(g, 3000, synth.BASE_SEED + 12)
-    fw = oracle_mod.fit(g, tk)
-    orc = oracle_mod.refit_inward(g, tk, fw["state"], fw["cov"], fw["q"], fw["ndof"])
+    fw = oracle_mod.fit(g, tk, meas_model=model)
+    orc = oracle_mod.refit_inward(g, tk, fw["state"], fw["cov"], fw["q"], fw["ndof"], meas_model=model)
     orc["q"] = fw["q"]
-    gpu = _gpu_fit_and_refit(ctx, g, tk, precision)
+    gpu = _gpu_fit_and_refit(ctx, g, tk, precision, meas_model=model)
     diff = np.nonzero((gpu["status"] & ST_BAD) != (orc["status"] & ST_BAD))[0]
     assert len(diff) == 0, [(int(t), int(gpu["status"][t]), int(orc["status"][t]), int(gpu["ndof"][t]),
                              int(orc["ndof"][t]), int(fw["ndof"][t]), int(fw["status"][t]),
