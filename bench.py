@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--tracks", type=int, default=N_TRACKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
-    ap.add_argument("--part", default="all", choices=["all", "build", "serving", "uneven", "layout"],
+    ap.add_argument("--part", default="all", choices=["all", "build", "serving", "uneven", "layout", "nonideal"],
                     help="build / serving: only that measurement, printed as its own JSON line")
     ap.add_argument("--ref-sample", type=int, default=0,
                     help="--impl reference: tracks of the workload the oracle fits per step "
@@ -180,7 +180,7 @@ BUILD_WORKLOAD = ("best-hit build of 10 events x 20,000 tracks, 17 barrel layers
                   "launch")
 
 
-def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000):
+def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000, meas_model=0, ckf_slots=(2, 4, 8)):
     """One step: bin every layer of every event (kf_bin_hits_batched), seed
     estimate from the seed hits (kf_make_seeds), best-hit build of all events
     (kf_build_besthit).  Inputs resident on the device."""
@@ -214,7 +214,7 @@ def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000):
     seed_q = torch.empty(n, dtype=torch.int8, device=dev)
     idx = torch.empty((L, n), dtype=torch.int32, device=dev)
     out = run.alloc_fit_out(n)
-    fp, bp = kf.fit_params(), kf.build_params()
+    fp, bp = kf.fit_params(meas_model=meas_model), kf.build_params()
     stream = torch.cuda.current_stream()
 
     def step(evs=None):
@@ -247,7 +247,7 @@ def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000):
 
     # combinatorial building of the same seeds: n_slots candidates per seed
     ckf = {}
-    for ns in (2, 4, 8):
+    for ns in ckf_slots:
         def ckf_launch():
             kf.kf_build_ckf(ctx, g, fp, bp, ns, n_events, L, layers, eoff, seed_st, seed_q, sh9, idx,
                             out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
@@ -269,6 +269,57 @@ def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000):
                 build_kernel_steps_per_s=units / (t_build * 1e-3), hits_binned=H, tracks=n,
                 steps_measured=steps, fraction_of_steps_with_a_hit=found, true_hit_efficiency=eff_best,
                 gpu_launches_per_step=5 + 1 + 4, combinatorial=ckf)
+
+
+NONIDEAL_WORKLOAD = ("non-ideal barrel (Sec. 4.1): 17 layers whose modules sit at alternating radii "
+                     "R - 0.25 / R + 0.25 cm (R = 4 + 6 i cm), measurement model 1 (each barrel hit reached on "
+                     "the cylinder through it, 2-D update on its tangent plane); fit of 1,000,000 tracks and "
+                     "best-hit building (two propagation steps per layer) of 10 events x 20,000 tracks")
+
+
+def nonideal_bench(ctx, steps, warmup, n_tracks=1_000_000):
+    """Measurement model 1 on the staggered barrel: the fit (kf_fit, grid schedule)
+    and best-hit building, with model 0 on the same inputs for comparison (its
+    parity against the oracle is the tests' business)."""
+    import torch
+    from paper_1711_06571_gb300 import kf, run, synth
+    geom = synth.geometry("barrel17s")
+    g = kf.make_geometry(geom)
+    tk = synth.gen_tracks(geom, n_tracks, synth.BASE_SEED + 400)
+    n = tk["n"]
+    dh = run.hits_to_device(tk)
+    seeds = run.make_seeds(ctx, g, dh)
+    stream = torch.cuda.current_stream()
+    fits = {}
+    for model in (1, 0):
+        out = run.alloc_fit_out(n)
+        p = kf.fit_params(meas_model=model)
+
+        def launch():
+            kf.kf_fit(ctx, g, p, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                      out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+        for _ in range(warmup):
+            launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            launch()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        upd = int(((out["ndof"] + 5) // 2).clamp(min=0).sum().item())
+        chi2 = out["chi2"].cpu().numpy()
+        ndof = out["ndof"].cpu().numpy()
+        good = ndof > 0
+        fits[f"model_{model}"] = dict(fit_ms_per_launch=ms, updates_per_s=upd / (ms * 1e-3),
+                                      median_chi2_per_ndof=float(np.median(chi2[good] / ndof[good])))
+    b1 = build_bench(ctx, geom, steps, warmup, meas_model=1, ckf_slots=())
+    b0 = build_bench(ctx, geom, 2, 1, meas_model=0, ckf_slots=())
+    build = dict(model_1=dict((k, b1[k]) for k in ("value", "unit", "ms_per_step", "bin_and_seed_ms",
+                                                      "build_launch_ms", "true_hit_efficiency")),
+                 model_0_true_hit_efficiency=b0["true_hit_efficiency"])
+    return dict(workload=NONIDEAL_WORKLOAD, tracks=n, fit=fits, build=build)
 
 
 UNEVEN_WORKLOAD = ("KF fit of 2,000,000 tracks, |eta| < 2.5, 17 barrel cylinders + 2 x 12 end-cap disks at "
@@ -517,6 +568,8 @@ def main():
                 r = uneven_bench(ctx, args.steps, args.warmup)
             elif args.part == "layout":
                 r = layout_study(ctx)
+            elif args.part == "nonideal":
+                r = nonideal_bench(ctx, args.steps, args.warmup)
             else:
                 rates = None if args.serving_rates == "auto" else [float(v) for v in args.serving_rates.split(",")]
                 r = serving_sweep(ctx, geom, rates, memory=args.serving_memory, zero_copy=not args.serving_copy)
@@ -645,6 +698,8 @@ def main():
     build = build_bench(ctx, geom, max(10, args.steps // 4), max(3, args.warmup // 2))
     # uneven batch: barrel + disks, persistent kernel in a CUDA graph, autotuned
     uneven = uneven_bench(ctx, max(10, args.steps // 4), max(3, args.warmup // 2))
+    # non-ideal barrel under measurement model 1
+    nonideal = nonideal_bench(ctx, max(10, args.steps // 4), max(3, args.warmup // 2))
 
     # serving loop: events of mixed sizes through kf_server (one rank's GPU each)
     serving = None
@@ -652,11 +707,11 @@ def main():
         rates = None if args.serving_rates == "auto" else [float(v) for v in args.serving_rates.split(",")]
         serving = serving_sweep(ctx, geom, rates, memory=args.serving_memory, zero_copy=not args.serving_copy)
 
-    # parity on a sample against the FP64 oracle
-    import oracle
+    # the CPU leg (rank 0): the FP64 oracle checks a sample of this run's fits, then is timed
     parity = None
     cpu_baseline = None
-    if rank == 0:
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
         sys.path.insert(0, os.path.join(ROOT, "tests"))
         import parity as par
         m = 2000
@@ -670,17 +725,16 @@ def main():
         parity = dict(tracks=int(ok.sum()), max_param_over_sigma=float(res["max_pull"].max()),
                       max_chi2_rel=float(res["chi2rel"].max()), max_cov_norm=float(res["dcov"].max()),
                       tolerance=dict(param_over_sigma=1e-3, chi2_rel=1e-3))
-        if not args.no_cpu_baseline:
-            # about 15 s of oracle work on all host cores: size the sample from a short probe
-            threads = os.cpu_count() or 1
-            _, _, dt0 = oracle_baseline(geom, tk, min(n, 50_000), threads)
-            want = 50_000 * 15.0 / max(dt0, 1e-3)  # tracks in about 15 s
-            n_sample = int(min(n, max(50_000, want)))
-            passes = max(1, int(round(want / n_sample)))
-            v, upd, dt = oracle_baseline(geom, tk, n_sample, threads, passes)
-            cpu_baseline = dict(value=v, unit=UNIT, cores=threads, kind="oracle",
-                                sample=f"first {n_sample} tracks of the workload, {passes} pass(es) "
-                                       f"({upd} updates, {dt:.1f} s)")
+        # about 15 s of oracle work on all host cores: size the sample from a short probe
+        threads = os.cpu_count() or 1
+        _, _, dt0 = oracle_baseline(geom, tk, min(n, 50_000), threads)
+        want = 50_000 * 15.0 / max(dt0, 1e-3)  # tracks in about 15 s
+        n_sample = int(min(n, max(50_000, want)))
+        passes = max(1, int(round(want / n_sample)))
+        v, upd, dt = oracle_baseline(geom, tk, n_sample, threads, passes)
+        cpu_baseline = dict(value=v, unit=UNIT, cores=threads, kind="oracle",
+                            sample=f"first {n_sample} tracks of the workload, {passes} pass(es) "
+                                   f"({upd} updates, {dt:.1f} s)")
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
@@ -695,7 +749,7 @@ def main():
                 fp64_path=dict(value=updates_per_step * world / (ms64 * 1e-3), unit=UNIT, fit_ms=ms64,
                                speedup_of_mixed=ms64 / fit_avg),
                 gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity, build=build, uneven_batch=uneven,
-                serving=serving)
+                nonideal=nonideal, serving=serving)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -74,7 +74,8 @@ extern "C" {
                             it (its module sits up to dr off the layer radius); the
                             track is carried to that cylinder and updated with the
                             two coordinates measured on the plane tangent to it at the
-                            hit (r-phi and z; disk hits keep KF_MEAS_LAYER).  Best-hit
+                            hit (r-phi and z; disk hits keep KF_MEAS_LAYER).  The first
+                            hit of a fit, where the state starts, keeps the 3-D update.  Best-hit
                             building takes two steps per layer: to the layer's average
                             cylinder (scattering noise and the window, widened by dr,
                             there), then to each candidate's cylinder to score it.

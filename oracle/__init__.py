@@ -303,7 +303,8 @@ def fit_one(geom, layer, hx, hy, hz, seed_state, q, seed_cov=1e4, ms_on=True, li
 
 def fit(geom, hits, seeds=None, q=None, seed_cov=1e4, ms_on=True, t0=0, t1=None, threads=1, meas_model=0):
     """Fit every track of a CSR hit set.  hits: dict offsets (n+1,), layer, x, y, z.
-    meas_model 1: barrel hits on their own radius, 2-D update (non-ideal geometry).
+    meas_model 1: barrel hits after the first reached on their own radius, 2-D update there
+    (non-ideal geometry); the first hit, where the state starts, takes the 3-D update.
     Returns dict with seed, q, state (n,6), cov (n,6,6), chi2, ndof, status."""
     cfg = fit_cfg(geom, seed_cov, ms_on, meas_model)
     sarr = surfaces(geom)

@@ -581,7 +581,11 @@ typedef struct {
 /* measurement model 1 (Sec. 4.1, non-ideal geometry): a barrel hit need  */
 /* not lie on its layer's average cylinder; the state is carried to the   */
 /* cylinder through the hit and updated on the plane tangent to it there, */
-/* with the two coordinates measured on that plane: r-phi and z.          */
+/* with the two coordinates measured on that plane: r-phi and z.  The    */
+/* first hit of a fit is the exception: the state starts there, with no   */
+/* propagation, so the hit's radius is the state's own and the update is  */
+/* the 3-D one of model 0 (a reading: the surface's radial resolution     */
+/* sig_n then fixes the start on the hit's cylinder).                     */
 /* ------------------------------------------------------------------ */
 
 /* the cylinder through a barrel hit: the layer surface with the hit's radius */
@@ -694,7 +698,7 @@ static unsigned or_fit_from(const or_fit_cfg *cfg, const or_surf *surfs, int nh,
     *n_used = 0;
     for (k = 0; k < nh; ++k) {
         double hit[3] = {(double)hx[k], (double)hy[k], (double)hz[k]};
-        const int m1 = cfg->meas_model == 1 && surfs[layer[k]].kind == 0;
+        const int m1 = cfg->meas_model == 1 && k > 0 && surfs[layer[k]].kind == 0;
         const or_surf hcyl = hit_cylinder(&surfs[layer[k]], hit);
         const or_surf *sf = m1 ? &hcyl : &surfs[layer[k]];
         double Rm[9], chi2 = 0.0;

@@ -478,7 +478,7 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
                     hz = a.seed_hits[(3 * k + 2) * n + t];
         if constexpr (M1) {
-            if (sf.kind == 0) {
+            if (k > 0 && sf.kind == 0) {  // the first hit: the 3-D update (the state starts on it)
                 const Surf h = hit_surface(sf, hx, hy);
                 alive = fit_step_on<true, double, true>(st, pd, k, alpha, mass2, a.ms_on, h, hx, hy, hz, chi2,
                                                         status);
@@ -519,7 +519,7 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
                     hz = a.seed_hits[(3 * k + 2) * n + t];
         if constexpr (M1) {
-            if (sf.kind == 0) {
+            if (k > 0 && sf.kind == 0) {  // the first hit: the 3-D update (the state starts on it)
                 const Surf h = hit_surface(sf, hx, hy);
                 alive = fit_step_on<false, C, true>(st, pc, k, alpha, mass2, a.ms_on, h, hx, hy, hz, chi2, status);
                 if (!alive) break;
@@ -598,9 +598,6 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
         StepOut so{-1, false};
         bool near_tangent = false;
         if constexpr (!FP64) near_tangent = alive && crossing_sine(st, alpha, sf) > 0.8f;
-        // model 1: the first update after the seed hits is strongly informative
-        // (six seed coordinates for five parameters) and runs in FP64 as well
-        if constexpr (!FP64 && M1) near_tangent = near_tangent || (alive && a.n64 > 0 && used < 4);
         if (near_tangent) {
             if constexpr (!FP64) {
                 Fp64LayerIO io;

@@ -122,14 +122,15 @@ struct FitTypes {
 };
 
 // one hit on layer surface sf.  M1 (measurement model 1, Sec. 4.1): a barrel
-// hit is reached on the cylinder through it and measured in 2-D there.
+// hit after the first (k > 0; the state starts on the first) is reached on the
+// cylinder through it and measured in 2-D there.
 template <bool JOSEPH, class C, bool M1 = false, class T, class P>
 __device__ __forceinline__ bool fit_step(Track<T, P> &st, C p[21], int k, T alpha, T mass2, int ms_on,
                                          const Surf &sf, float hx, float hy, float hz, double &chi2,
                                          unsigned &status)
 {
     if constexpr (M1) {
-        if (sf.kind == 0) {
+        if (k > 0 && sf.kind == 0) {
             const Surf h = hit_surface(sf, hx, hy);
             return fit_step_on<JOSEPH, C, true>(st, p, k, alpha, mass2, ms_on, h, hx, hy, hz, chi2, status);
         }
@@ -289,10 +290,6 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
     if (a.n64 > 0 && nh >= 3) {
         const int s2 = seed_hit_last(a.hx + o0, a.hy + o0, nh);
         n1 = max(n1, s2 + 1);
-        // model 1: the three seed hits measure six coordinates for five track
-        // parameters (the first hit's radial position stays at the seed prior),
-        // so the next update is still a strongly informative one: FP64 too
-        if (M1) n1 = max(n1, s2 + 2);
     }
     n1 = min(n1, nh);
     if (n1 > 0) {
@@ -300,18 +297,11 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         const Surf &sf = surf[a.layer[o0]];
         T cphi, sphi;
         sincos_pos(st.phi, sphi, cphi);
-        bool ok0;
-        if (M1 && sf.kind == 0) {
-            // model 1: the seed sits at the hit; the 2-D update on the hit's cylinder
-            const Surf h = hit_surface(sf, a.hx[o0], a.hy[o0]);
-            if (a.ms_on) status |= ms_noise<T, double>(st, h, cphi, sphi, mass2, pd);
-            ok0 = kf_update2d<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], h, chi2);
-        } else {
-            if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
-            // the structured update needs the diagonal seed covariance; a given one takes the general form
-            ok0 = a.p0 ? kf_update<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)
-                       : kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
-        }
+        // (under model 1 as well: the state starts at this hit, on its own radius)
+        if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
+        // the structured update needs the diagonal seed covariance; a given one takes the general form
+        const bool ok0 = a.p0 ? kf_update<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)
+                              : kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
         if (ok0) {
             ++used;
             k = 1;

@@ -288,12 +288,14 @@ def _with_oracle_q(oracle_mod, g, ev, orc):
     return dict(orc, q=q)
 
 
-def test_build_full_size_sampled(ctx, oracle_mod):
+@pytest.mark.parametrize("name,model", [("barrel17", 0), ("barrel17s", 1)])
+def test_build_full_size_sampled(ctx, oracle_mod, name, model):
     """Ten events of 20,000 tracks with 20% noise in one launch; the oracle checks 300
-    tracks of each event against the same binned layers."""
-    g = synth.geometry("barrel17")
+    tracks of each event against the same binned layers.  The staggered barrel runs
+    measurement model 1."""
+    g = synth.geometry(name)
     events = [synth.gen_event(g, 20000, synth.BASE_SEED + 3 + i) for i in range(10)]
-    gpu = run.build_numpy(ctx, g, events)
+    gpu = run.build_numpy(ctx, g, events, meas_model=model)
     t0 = 0
     tot = [0, 0]
     eff = []
@@ -301,7 +303,7 @@ def test_build_full_size_sampled(ctx, oracle_mod):
         n = ev["n"]
         ev = _binned_oracle_event(oracle_mod, g, ev)
         sel = np.sort(np.random.default_rng(t0).choice(n, 300, replace=False))
-        orc = oracle_mod.build_besthit(g, ev, record=True)  # all tracks: the oracle is fast enough
+        orc = oracle_mod.build_besthit(g, ev, record=True, meas_model=model)  # all tracks: fast enough
         steps, allowed, bad = classify_build(oracle_mod, g, ev, orc, gpu["idx"][t0:t0 + n], sel)
         assert not bad, bad[:5]
         tot[0] += steps
@@ -313,7 +315,7 @@ def test_build_full_size_sampled(ctx, oracle_mod):
                     np.mean(orc["idx"][sel, 3:][has] == where[has])))
         t0 += n
     eg, eo = np.mean(eff, axis=0)
-    print(f"full size: {tot[1]} allowed differences in {tot[0]} sampled steps; "
+    print(f"full size {name} model {model}: {tot[1]} allowed differences in {tot[0]} sampled steps; "
           f"true-hit efficiency GPU {eg:.4f}, oracle {eo:.4f}")
     assert abs(eg - eo) <= 2e-3 * max(1, tot[1])
     assert eg > 0.85
