@@ -666,6 +666,27 @@ def main():
     torch.cuda.synchronize()
     ms64 = a.elapsed_time(b) / reps
 
+    # outward-inward refit of the same tracks from the forward fit (kf_refit_inward)
+    outr = run.alloc_fit_out(n)
+
+    def refit():
+        kf.kf_refit_inward(ctx, g, params, n, dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"], out["state"],
+                           out["cov"], seeds[1], out["ndof"], 100.0, outr["state"], outr["cov"], outr["chi2"],
+                           outr["ndof"], outr["status"])
+    for _ in range(2):
+        refit()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        refit()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_refit = a.elapsed_time(b) / reps
+    refit_updates = int(((outr["ndof"] + 5) // 2).clamp(min=0).sum().item())
+    refit_line = dict(value=refit_updates / (ms_refit * 1e-3), unit=UNIT, ms_per_launch=ms_refit,
+                      updates=refit_updates, what="reverse the used hits and the forward state (covariance x 100), "
+                                                  "fit inwards, turn the result back")
+
     # end to end through the C ABI with host buffers (page-locked), copies inside
     hh = dict(offsets=torch.from_numpy(tk["offsets"]).pin_memory(), layer=torch.from_numpy(tk["layer"]).pin_memory(),
               x=torch.from_numpy(tk["x"]).pin_memory(), y=torch.from_numpy(tk["y"]).pin_memory(),
@@ -749,7 +770,7 @@ def main():
                 fp64_path=dict(value=updates_per_step * world / (ms64 * 1e-3), unit=UNIT, fit_ms=ms64,
                                speedup_of_mixed=ms64 / fit_avg),
                 gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity, build=build, uneven_batch=uneven,
-                nonideal=nonideal, serving=serving)
+                refit_inward=refit_line, nonideal=nonideal, serving=serving)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

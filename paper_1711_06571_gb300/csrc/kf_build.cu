@@ -113,13 +113,13 @@ __device__ __forceinline__ double cand_chi2(const Track<T, P> &st, const float p
 // position block of its covariance, and the 2-D chi2 there; -1 when the hit's
 // cylinder is out of reach or S is not positive definite.
 template <class T, class P, class C>
-__device__ __forceinline__ double cand_chi2_m1(const Track<T, P> &st, const C pc[21], const Surf &sf, T alpha,
-                                               float4 h)
+__device__ __forceinline__ double cand_chi2_m1(const Track<T, P> &st, const Dir<T> &dir, const C pc[21],
+                                               const Surf &sf, T alpha, float4 h)
 {
     const Surf hs = hit_surface(sf, h.x, h.y);
     Track<T, P> s2 = st;
     Jac<T> J;
-    if (!propagate(s2, alpha, hs, J)) return -1.0;
+    if (!propagate_from(s2, alpha, hs, J, dir)) return -1.0;
     C q[6];
     transport_pos<C>(pc, JacAs<C>::get(J), q);
     return kf_chi2_2d(s2, q, h.x, h.y, h.z, hs);
@@ -145,6 +145,8 @@ __device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[
                                           bool &capped)
 {
     int ncand = 0;
+    Dir<T> dir;
+    if constexpr (M1) dir = direction(st);  // shared by the candidates' second steps
     for (int zb = w.z_lo; zb <= w.z_hi && !capped; ++zb) {
         const int row = zb * KF_NPHI;
         const int first = w.phi_lo, last = w.phi_lo + w.nphi - 1;
@@ -167,7 +169,7 @@ __device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[
                 ++ncand;
                 const float4 h = ly.packed[j];
                 double c2;
-                if constexpr (M1) c2 = cand_chi2_m1(st, pc, sf, alpha, h);
+                if constexpr (M1) c2 = cand_chi2_m1(st, dir, pc, sf, alpha, h);
                 else c2 = cand_chi2(st, pw, sf, shared, fs, h);
                 const int hi = __float_as_int(h.w);
                 if (c2 >= 0.0 && (best < 0 || c2 < bchi || (c2 == bchi && hi < best))) {
@@ -567,7 +569,10 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i0 < a.n;
     const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real track but write nothing
-    const int t = a.order ? a.order[i] : i;
+    // the order runs from high to low seed pT; walked backwards, the costliest
+    // tracks (low pT: wider windows, more near-tangent FP64 steps) start in the
+    // first wave of blocks and the cheap ones fill the tail
+    const int t = a.order ? a.order[a.n - 1 - i] : i;
     const int n = a.n;
     const int e = find_event(a.event_off, a.n_events, t);
     const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
@@ -827,7 +832,7 @@ __global__ void __launch_bounds__(128, 3) ckf_kernel(const Geom g, const CkfArgs
     const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) / NS;
     const bool active = i0 < a.n;
     const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real seed but write nothing
-    const int t = a.order ? a.order[i] : i;
+    const int t = a.order ? a.order[a.n - 1 - i] : i;  // costliest (low-pT) seeds first, as build_kernel
     const int n = a.n;
     const size_t nslots = (size_t)n * NS;
     const int e = find_event(a.event_off, a.n_events, t);

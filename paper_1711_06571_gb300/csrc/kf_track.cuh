@@ -75,14 +75,26 @@ constexpr float MAX_PATH = 1.0e6f;  // longer transverse paths count as no inter
 // the second-order (parabolic) estimate; from outside: the crossing nearest s = 0.  Disk: s = (Z - z) tan(theta).
 // alpha = -q * kappa * Bz (c = alpha / pT).  Returns false (state untouched)
 // when the surface is not reached.
+// The direction's sines and cosines of the state, which several propagations of
+// the same state share (propagate_from).
+template <class T>
+struct Dir {
+    T sphi, cphi, sth, cth;
+};
 template <class T, class P>
-__device__ __forceinline__ bool propagate(Track<T, P> &st, T alpha, const Surf &sf, Jac<T> &J)
+__device__ __forceinline__ Dir<T> direction(const Track<T, P> &st)
+{
+    Dir<T> d;
+    sincos_pos(st.phi, d.sphi, d.cphi);
+    sincos_pos(st.th, d.sth, d.cth);
+    return d;
+}
+
+template <class T, class P>
+__device__ __forceinline__ bool propagate_from(Track<T, P> &st, T alpha, const Surf &sf, Jac<T> &J, const Dir<T> &d)
 {
     T c = alpha * st.ip;
-    T sphi, cphi;
-    sincos_pos(st.phi, sphi, cphi);
-    T sth, cth;
-    sincos_pos(st.th, sth, cth);
+    const T sphi = d.sphi, cphi = d.cphi, sth = d.sth, cth = d.cth;
     T cot = cth / sth;
     T s;
     const T X = lead(st.x), Y = lead(st.y);
@@ -169,6 +181,12 @@ __device__ __forceinline__ bool propagate(Track<T, P> &st, T alpha, const Surf &
     st.y = ny;
     st.phi = wrap(inc(st.phi, c * s));
     return true;
+}
+
+template <class T, class P>
+__device__ __forceinline__ bool propagate(Track<T, P> &st, T alpha, const Surf &sf, Jac<T> &J)
+{
+    return propagate_from(st, alpha, sf, J, direction(st));
 }
 
 // Sine of the angle between track and radial direction where the helix meets
@@ -569,16 +587,21 @@ __device__ __forceinline__ bool kf_update_mixed_factored(Track<float, Pp> &st, f
 // H has rows t = (-sin a, cos a, 0, ..) and (0, 0, 1, ..), a the hit azimuth;
 // R = diag(sig_rphi^2, sig_z^2); chi2 and S^-1 from a 2x2 LDL^T in FP64.
 
-// the cylinder through a barrel hit: R^2 = hx^2 + hy^2 (exact in FP64 to the
-// last bit of the sum), carried as a float-float for the FP32 propagation
+// the cylinder through a barrel hit: R^2 = hx^2 + hy^2 as a float-float (the
+// squares exact by FMA, their sum by two_sum; about 48 bits) for the FP32
+// propagation, R in FP64 for the FP64 one
 __device__ __forceinline__ Surf hit_surface(const Surf &sf, float hx, float hy)
 {
     Surf h = sf;
-    const double r2 = fma((double)hx, (double)hx, (double)hy * (double)hy);
-    h.pos2 = (float)r2;
-    h.pos2lo = (float)(r2 - (double)h.pos2);
+    const float p1 = __fmul_rn(hx, hx), e1 = fmaf(hx, hx, -p1);
+    const float p2 = __fmul_rn(hy, hy), e2 = fmaf(hy, hy, -p2);
+    float s, e;
+    two_sum(p1, p2, s, e);
+    const float lo = e + (e1 + e2);
+    h.pos2 = s + lo;
+    h.pos2lo = lo - (h.pos2 - s);
     h.pos = sqrtf(h.pos2);
-    h.posd = sqrt(r2);
+    h.posd = sqrt((double)h.pos2 + (double)h.pos2lo);
     return h;
 }
 
@@ -658,7 +681,9 @@ __device__ __forceinline__ bool kf_update2d(Track<T, Pp> &st, C p[21], float hx,
 }
 
 // chi2 of a hit under model 1 without the update (the S of kf_update2d), or -1
-// when S is not positive definite
+// when S is not positive definite: chi2 = (s22 rt^2 - 2 s21 rt rz + s11 rz^2) /
+// det S in FP64 from the entries of S and the residual in C (the candidate
+// score of a build step; the update recomputes chi2 through its LDL^T factor).
 template <class C, class T, class Pp>
 __device__ __forceinline__ double kf_chi2_2d(const Track<T, Pp> &st, const C p[21], float hx, float hy, float hz,
                                              const Surf &sf)
@@ -671,12 +696,11 @@ __device__ __forceinline__ double kf_chi2_2d(const Track<T, Pp> &st, const C p[2
     const C g0 = -sa * p[pk(0, 0)] + ca * p[pk(1, 0)], g1 = -sa * p[pk(1, 0)] + ca * p[pk(1, 1)];
     const double e11 = wide(C(-sa * g0 + ca * g1 + vt));
     const double e21 = wide(C(-sa * p[pk(2, 0)] + ca * p[pk(2, 1)])), e22 = wide(C(p[pk(2, 2)] + vz));
-    if (!(e11 > 0.0)) return -1.0;
-    const double i1 = rcp_d(e11), l21 = e21 * i1, d2 = fma(-l21, e21, e22);
-    if (!(d2 > 0.0)) return -1.0;
-    const double rt = -wide(sa) * wide(C(r0)) + wide(ca) * wide(C(r1)), rz = wide(C(r2));
-    const double z2 = fma(-l21, rt, rz);
-    return fma(z2 * rcp_d(d2), z2, rt * i1 * rt);
+    const double det = fma(e11, e22, -e21 * e21);
+    if (!(e11 > 0.0) || !(det > 0.0)) return -1.0;
+    const double rt = wide(C(-sa * C(r0) + ca * C(r1))), rz = wide(C(r2));
+    const double num = fma(e22 * rt, rt, fma(-2.0 * e21 * rt, rz, e11 * rz * rz));
+    return num * rcp_d(det);
 }
 
 // the FP64 Joseph 2-D update of an FP32 covariance, out of line
