@@ -482,8 +482,11 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         if constexpr (M1) {
             if (k > 0 && sf.kind == 0) {  // the first hit: the 3-D update (the state starts on it)
                 const Surf h = hit_surface(sf, hx, hy);
-                alive = fit_step_on<true, double, true>(st, pd, k, alpha, mass2, a.ms_on, h, hx, hy, hz, chi2,
-                                                        status);
+                // k == 1: the covariance is the one the structured seed-hit update left
+                alive = k == 1 ? fit_step_on<true, double, true, true>(st, pd, k, alpha, mass2, a.ms_on, h, hx, hy,
+                                                                       hz, chi2, status)
+                               : fit_step_on<true, double, true>(st, pd, k, alpha, mass2, a.ms_on, h, hx, hy, hz,
+                                                                 chi2, status);
                 if (!alive) break;
                 ++used;
                 continue;
@@ -497,7 +500,9 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
                 alive = false;
                 break;
             }
-            transport<double>(pd, JacAs<double>::get(J));
+            // k == 1: the covariance is the one the structured seed-hit update left
+            if (k == 1) transport_seeded<double>(pd, JacAs<double>::get(J));
+            else transport<double>(pd, JacAs<double>::get(J));
             cphi = J.cphi1;
             sphi = J.sphi1;
         } else {
