@@ -753,9 +753,14 @@ def main():
         n_sample = int(min(n, max(50_000, want)))
         passes = max(1, int(round(want / n_sample)))
         v, upd, dt = oracle_baseline(geom, tk, n_sample, threads, passes)
+        # and on one host thread, about 5 s
+        n1 = int(min(n, max(5_000, 50_000 * 5.0 / (max(dt0, 1e-3) * threads))))
+        v1, upd1, dt1 = oracle_baseline(geom, tk, n1, 1)
         cpu_baseline = dict(value=v, unit=UNIT, cores=threads, kind="oracle",
                             sample=f"first {n_sample} tracks of the workload, {passes} pass(es) "
-                                   f"({upd} updates, {dt:.1f} s)")
+                                   f"({upd} updates, {dt:.1f} s)",
+                            single_thread=dict(value=v1, unit=UNIT, cores=1,
+                                               sample=f"first {n1} tracks ({upd1} updates, {dt1:.1f} s)"))
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
