@@ -219,8 +219,8 @@ int kf_fit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, in
  *     [n], its ndof.  cov_scale > 0.
  *   out: device, state and covariance at the first hit (forward direction),
  *     chi2 and ndof of the backward pass, status.
- * Blocks until offsets[n] is read; the rest runs on the stream (kf_fit's
- * schedule and precision from params). */
+ * Blocks until offsets[n] is read; the rest runs on the stream (precision and
+ * measurement model from params; always the grid schedule). */
 int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
                     const kf_track_hits *hits, const double *fwd_state, const double *fwd_cov, const int8_t *q,
                     const int32_t *fwd_ndof, double cov_scale, const kf_tracks_out *out, void *stream);

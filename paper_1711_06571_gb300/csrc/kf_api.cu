@@ -411,6 +411,7 @@ int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     kf_fit_params P;
     int rc = check_fit_params(ctx, params, P);
     if (rc) return rc;
+    P.schedule = KF_SCHED_GRID;  // the refit's fit runs on the grid schedule
     Geom G;
     if ((rc = to_geom(ctx, geom, G))) return rc;
     if ((rc = set_dev(ctx))) return rc;

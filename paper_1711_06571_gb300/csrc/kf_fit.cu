@@ -250,7 +250,9 @@ __device__ __forceinline__ void store_cov(double *o_cov, int n, int t, const C p
     for (int i = 0; i < 21; ++i) o_cov[(size_t)i * n + t] = (double)p[i];
 }
 
-template <bool FP64, bool M1 = false>
+// P0: the initial covariance is a.p0_scale * a.p0 (the refit), not seed_cov * I;
+// a separate instance, so that the plain fit does not carry the general first update.
+template <bool FP64, bool M1 = false, bool P0 = false>
 __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *surf, float kb, float mass2f,
                                           double kbd, double mass2d)
 {
@@ -273,7 +275,7 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
     int used = 0, k = 0;
     bool alive = true;
     double pd[21];
-    if (a.p0) {
+    if constexpr (P0) {
 #pragma unroll
         for (int i = 0; i < 21; ++i) pd[i] = a.p0_scale * a.p0[(size_t)i * n + t];
     } else {
@@ -300,8 +302,9 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         // (under model 1 as well: the state starts at this hit, on its own radius)
         if (a.ms_on) status |= ms_noise<T, double>(st, sf, cphi, sphi, mass2, pd);
         // the structured update needs the diagonal seed covariance; a given one takes the general form
-        const bool ok0 = a.p0 ? kf_update<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2)
-                              : kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
+        bool ok0;
+        if constexpr (P0) ok0 = kf_update<true>(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
+        else ok0 = kf_seed_update(st, pd, a.hx[o0], a.hy[o0], a.hz[o0], sf, chi2);
         if (ok0) {
             ++used;
             k = 1;
@@ -314,7 +317,9 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         const int h = o0 + k;
         const Surf &sf = surf[a.layer[h]];
         bool ok;
-        if constexpr (!FP64) {
+        // the refit meets a track's near-tangent crossings (its outer end) among its
+        // first updates: there the FP64-covariance step also propagates in FP64
+        if constexpr (!FP64 && P0) {
             if (grazing_crossing<M1>(st, alpha, sf, a.hx[h], a.hy[h])) {
                 MixedIOD m;
                 m.st = st;
@@ -386,7 +391,7 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
     if (a.o_status) a.o_status[t] = status;
 }
 
-template <bool FP64, bool M1>
+template <bool FP64, bool M1, bool P0>
 __global__ void __launch_bounds__(128) fit_kernel(const Geom g, const FitArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(128) fit_kernel(const Geom g, const FitArgs a)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.count) return;
     const int t = a.t_begin + (a.order ? a.order[i] : i);
-    fit_track<FP64, M1>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
+    fit_track<FP64, M1, P0>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
 }
 
 // Persistent form: a grid sized to the machine; each block takes
@@ -534,12 +539,21 @@ cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cu
     (void)block;
     const int b = 128;
     const int grid = (a.count + b - 1) / b;
-    if (a.meas_model == 1) {
-        if (fp64) fit_kernel<true, true><<<grid, b, 0, st>>>(g, a);
-        else fit_kernel<false, true><<<grid, b, 0, st>>>(g, a);
+    const bool m1 = a.meas_model == 1, p0 = a.p0 != nullptr;
+    if (p0) {  // the refit
+        if (m1) {
+            if (fp64) fit_kernel<true, true, true><<<grid, b, 0, st>>>(g, a);
+            else fit_kernel<false, true, true><<<grid, b, 0, st>>>(g, a);
+        } else {
+            if (fp64) fit_kernel<true, false, true><<<grid, b, 0, st>>>(g, a);
+            else fit_kernel<false, false, true><<<grid, b, 0, st>>>(g, a);
+        }
+    } else if (m1) {
+        if (fp64) fit_kernel<true, true, false><<<grid, b, 0, st>>>(g, a);
+        else fit_kernel<false, true, false><<<grid, b, 0, st>>>(g, a);
     } else {
-        if (fp64) fit_kernel<true, false><<<grid, b, 0, st>>>(g, a);
-        else fit_kernel<false, false><<<grid, b, 0, st>>>(g, a);
+        if (fp64) fit_kernel<true, false, false><<<grid, b, 0, st>>>(g, a);
+        else fit_kernel<false, false, false><<<grid, b, 0, st>>>(g, a);
     }
     return cudaGetLastError();
 }
@@ -559,7 +573,8 @@ static cudaError_t launch_pers(const Geom &g, const FitArgs &a, int block, int g
 cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, int block, int grid, cudaStream_t st)
 {
     if (a.count <= 0) return cudaSuccess;
-    if (a.meas_model != 0) return cudaErrorInvalidValue;  // model 1 runs on the grid schedule
+    // model 1 and the refit's initial covariance run on the grid schedule
+    if (a.meas_model != 0 || a.p0) return cudaErrorInvalidValue;
     return fp64 ? launch_pers<true>(g, a, block, grid, st) : launch_pers<false>(g, a, block, grid, st);
 }
 
