@@ -574,10 +574,7 @@ __global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const Build
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i0 < a.n;
     const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real track but write nothing
-    // the order runs from high to low seed pT; walked backwards, the costliest
-    // tracks (low pT: wider windows, more near-tangent FP64 steps) start in the
-    // first wave of blocks and the cheap ones fill the tail
-    const int t = a.order ? a.order[a.n - 1 - i] : i;
+    const int t = a.order ? a.order[i] : i;
     const int n = a.n;
     const int e = find_event(a.event_off, a.n_events, t);
     const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
@@ -837,7 +834,7 @@ __global__ void __launch_bounds__(128, 3) ckf_kernel(const Geom g, const CkfArgs
     const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) / NS;
     const bool active = i0 < a.n;
     const int i = active ? i0 : a.n - 1;  // inactive lanes shadow a real seed but write nothing
-    const int t = a.order ? a.order[a.n - 1 - i] : i;  // costliest (low-pT) seeds first, as build_kernel
+    const int t = a.order ? a.order[i] : i;
     const int n = a.n;
     const size_t nslots = (size_t)n * NS;
     const int e = find_event(a.event_off, a.n_events, t);

@@ -604,10 +604,12 @@ int persistent_blocks_per_sm(bool fp64, int block)
 // ------------------------------------------------------------------ processing order
 
 // Counting sort of the tracks into buckets of (hit count, descending) x (seed
-// |1/pT|, 64 bins of 1/32 GeV^-1, clamped): a warp then takes 32 tracks that
-// cross nearly the same layers and bend alike, so the layer loop and the
-// near-tangent FP64 steps (low-pT tracks at their apex) diverge little.  The
-// order inside a bucket is that of the atomics, which does not change any
+// |1/pT|, 64 bins of 1/32 GeV^-1, clamped, descending): a warp then takes 32
+// tracks that cross nearly the same layers and bend alike, so the layer loop and
+// the near-tangent FP64 steps (low-pT tracks at their apex) diverge little, and
+// the costliest tracks (most hits, then lowest pT: widest build windows, most
+// near-tangent steps) come first, so that the short ones fill the launch's tail.
+// The order inside a bucket is that of the atomics, which does not change any
 // track's result.
 constexpr int ORDER_BUCKETS = 65 * 64;
 
@@ -615,7 +617,7 @@ __device__ __forceinline__ int order_key(const int32_t *__restrict__ off, const 
 {
     const int nh = off ? min(off[t + 1] - off[t], 64) : 0;
     const int b = min((int)(fabsf(ip[t]) * 32.f), 63);
-    return (64 - nh) * 64 + b;
+    return (64 - nh) * 64 + (63 - b);
 }
 // Histogram and scatter count in shared memory per block and touch global
 // memory once per non-empty bucket and block: the keys of neighbouring tracks
