@@ -32,15 +32,16 @@ WORKLOAD = ("KF fit of 1,000,000 tracks x 17 barrel layers (R 4-100 cm), Bz 3.8 
             "pT log-uniform 0.5-10 GeV, |eta|<1, seeds from 3 hits, seed cov 1e4")
 
 # Algorithmic work per unit, counted from the formulas the fit kernel evaluates:
-# FP64 FLOP of the seed phase per track (structured seed-hit update 187, two
-# covariance transports 2 x 310, two Joseph updates 2 x 542, noise 6) and of the
+# FP64 FLOP of the seed phase per track (structured seed-hit update 187, the
+# first transport on the covariance that update leaves 151, the second 310, two
+# Joseph updates 2 x 542, noise 6) and of the
 # FP64 S solve per later update (LDL^T 29 + chi2 15); FP32 FLOP per later update
 # (propagation ~250, transport 310, noise ~25, update ~314).
 # DRAM bytes (read + write) of one fit-kernel launch on this workload, from an
 # ncu capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
 # set to None whenever the kernel changes until it is captured again
-FIT_KERNEL_DRAM_BYTES = 3.272e9
-FP64_FLOP_SEED_PHASE = 1897.0
+FIT_KERNEL_DRAM_BYTES = None
+FP64_FLOP_SEED_PHASE = 1738.0
 FP64_FLOP_PER_FP32_UPDATE = 44.0
 FP32_FLOP_PER_FP32_UPDATE = 900.0
 

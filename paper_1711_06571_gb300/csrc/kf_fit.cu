@@ -127,15 +127,16 @@ struct FitTypes {
 template <bool JOSEPH, class C, bool M1 = false, class T, class P>
 __device__ __forceinline__ bool fit_step(Track<T, P> &st, C p[21], int k, T alpha, T mass2, int ms_on,
                                          const Surf &sf, float hx, float hy, float hz, double &chi2,
-                                         unsigned &status)
+                                         unsigned &status, bool seeded = false)
 {
     if constexpr (M1) {
         if (k > 0 && sf.kind == 0) {
             const Surf h = hit_surface(sf, hx, hy);
-            return fit_step_on<JOSEPH, C, true>(st, p, k, alpha, mass2, ms_on, h, hx, hy, hz, chi2, status);
+            return fit_step_on<JOSEPH, C, true>(st, p, k, alpha, mass2, ms_on, h, hx, hy, hz, chi2, status,
+                                                seeded);
         }
     }
-    return fit_step_on<JOSEPH, C, false>(st, p, k, alpha, mass2, ms_on, sf, hx, hy, hz, chi2, status);
+    return fit_step_on<JOSEPH, C, false>(st, p, k, alpha, mass2, ms_on, sf, hx, hy, hz, chi2, status, seeded);
 }
 
 // Sine of the crossing angle above which a mixed-path step runs in FP64:
@@ -340,8 +341,9 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
                                                 chi2, status);
             }
         } else {
+            // k == 1 after the structured seed-hit update: the transport skips its zero blocks
             ok = fit_step<true, double, M1>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
-                                            status);
+                                            status, !P0 && k == 1);
         }
         if (!ok) {
             alive = false;

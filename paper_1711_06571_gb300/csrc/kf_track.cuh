@@ -850,11 +850,12 @@ __device__ __forceinline__ bool kf_seed_update(Track<T, Pp> &st, double p[21], f
 // one surface crossing + update on surface sf; returns false when the track
 // ends here.  TWO_D: the 2-D update on the plane tangent to sf at the hit
 // (model 1, sf the hit's own cylinder).
-// SEEDED: P is the one left by the structured first update (transport_seeded).
+// SEEDED, or seeded at run time: P is the one left by the structured first
+// update (transport_seeded).
 template <bool JOSEPH, class C, bool TWO_D, bool SEEDED = false, class T, class P>
 __device__ __forceinline__ bool fit_step_on(Track<T, P> &st, C p[21], int k, T alpha, T mass2, int ms_on,
                                             const Surf &sf, float hx, float hy, float hz, double &chi2,
-                                            unsigned &status)
+                                            unsigned &status, bool seeded = false)
 {
     T cphi, sphi;
     if (k > 0) {
@@ -863,7 +864,7 @@ __device__ __forceinline__ bool fit_step_on(Track<T, P> &st, C p[21], int k, T a
             status |= KF_ST_NO_INTERSECT;
             return false;
         }
-        if constexpr (SEEDED) transport_seeded<C>(p, JacAs<C>::get(J));
+        if (SEEDED || seeded) transport_seeded<C>(p, JacAs<C>::get(J));
         else transport<C>(p, JacAs<C>::get(J));
         cphi = J.cphi1;
         sphi = J.sphi1;
