@@ -227,9 +227,10 @@ int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
 
 /* End-to-end fit from host memory: copies the hits to the device, estimates
  * the seeds (kf_make_seeds), fits (kf_fit) and copies the results back.  The
- * tracks are split into n_chunks ranges processed alternately on two internal
- * streams, so the copies of one range overlap the kernels of the other (Sec.
- * 4.3: copies overlapped with processing).  Blocks until the results are in
+ * tracks are split into n_chunks ranges processed in turn on three internal
+ * streams, so that one range's copy in, another's kernels and a third's copy
+ * out overlap (Sec. 4.3: copies overlapped with processing); the first and last
+ * ranges are half the size of the others.  Blocks until the results are in
  * host memory.  hits: host CSR as in kf_track_hits; out: host arrays with the
  * layouts of kf_tracks_out (any may be NULL).  Page-locked host memory makes
  * the copies asynchronous; pageable memory works but serialises them.

@@ -48,7 +48,7 @@ struct kf_ctx {
     cudaGraphExec_t gexec = nullptr;
     // end-to-end host path: device buffers and two streams
     Buf host_ws;
-    cudaStream_t hs[2] = {nullptr, nullptr};
+    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};  // kf_fit_host's copy/compute pipeline
 };
 
 namespace {
@@ -251,7 +251,7 @@ void kf_ctx_destroy(kf_ctx *c)
         if (kv.second.p) cudaFree(kv.second.p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->host_ws.p) cudaFree(c->host_ws.p);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
         if (c->hs[i]) cudaStreamDestroy(c->hs[i]);
     delete c;
 }
@@ -519,10 +519,10 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
            o_z = o_y + al(nh * 4), o_seed = o_z + al(nh * 4), o_q = o_seed + al((size_t)6 * n * 4),
            o_st = o_q + al((size_t)n), o_cov = o_st + al((size_t)6 * n * 8), o_chi = o_cov + al((size_t)21 * n * 8),
            o_nd = o_chi + al((size_t)n * 8), o_sts = o_nd + al((size_t)n * 4), o_ord = o_sts + al((size_t)n * 4),
-           total = o_ord + 2 * al((nhist + (size_t)n) * 4);
+           total = o_ord + 3 * al((nhist + (size_t)n) * 4);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < 3; ++i)
             if (!ctx->hs[i] && cudaStreamCreateWithFlags(&ctx->hs[i], cudaStreamNonBlocking) != cudaSuccess)
                 return cuda_fail(ctx, cudaGetLastError(), "stream create");
         Buf &b = ctx->host_ws;
@@ -557,12 +557,21 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
     uint32_t *d_sts = reinterpret_cast<uint32_t *>(base + o_sts);
     const bool fp64 = P.precision == KF_PREC_FP64;
     cudaError_t e = cudaSuccess;
+    // Three streams in turn, so that one chunk's copy in, another's fit and a
+    // third's copy out overlap; the first and last chunks are half as large as the
+    // others, since their copy in (resp. out) has nothing to overlap with.
+    const int64_t wsum = 2 * (int64_t)C - 2;  // chunk weights 1, 2, ..., 2, 1
+    auto bound = [&](int c) -> int {
+        if (C == 1) return c == 0 ? 0 : n;
+        const int64_t w = c == 0 ? 0 : (c == C ? wsum : 2 * (int64_t)c - 1);
+        return (int)((int64_t)n * w / wsum);
+    };
     for (int c = 0; c < C && e == cudaSuccess; ++c) {
-        const int t0 = (int)((int64_t)n * c / C), t1 = (int)((int64_t)n * (c + 1) / C);
+        const int t0 = bound(c), t1 = bound(c + 1);
         const int cnt = t1 - t0;
         if (cnt <= 0) continue;
-        cudaStream_t st = ctx->hs[c & 1];
-        int32_t *hist = reinterpret_cast<int32_t *>(base + o_ord + (c & 1) * al((nhist + (size_t)n) * 4));
+        cudaStream_t st = ctx->hs[c % 3];
+        int32_t *hist = reinterpret_cast<int32_t *>(base + o_ord + (c % 3) * al((nhist + (size_t)n) * 4));
         int32_t *order = hist + nhist;
         const int64_t h0 = hits->offsets[t0], h1 = hits->offsets[t1];
         e = cudaMemcpyAsync(d_off + t0, hits->offsets + t0, (size_t)(cnt + 1) * 4, cudaMemcpyHostToDevice, st);
@@ -584,7 +593,6 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             a.seed_cov = P.seed_cov;
             a.ms_on = P.ms_on;
             a.meas_model = P.meas_model;
-    a.meas_model = P.meas_model;
             a.seed_state = d_seed;
             a.q = d_q;
             a.off = d_off;
@@ -600,13 +608,14 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             a.order = order;
             e = launch_fit(G, a, fp64, 128, st);
         }
-        // results of this range back to the host
-        for (int i = 0; i < 6 && e == cudaSuccess && out->state; ++i)
-            e = cudaMemcpyAsync(out->state + (size_t)i * n + t0, d_st + (size_t)i * n + t0, (size_t)cnt * 8,
-                                cudaMemcpyDeviceToHost, st);
-        for (int i = 0; i < 21 && e == cudaSuccess && out->cov; ++i)
-            e = cudaMemcpyAsync(out->cov + (size_t)i * n + t0, d_cov + (size_t)i * n + t0, (size_t)cnt * 8,
-                                cudaMemcpyDeviceToHost, st);
+        // results of this range back to the host: the range of every state and
+        // covariance plane as one strided copy each
+        if (e == cudaSuccess && out->state)
+            e = cudaMemcpy2DAsync(out->state + t0, (size_t)n * 8, d_st + t0, (size_t)n * 8, (size_t)cnt * 8, 6,
+                                  cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->cov)
+            e = cudaMemcpy2DAsync(out->cov + t0, (size_t)n * 8, d_cov + t0, (size_t)n * 8, (size_t)cnt * 8, 21,
+                                  cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && out->chi2)
             e = cudaMemcpyAsync(out->chi2 + t0, d_chi + t0, (size_t)cnt * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && out->ndof)
@@ -614,9 +623,10 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
         if (e == cudaSuccess && out->status)
             e = cudaMemcpyAsync(out->status + t0, d_sts + t0, (size_t)cnt * 4, cudaMemcpyDeviceToHost, st);
     }
-    cudaError_t e0 = cudaStreamSynchronize(ctx->hs[0]);
-    cudaError_t e1 = cudaStreamSynchronize(ctx->hs[1]);
-    if (e == cudaSuccess) e = e0 != cudaSuccess ? e0 : e1;
+    for (int i = 0; i < 3; ++i) {
+        const cudaError_t es = cudaStreamSynchronize(ctx->hs[i]);
+        if (e == cudaSuccess) e = es;
+    }
     return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "kf_fit_host");
 }
 
