@@ -122,6 +122,59 @@ def test_hit_2d_rejected_where_unsupported(ctx):
         run.fit_numpy(ctx, g, tk, meas_model=2)
 
 
+def _host_fit(ctx, g, tk, n_chunks, pinned, meas_model=kf.KF_MEAS_LAYER):
+    n = tk["n"]
+
+    def buf(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        return t.pin_memory() if pinned else t
+    hh = {k: buf(tk[k]) for k in ("offsets", "layer", "x", "y", "z")}
+    out = dict(state=np.full((6, n), np.nan), cov=np.full((21, n), np.nan), chi2=np.full(n, np.nan),
+               ndof=np.full(n, -99, np.int32), status=np.full(n, 0xffff, np.uint32))
+    if pinned:
+        out = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in out.items()}
+    kf.kf_fit_host(ctx, kf.make_geometry(g), kf.fit_params(meas_model=meas_model), n, hh["offsets"], hh["layer"],
+                   hh["x"], hh["y"], hh["z"], out["state"], out["cov"], out["chi2"], out["ndof"], out["status"],
+                   n_chunks=n_chunks)
+    return out
+
+
+def test_fit_host_matches_device_path(ctx):
+    """kf_fit_host (host buffers in and out, the tracks split into ranges on three
+    streams, the first and last ranges half size) returns exactly what the device
+    path returns, for any number of ranges, page-locked or pageable buffers."""
+    g = synth.geometry("barrel17")
+    tk = synth.gen_tracks(g, 70001, synth.BASE_SEED + 23)
+    gg = kf.make_geometry(g)
+    dh = run.hits_to_device(tk)
+    seeds = run.make_seeds(ctx, gg, dh)
+    ref = run.alloc_fit_out(dh["n"])
+    run.fit(ctx, gg, dh, seeds, ref)
+    torch.cuda.synchronize()
+    ref = dict(state=ref["state"].cpu().numpy(), cov=ref["cov"].cpu().numpy(), chi2=ref["chi2"].cpu().numpy(),
+               ndof=ref["ndof"].cpu().numpy(), status=ref["status"].cpu().numpy().astype(np.uint32))
+    for n_chunks, pinned in ((0, True), (1, True), (2, False), (3, True), (7, True), (64, False)):
+        got = _host_fit(ctx, g, tk, n_chunks, pinned)
+        for k in ref:
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{k} n_chunks={n_chunks} pinned={pinned}")
+
+
+def test_fit_host_small_and_bad_arguments(ctx):
+    g = synth.geometry("barrel10")
+    tk = synth.gen_tracks(g, 5, synth.BASE_SEED + 24)
+    a = _host_fit(ctx, g, tk, 0, False)
+    b = _host_fit(ctx, g, tk, 64, False)  # more ranges than tracks: one track per range
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert np.all(a["ndof"] > 0)
+    with pytest.raises(kf.KfError):
+        _host_fit(ctx, g, tk, 65, False)
+    dh = run.hits_to_device(tk)
+    with pytest.raises(ValueError):  # device memory where host memory is required
+        kf.kf_fit_host(ctx, kf.make_geometry(g), None, tk["n"], dh["offsets"], dh["layer"], dh["x"], dh["y"],
+                       dh["z"])
+
+
 def test_persistent_schedule_matches_grid(ctx):
     g = synth.geometry("lids")
     tk = synth.gen_tracks(g, 20000, synth.BASE_SEED + 5, eta_max=2.5, min_hits=4)
