@@ -508,19 +508,27 @@ __device__ __forceinline__ void kf_apply_gain(Track<T, Pp> &st, C p[21], R r0, R
     st.phi = wrap(st.phi);
     add_inc(st.th, d[5]);  // float-float or double
     if (JOSEPH) {
+        // W = K S - G and P - K G^T + W K^T, each as one chain of fused
+        // multiply-adds from its accumulator (no separate products or sums: the
+        // FP64 pipe issues an FMA in the slot of a multiply or an add)
         C W[6][3];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            W[i][0] = K[i][0] * s11 + K[i][1] * s21 + K[i][2] * s31 - G[i][0];
-            W[i][1] = K[i][0] * s21 + K[i][1] * s22 + K[i][2] * s32 - G[i][1];
-            W[i][2] = K[i][0] * s31 + K[i][1] * s32 + K[i][2] * s33 - G[i][2];
+            W[i][0] = fma(K[i][2], s31, fma(K[i][1], s21, fma(K[i][0], s11, -G[i][0])));
+            W[i][1] = fma(K[i][2], s32, fma(K[i][1], s22, fma(K[i][0], s21, -G[i][1])));
+            W[i][2] = fma(K[i][2], s33, fma(K[i][1], s32, fma(K[i][0], s31, -G[i][2])));
         }
 #pragma unroll
         for (int i = 0; i < 6; ++i)
 #pragma unroll
-            for (int j = 0; j <= i; ++j)
-                p[pk(i, j)] = p[pk(i, j)] - (K[i][0] * G[j][0] + K[i][1] * G[j][1] + K[i][2] * G[j][2]) +
-                              (W[i][0] * K[j][0] + W[i][1] * K[j][1] + W[i][2] * K[j][2]);
+            for (int j = 0; j <= i; ++j) {
+                C v = fma(-K[i][0], G[j][0], p[pk(i, j)]);
+                v = fma(-K[i][1], G[j][1], v);
+                v = fma(-K[i][2], G[j][2], v);
+                v = fma(W[i][0], K[j][0], v);
+                v = fma(W[i][1], K[j][1], v);
+                p[pk(i, j)] = fma(W[i][2], K[j][2], v);
+            }
     } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i)
@@ -722,19 +730,22 @@ __device__ __forceinline__ bool kf_update2d(Track<T, Pp> &st, C p[21], float hx,
     st.phi = wrap(st.phi);
     add_inc(st.th, dd[5]);
     if (JOSEPH) {
-        // P - K G^T + (K S - G) K^T
+        // P - K G^T + (K S - G) K^T, as chains of fused multiply-adds (kf_apply_gain)
         C W[6][2];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            W[i][0] = K[i][0] * s11 + K[i][1] * s21 - G[i][0];
-            W[i][1] = K[i][0] * s21 + K[i][1] * s22 - G[i][1];
+            W[i][0] = fma(K[i][1], s21, fma(K[i][0], s11, -G[i][0]));
+            W[i][1] = fma(K[i][1], s22, fma(K[i][0], s21, -G[i][1]));
         }
 #pragma unroll
         for (int i = 0; i < 6; ++i)
 #pragma unroll
-            for (int j = 0; j <= i; ++j)
-                p[pk(i, j)] = p[pk(i, j)] - (K[i][0] * G[j][0] + K[i][1] * G[j][1]) +
-                              (W[i][0] * K[j][0] + W[i][1] * K[j][1]);
+            for (int j = 0; j <= i; ++j) {
+                C v = fma(-K[i][0], G[j][0], p[pk(i, j)]);
+                v = fma(-K[i][1], G[j][1], v);
+                v = fma(W[i][0], K[j][0], v);
+                p[pk(i, j)] = fma(W[i][1], K[j][1], v);
+            }
     } else {
 #pragma unroll
         for (int i = 0; i < 6; ++i)
@@ -833,17 +844,19 @@ __device__ __forceinline__ bool kf_seed_update(Track<T, Pp> &st, double p[21], f
     add_inc(st.y, d[1]);
     add_inc(st.z, d[2]);
     // Joseph: P = P - K G^T + (K S - G) K^T with G = c I on the position block
-    const double S[3][3] = {{s11, s21, 0.0}, {s21, s22, 0.0}, {0.0, 0.0, s33}};
+    // (S has no x-z or y-z terms here; chains of fused multiply-adds as in kf_apply_gain)
     double W[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) W[i][j] = K[i][0] * S[0][j] + K[i][1] * S[1][j] + K[i][2] * S[2][j] - (i == j ? c : 0.0);
+    for (int i = 0; i < 3; ++i) {
+        W[i][0] = fma(K[i][1], s21, fma(K[i][0], s11, i == 0 ? -c : 0.0));
+        W[i][1] = fma(K[i][1], s22, fma(K[i][0], s21, i == 1 ? -c : 0.0));
+        W[i][2] = fma(K[i][2], s33, i == 2 ? -c : 0.0);
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j)
-            p[pk(i, j)] = p[pk(i, j)] - K[i][j] * c + (W[i][0] * K[j][0] + W[i][1] * K[j][1] + W[i][2] * K[j][2]);
+            p[pk(i, j)] = fma(W[i][2], K[j][2], fma(W[i][1], K[j][1], fma(W[i][0], K[j][0], fma(-K[i][j], c, p[pk(i, j)]))));
     return true;
 }
 
