@@ -560,10 +560,12 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
 }
 
 template <bool FP64, bool COOP, bool M1>
-// three blocks per SM (at most 168 registers a thread): 12 warps to hide the
-// FP64 and memory latencies of the layer steps.  M1: measurement model 1
-// (per-thread scoring).
-__global__ void __launch_bounds__(128, 3) build_kernel(const Geom g, const BuildArgs a)
+// Model 0: four blocks per SM (at most 128 registers a thread): 16 warps to hide
+// the FP64 and memory latencies of the layer steps (2.05 ms for 10 x 20,000
+// tracks against 2.11 with three blocks, 2.20 with two).  M1, measurement model 1
+// (per-thread scoring): two blocks (255 registers; its larger step spills less),
+// 6.31 ms against 6.94 with three and 7.06 with four.
+__global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, const BuildArgs a)
 {
     using T = typename sel_t<FP64>::T;
     using P = typename sel_t<FP64>::P;
@@ -821,8 +823,10 @@ __device__ __forceinline__ ff shfl_ff(ff v, int src)
     return ff{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
 
+// four blocks per SM (at most 128 registers a thread): 3.15 / 6.27 / 13.0 ms for
+// 2 / 4 / 8 slots on 10 x 20,000 tracks, against 3.24 / 6.43 / 13.7 with three
 template <int NS>
-__global__ void __launch_bounds__(128, 3) ckf_kernel(const Geom g, const CkfArgs c)
+__global__ void __launch_bounds__(128, 4) ckf_kernel(const Geom g, const CkfArgs c)
 {
     const BuildArgs &a = c.b;
     __shared__ Surf s_surf[MAX_SURF];
