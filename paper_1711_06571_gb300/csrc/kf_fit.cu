@@ -415,7 +415,10 @@ __global__ void __launch_bounds__(128, FP64 ? 3 : 4) fit_kernel(const Geom g, co
 // warps run the same part of the loop at the same time (warps that drift apart
 // in a loop of this size compete for the instruction cache).
 template <bool FP64, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const Geom g, const FitArgs a)
+// 512 threads (16 warps) per SM whatever the block size, at most 128 registers a
+// thread: on the uneven barrel+disk batch 15.3 ms against 16.6 with the registers
+// uncapped (block 256: one block, 8 warps per SM)
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) fit_persistent_kernel(const Geom g, const FitArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
     __shared__ int s_base;
