@@ -324,7 +324,8 @@ typedef struct {
     double chi2_cut;  /* accept the best hit only if chi2 < cut (30) */
     int32_t max_cand; /* candidates scored per step, in enumeration order (32), 1..64 */
     int32_t warp_coop;/* 1: score window candidates across the warp with a
-                         shuffle min-reduction; 0: one thread per track */
+                         shuffle min-reduction; 0: one thread per track
+                         (KF_MEAS_HIT_2D always scores one thread per track) */
 } kf_build_params;
 
 /* Best-hit track building (Sec. 2: project the candidate outwards, use the KF
