@@ -98,14 +98,14 @@ __device__ __forceinline__ double cand_chi2(const Track<T, P> &st, const float p
                                             const Ldl3 &f, float4 h)
 {
     const auto r0 = resid(h.x, st.x), r1 = resid(h.y, st.y), r2 = resid(h.z, st.z);
-    if (shared) return ldl3_chi2(f, (double)r0, (double)r1, (double)r2);
+    if (shared) return ldl3_chi2(f, wide(r0), wide(r1), wide(r2));
     float rxx, rxy, ryy, rzz;
     meas_cov<float>(sf, h.x, h.y, rxx, rxy, ryy, rzz);
     Ldl3 g;
-    if (!ldl3((double)(p[pk(0, 0)] + rxx), (double)(p[pk(1, 0)] + rxy), (double)(p[pk(1, 1)] + ryy),
-              (double)p[pk(2, 0)], (double)p[pk(2, 1)], (double)(p[pk(2, 2)] + rzz), g))
+    if (!ldl3<false>(wide(p[pk(0, 0)] + rxx), wide(p[pk(1, 0)] + rxy), wide(p[pk(1, 1)] + ryy), wide(p[pk(2, 0)]),
+              wide(p[pk(2, 1)]), wide(p[pk(2, 2)] + rzz), g))
         return -1.0;
-    return ldl3_chi2(g, (double)r0, (double)r1, (double)r2);
+    return ldl3_chi2(g, wide(r0), wide(r1), wide(r2));
 }
 
 // chi2 of one candidate under model 1: the predicted state (on the layer's
@@ -188,8 +188,9 @@ __device__ __forceinline__ bool shared_factor(const C pc[21], const Surf &sf, Ld
 {
     const C vr = sizeof(C) == 8 ? (C)sf.var_radd : (C)sf.var_rad;
     const C vz = sizeof(C) == 8 ? (C)sf.var_zzd : (C)sf.var_zz;
-    return ldl3((double)(pc[pk(0, 0)] + vr), (double)pc[pk(1, 0)], (double)(pc[pk(1, 1)] + vr), (double)pc[pk(2, 0)],
-                (double)pc[pk(2, 1)], (double)(pc[pk(2, 2)] + vz), fs);
+    // float -> double by bit operations (wide): a conversion instruction would take an FP64 issue slot
+    return ldl3<sizeof(C) == 8>(wide(C(pc[pk(0, 0)] + vr)), wide(pc[pk(1, 0)]), wide(C(pc[pk(1, 1)] + vr)), wide(pc[pk(2, 0)]),
+                wide(pc[pk(2, 1)]), wide(C(pc[pk(2, 2)] + vz)), fs);
 }
 
 // The build parameters a layer step reads.
@@ -429,7 +430,7 @@ __device__ __forceinline__ void score_coop(const Track<T, P> &st, bool do_step, 
                 const float rx = __fsub_rn(__fsub_rn(h.x, oXh), oXl);
                 const float ry = __fsub_rn(__fsub_rn(h.y, oYh), oYl);
                 const float rz = __fsub_rn(__fsub_rn(h.z, oZh), oZl);
-                c2 = ldl3_chi2(of, (double)rx, (double)ry, (double)rz);
+                c2 = ldl3_chi2(of, wide(rx), wide(ry), wide(rz));
             }
         }
         // each owner folds the round's items that belong to it

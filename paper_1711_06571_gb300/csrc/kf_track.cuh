@@ -548,7 +548,7 @@ __device__ __forceinline__ bool kf_update(Track<T, Pp> &st, C p[21], float hx, f
     C s11 = p[pk(0, 0)] + rxx, s21 = p[pk(1, 0)] + rxy, s22 = p[pk(1, 1)] + ryy;
     C s31 = p[pk(2, 0)], s32 = p[pk(2, 1)], s33 = p[pk(2, 2)] + rzz;
     Ldl3 f;
-    if (!ldl3(wide(s11), wide(s21), wide(s22), wide(s31), wide(s32), wide(s33), f)) return false;
+    if (!ldl3<sizeof(C) == 8>(wide(s11), wide(s21), wide(s22), wide(s31), wide(s32), wide(s33), f)) return false;
     chi2 += ldl3_chi2(f, wide(r0), wide(r1), wide(r2));
     kf_apply_gain<JOSEPH>(st, p, r0, r1, r2, f, s11, s21, s22, s31, s32, s33);
     return true;
