@@ -677,13 +677,6 @@ __device__ __forceinline__ Surf hit_surface(const Surf &sf, float hx, float hy)
     return h;
 }
 
-// the surface a hit is measured on: its own cylinder under model 1 (barrel), the layer otherwise
-template <bool M1>
-__device__ __forceinline__ Surf meas_surface(const Surf &sf, float hx, float hy)
-{
-    if (M1 && sf.kind == 0) return hit_surface(sf, hx, hy);
-    return sf;
-}
 
 template <bool JOSEPH, class C, class T, class Pp>
 __device__ __forceinline__ bool kf_update2d(Track<T, Pp> &st, C p[21], float hx, float hy, float hz, const Surf &sf,
