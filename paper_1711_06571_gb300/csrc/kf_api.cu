@@ -883,8 +883,9 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     LayerDev *dl = nullptr;
     int32_t *deoff = nullptr;
     const size_t nhist = order_scratch_ints();
+    const size_t ord_bytes = ((nhist + (size_t)n) * sizeof(int32_t) + 255) & ~(size_t)255;
     if ((rc = upload_layers(ctx, st, n_events, n_layers, layers, event_offsets,
-                            (nhist + (size_t)n) * sizeof(int32_t) + 256, &rest, &dl, &deoff, false)))
+                            ord_bytes + build_seed_scratch_bytes(n), &rest, &dl, &deoff, false)))
         return rc;
     int32_t *hist = reinterpret_cast<int32_t *>(rest);
     int32_t *order = hist + nhist;
@@ -892,6 +893,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
     BuildArgs a;
     memset(&a, 0, sizeof a);
+    a.seed_scratch = static_cast<char *>(rest) + ord_bytes;
     a.n = n;
     a.n_events = n_events;
     a.n_layers = n_layers;

@@ -560,6 +560,86 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
     return alive;
 }
 
+// The seed fit of a mixed-path build track as the pre-pass leaves it: state as
+// float-float (x, y, z, phi, theta; hi then lo) and 1/pT, the FP32 covariance,
+// chi2, hits used, status, alive; [k][n] arrays.
+struct SeedFits {
+    float *st;       // [11][n]
+    float *cov;      // [21][n]
+    double *chi2;    // [n]
+    int32_t *used;   // [n]
+    uint32_t *status;
+    int8_t *alive;
+};
+__host__ __device__ inline size_t seed_al(size_t b) { return (b + 255) & ~(size_t)255; }
+__host__ __device__ inline SeedFits seed_carve(void *scratch, int n)
+{
+    const size_t m = (size_t)n;
+    char *p = static_cast<char *>(scratch);
+    SeedFits f;
+    f.st = reinterpret_cast<float *>(p);
+    p += seed_al(11 * 4 * m);
+    f.cov = reinterpret_cast<float *>(p);
+    p += seed_al(21 * 4 * m);
+    f.chi2 = reinterpret_cast<double *>(p);
+    p += seed_al(8 * m);
+    f.used = reinterpret_cast<int32_t *>(p);
+    p += seed_al(4 * m);
+    f.status = reinterpret_cast<uint32_t *>(p);
+    p += seed_al(4 * m);
+    f.alive = reinterpret_cast<int8_t *>(p);
+    return f;
+}
+size_t build_seed_scratch_bytes(int n)
+{
+    const size_t m = (size_t)n;
+    return seed_al(11 * 4 * m) + seed_al(21 * 4 * m) + seed_al(8 * m) + seed_al(4 * m) + seed_al(4 * m) + seed_al(m) +
+           256;
+}
+
+// Pre-pass of the mixed-path best-hit build: the seed fit of every track (its
+// FP64 phase) in a kernel of its own, so that the layer kernel's code holds the
+// layer loop alone (warps at different stages of one kernel share its
+// instruction cache).  Tracks in processing order, as the layer kernel.
+template <bool M1>
+__global__ void __launch_bounds__(128) build_seed_kernel(const Geom g, const BuildArgs a)
+{
+    __shared__ Surf s_surf[MAX_SURF];
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int t = a.order ? a.order[i] : i;
+    const int n = a.n;
+    const int e = find_event(a.event_off, a.n_events, t);
+    const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
+    Track<float, ff> st;
+    st.x = from_f<ff>(a.seed_state[0 * n + t]);
+    st.y = from_f<ff>(a.seed_state[1 * n + t]);
+    st.z = from_f<ff>(a.seed_state[2 * n + t]);
+    st.ip = a.seed_state[3 * n + t];
+    st.phi = from_f<ff>(a.seed_state[4 * n + t]);
+    st.th = from_f<ff>(a.seed_state[5 * n + t]);
+    const int q = a.q[t];
+    float pc[21];
+    unsigned status = 0u;
+    double chi2 = 0.0;
+    int used = 0;
+    const bool alive =
+        seed_fit<false, M1>(a, s_surf, lays, n, t, st, pc, float(-q) * g.kb, g.mass2, status, chi2, used, true);
+    const SeedFits f = seed_carve(a.seed_scratch, n);
+    const float w[11] = {st.x.hi, st.x.lo, st.y.hi, st.y.lo, st.z.hi, st.z.lo, st.phi.hi, st.phi.lo, st.th.hi,
+                         st.th.lo, st.ip};
+#pragma unroll
+    for (int k = 0; k < 11; ++k) f.st[(size_t)k * n + t] = w[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) f.cov[(size_t)k * n + t] = pc[k];
+    f.chi2[t] = chi2;
+    f.used[t] = used;
+    f.status[t] = status;
+    f.alive[t] = alive ? 1 : 0;
+}
+
 template <bool FP64, bool COOP, bool M1>
 // Model 0: four blocks per SM (at most 128 registers a thread): 16 warps to hide
 // the FP64 and memory latencies of the layer steps (2.05 ms for 10 x 20,000
@@ -598,7 +678,23 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
     bool alive = active;
     C pc[21];
     const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
-    alive = seed_fit<FP64, M1>(a, s_surf, lays, n, t, st, pc, alpha, mass2, status, chi2, used, alive);
+    if constexpr (FP64) {
+        alive = seed_fit<FP64, M1>(a, s_surf, lays, n, t, st, pc, alpha, mass2, status, chi2, used, alive);
+    } else {  // the pre-pass's seed fit
+        const SeedFits f = seed_carve(a.seed_scratch, n);
+        st.x = ff{f.st[0 * (size_t)n + t], f.st[1 * (size_t)n + t]};
+        st.y = ff{f.st[2 * (size_t)n + t], f.st[3 * (size_t)n + t]};
+        st.z = ff{f.st[4 * (size_t)n + t], f.st[5 * (size_t)n + t]};
+        st.phi = ff{f.st[6 * (size_t)n + t], f.st[7 * (size_t)n + t]};
+        st.th = ff{f.st[8 * (size_t)n + t], f.st[9 * (size_t)n + t]};
+        st.ip = f.st[10 * (size_t)n + t];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) pc[k] = f.cov[(size_t)k * n + t];
+        chi2 = f.chi2[t];
+        used = f.used[t];
+        status = f.status[t];
+        alive = active && f.alive[t] != 0;
+    }
     if (active)
         for (int L = 0; L < 3; ++L) a.hit_idx[(size_t)L * n + t] = -1;
     // build layers
@@ -690,6 +786,11 @@ cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp
 {
     if (a.n <= 0) return cudaSuccess;
     const int b = 128, grid = (a.n + b - 1) / b;
+    if (!fp64) {
+        if (!a.seed_scratch) return cudaErrorInvalidValue;
+        if (a.meas_model == 1) build_seed_kernel<true><<<grid, b, 0, st>>>(g, a);
+        else build_seed_kernel<false><<<grid, b, 0, st>>>(g, a);
+    }
     if (a.meas_model == 1) {  // per-thread scoring
         if (fp64) build_kernel<true, false, true><<<grid, b, 0, st>>>(g, a);
         else build_kernel<false, false, true><<<grid, b, 0, st>>>(g, a);

@@ -97,7 +97,11 @@ struct BuildArgs {
     uint32_t *o_status;
     int meas_model;  // as FitArgs::meas_model (per-thread scoring only)
     int pad_;
+    // mixed path: device scratch of build_seed_scratch_bytes(n) bytes, where a
+    // pre-pass kernel leaves each track's seed fit for the layer kernel
+    void *seed_scratch;
 };
+size_t build_seed_scratch_bytes(int n);
 cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp_coop, cudaStream_t st);
 
 // Combinatorial building: n_slots candidates per seed (mixed precision).  The

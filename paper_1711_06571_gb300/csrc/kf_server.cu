@@ -400,6 +400,7 @@ size_t kf_server::event_bytes(int n, int L, int64_t hb) const
     b += al(4 * (size_t)n + 4) + al((size_t)L * n) + 3 * al(4 * (size_t)L * n) + al(gather_scratch_bytes(n));
     b += al(24 * (size_t)n) + al((size_t)n);                    // final-fit seeds
     b += al(48 * (size_t)n) + al(168 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * (size_t)n);  // outputs
+    b += build_seed_scratch_bytes(n);                           // seed fits of the build
     b += al(sizeof(LayerDev) * (size_t)L) + al(sizeof(SegIn) * nseg) + al(sizeof(EvIO));  // tables
     // a merged batch rounds each of its ~40 arrays up once: an event's share of
     // that rounding is below 40 * 256 bytes, so the sum over a batch's events
@@ -451,7 +452,7 @@ int kf_server::launch(Batch &b)
                  d_gz = take(4 * (size_t)L * N), d_gsc = take(gather_scratch_bytes(N)), d_fseed = take(24 * (size_t)N),
                  d_fq = take(N), d_ord2 = take(4 * (order_scratch_ints() + N)), d_st = take(48 * (size_t)N),
                  d_cov = take(168 * (size_t)N), d_chi = take(8 * (size_t)N), d_nd = take(4 * (size_t)N),
-                 d_sts = take(4 * (size_t)N);
+                 d_sts = take(4 * (size_t)N), d_bseed = take(build_seed_scratch_bytes((int)N));
     // ---- page-locked host: the tables, then staged results of events the kernels cannot write directly
     size_t h = tables;
     b.staged_res.assign(E, SIZE_MAX);
@@ -592,6 +593,7 @@ int kf_server::launch(Batch &b)
         a.hit_idx = idx;
         a.order = ord1 + order_scratch_ints();
         a.o_status = reinterpret_cast<uint32_t *>(dp(d_bsts));
+        a.seed_scratch = dp(d_bseed);
         e = launch_build(geom, a, p.fit.precision == KF_PREC_FP64, p.build.warp_coop != 0, st);
     }
     // gather the chosen hits and fit them
