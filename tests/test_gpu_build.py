@@ -282,6 +282,17 @@ def test_build_parity_hit_2d_staggered(ctx, oracle_mod, precision):
     assert np.mean(effs) > 0.85
 
 
+def test_build_hit_2d_ignores_warp_coop(ctx):
+    """Measurement model 1 always scores one thread per track: asking for the
+    warp-cooperative scheme changes nothing."""
+    g = synth.geometry("barrel17s")
+    events = [synth.gen_event(g, 2000, synth.BASE_SEED + 51)]
+    a = run.build_numpy(ctx, g, events, meas_model=kf.KF_MEAS_HIT_2D, warp_coop=False)
+    b = run.build_numpy(ctx, g, events, meas_model=kf.KF_MEAS_HIT_2D, warp_coop=True)
+    for k in ("idx", "state", "cov", "chi2", "ndof", "status"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
 def _with_oracle_q(oracle_mod, g, ev, orc):
     q = np.array([oracle_mod.seed(ev["seed_hits"][t, 0], ev["seed_hits"][t, 1], ev["seed_hits"][t, 2], g["bz"])[1]
                   for t in range(ev["n"])], np.int8)
