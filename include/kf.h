@@ -235,7 +235,9 @@ int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
  * layouts of kf_tracks_out (any may be NULL).  Page-locked host memory makes
  * the copies asynchronous; pageable memory works but serialises them.
  * n_chunks: 1..64, 0 = automatic.  Device buffers are owned by the context and
- * kept for later calls of the same or smaller size. */
+ * kept for later calls of the same or smaller size.  Calls on one context from
+ * several host threads run one at a time (they share those buffers and the
+ * internal streams). */
 int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
                 const kf_track_hits *hits, const kf_tracks_out *out, int32_t n_chunks);
 

@@ -46,9 +46,11 @@ struct kf_ctx {
     // one cached graph of the persistent fit
     GraphKey gkey;
     cudaGraphExec_t gexec = nullptr;
-    // end-to-end host path: device buffers and two streams
+    // end-to-end host path: device buffers and the streams of kf_fit_host's
+    // copy/compute pipeline, used by one kf_fit_host call at a time (host_mu)
     Buf host_ws;
-    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};  // kf_fit_host's copy/compute pipeline
+    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+    std::mutex host_mu;
 };
 
 namespace {
@@ -512,6 +514,8 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
     if (nh < 0) return fail(ctx, KF_EINVAL, "offsets[n] < 0");
     int C = n_chunks ? n_chunks : (n >= 65536 ? 8 : 1);
     if (C > n) C = n;
+    // concurrent calls on one context share host_ws and hs: one at a time
+    std::lock_guard<std::mutex> hold(ctx->host_mu);
     // device layout
     const size_t nhist = order_scratch_ints();
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };

@@ -159,6 +159,37 @@ def test_fit_host_matches_device_path(ctx):
             np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{k} n_chunks={n_chunks} pinned={pinned}")
 
 
+def test_fit_host_concurrent_calls_on_one_context(ctx):
+    """kf_fit_host from two host threads on one context: the calls share the
+    context's device buffers and streams, so the library runs them one at a time,
+    and each returns what it returns alone (the larger batch regrows the buffers
+    in between)."""
+    import threading
+    g = synth.geometry("barrel17")
+    tks = [synth.gen_tracks(g, n, synth.BASE_SEED + 25 + i) for i, n in enumerate((40000, 65537))]
+    alone = [_host_fit(ctx, g, tk, 0, True) for tk in tks]
+    got = [[None] * 3 for _ in tks]
+    errors = []
+
+    def worker(i):
+        try:
+            for r in range(3):
+                got[i][r] = _host_fit(ctx, g, tks[i], 0, True)
+        except Exception as e:  # reported below, in the test's own thread
+            errors.append(e)
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(tks))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    assert not any(t.is_alive() for t in threads)
+    for i in range(len(tks)):
+        for r in range(3):
+            for k in alone[i]:
+                np.testing.assert_array_equal(got[i][r][k], alone[i][k], err_msg=f"{k} thread {i} call {r}")
+
+
 def test_fit_host_small_and_bad_arguments(ctx):
     g = synth.geometry("barrel10")
     tk = synth.gen_tracks(g, 5, synth.BASE_SEED + 24)
