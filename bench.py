@@ -538,13 +538,14 @@ def run_reference(args, world, rank):
     tot_upd = sum(u for u, _ in vals)
     tot_t = sum(d for _, d in vals)
     value = tot_upd / tot_t
-    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=0, steps=args.steps,
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * tot_t / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=WORKLOAD + f" (per step a sample of {n_sample} tracks)", tracks=n_sample),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=threads, kind="oracle",
                                   sample=f"{n_sample} tracks x up to 17 layers per step"),
-                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                runs_on=f"host cores only ({threads} threads); n_gpus is the launch's world size")
     print(json.dumps(line), flush=True)
 
 
