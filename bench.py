@@ -91,20 +91,36 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except FileNotFoundError:
             self.proc = None
+            os.unlink(self.path)
 
     def stop(self):
         if self.proc is None:
             return None
         self.proc.terminate()
         self.proc.wait(timeout=10)
-        rows = [l.split(",") for l in open(self.path).read().splitlines() if l.strip()]
+        text = open(self.path).read()
         os.unlink(self.path)
+        return self.parse(text)
+
+    @staticmethod
+    def parse(text):
+        """Median SM clock, maximum clock and the throttle reasons seen, from
+        nvidia-smi's CSV rows; rows cut short (the sampler is stopped in the
+        middle of a line) are skipped."""
+        rows = [[f.strip() for f in l.split(",")] for l in text.splitlines() if l.strip()]
+        rows = [r for r in rows if len(r) >= 9]
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
         return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
                     samples=len(rows), reasons=reasons)
 
