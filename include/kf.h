@@ -57,11 +57,27 @@ extern "C" {
 #define KF_ST_NONFINITE 4u    /* non-finite state */
 #define KF_ST_CAND_CAPPED 8u  /* building: more window candidates than the cap */
 #define KF_ST_GRAZING 16u     /* scattering thickness used the |cos(alpha)| >= 0.05 guard */
+#define KF_ST_THETA_RANGE 32u /* an update carried theta out of (0, pi), through the pole of the
+                                 (.., phi, theta) parametrisation where cot(theta) diverges: the
+                                 next propagation is refused and the track ends there (set
+                                 together with KF_ST_NO_INTERSECT) */
+#define KF_ST_FP64_TRACK 64u  /* KF_PREC_MIXED: the track crosses one surface twice in a row (it
+                                 turns back through a layer near its apex); it was fitted in
+                                 FP64 throughout */
 
 /* precision policies (kf_fit_params.precision) */
 #define KF_PREC_MIXED 0 /* FP32 propagation/transport/update; FP64 for the 3x3 S
                            solve and for the first n_fp64_updates updates */
 #define KF_PREC_FP64 1  /* every step in FP64 (the plain reference path) */
+
+/* arithmetic of the first updates of a KF_PREC_MIXED fit, where the 1e4 seed
+ * covariance cancels eight to ten digits (kf_fit_params.seed_update) */
+#define KF_SEED_UD_DF 0       /* default: double-float arithmetic (an unevaluated sum of
+                                 two floats, about 48 bits) on the FP32 pipe, the
+                                 covariance update in Bierman's U-D factored form
+                                 (P = U D U^T, one scalar measurement at a time), the
+                                 update at the seed hit in closed form */
+#define KF_SEED_JOSEPH_FP64 1 /* FP64 covariance, Joseph-form updates */
 
 /* scheduling of kf_fit (kf_fit_params.schedule) */
 #define KF_SCHED_GRID 0       /* one thread per track, one launch */
@@ -127,7 +143,9 @@ typedef struct {
     int32_t ms_on;          /* 1: add multiple-scattering noise at every surface */
     int32_t schedule;       /* KF_SCHED_GRID | KF_SCHED_PERSISTENT */
     int32_t meas_model;     /* KF_MEAS_LAYER (default) | KF_MEAS_HIT_2D */
-    int32_t pad_;
+    int32_t seed_update;    /* MIXED: KF_SEED_UD_DF (default) | KF_SEED_JOSEPH_FP64, for the
+                               first n_fp64_updates updates (the name predates the
+                               double-float form: these are the extended-precision updates) */
 } kf_fit_params;
 
 /* Seeds: device SoA. state [6][n] FP32 (x, y, z, 1/pT, phi, theta at the
@@ -241,6 +259,19 @@ int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
 int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *params, int32_t n,
                 const kf_track_hits *hits, const kf_tracks_out *out, int32_t n_chunks);
 
+/* Timing of kf_fit's kernels (no counterpart in the paper; it gives the roofline
+ * of each phase).  enable != 0: every later grid-schedule kf_fit on this context
+ * records CUDA events on its stream around its two phases -- on the mixed path
+ * phase 1 is the kernel that runs the first updates from the seed (extended
+ * precision) and phase 2 the kernel of the FP32 layer loop; the all-FP64 path
+ * runs one kernel, timed as phase 1.  enable == 0 stops recording; enabling
+ * again starts a new count.  kf_fit_phase_times waits for the timed calls and
+ * returns their number (the last 1024 at most) and the mean durations of the
+ * two phases in ms; KF_EINVAL if there is none.  Recording adds three event
+ * records to each call and no synchronisation. */
+int kf_fit_timing(kf_ctx *ctx, int enable);
+int kf_fit_phase_times(kf_ctx *ctx, int32_t *n_calls, double *ms_phase1, double *ms_phase2);
+
 /* Choose block size and tracks per thread (per work-queue grab) of the persistent
  * fit for this (n, hit count) by timing candidates on the given inputs (it
  * runs the fit several times and overwrites out).  The choice is cached in the
@@ -294,17 +325,18 @@ int kf_bin_hits_batched(kf_ctx *ctx, int32_t n_segments, const int32_t *segment_
  * GPU that loads the library holds until the process exits.
  *   - Arguments, layouts and results are those of kf_bin_hits; n_hits may be
  *     at most KF_STATIC_MAX_HITS, larger sizes return KF_ESIZE and do nothing.
- *     Host pointers or a bad half_len return KF_EINVAL.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     Host pointers, memory of a GPU other than the current one, or a bad
+ *     half_len return KF_EINVAL.
+ *   - Each call looks up the array's device address (cudaGetSymbolAddress)
+ *     with the caller's current device, so a cudaDeviceReset between calls is
+ *     harmless; the first call on a device also loads the library's code
+ *     there, so make that first call before any stream capture.
  *   - All calls on a device share the array and it keeps the last call's
  *     contents (nothing in it needs clearing: each call writes every scratch
  *     word it reads).  Calls whose work overlaps on the GPU, from different
  *     streams or threads, race on it; serialise them.
  *   - It calls no allocation routine of any kind. */
 #define KF_STATIC_MAX_HITS 262144
-#define KF_MAX_DEVICES 64
 int kf_bin_hits_static(int32_t n_hits, const float *x, const float *y, const float *z, double half_len,
                        int32_t *perm_out, int32_t *offsets_out, float *packed_out, void *stream);
 
@@ -328,6 +360,13 @@ typedef struct {
     int32_t warp_coop;/* 1: score window candidates across the warp with a
                          shuffle min-reduction; 0: one thread per track
                          (KF_MEAS_HIT_2D always scores one thread per track) */
+    double *debug_pred; /* diagnostics, NULL in normal use; kf_build_besthit only: device
+                           [n_layers][27][n] FP64, for every build layer L >= 3 a track
+                           reaches, its predicted state (6) and packed covariance (21)
+                           after propagation and scattering noise, before its hit is
+                           chosen (what its window and candidate scores were computed
+                           from); entries of layers a track does not reach are left
+                           as they are.  Lets a test replay one build decision. */
 } kf_build_params;
 
 /* Best-hit track building (Sec. 2: project the candidate outwards, use the KF

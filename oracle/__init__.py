@@ -31,6 +31,7 @@ ST_CHOL_FAIL = 2
 ST_NONFINITE = 4
 ST_CAND_CAPPED = 8
 ST_GRAZING = 16
+ST_THETA_RANGE = 32
 
 
 def build_lib(force: bool = False) -> str:
@@ -147,6 +148,11 @@ def lib():
             L.or_ckf_tracks.argtypes = [C.POINTER(FitCfg), C.POINTER(CkfCfg), C.POINTER(Surf), C.c_int,
                                         C.POINTER(Layer), C.c_int, C.c_int, _F, _I32, _I32, _D, _D, _D, _I32,
                                         _U32, C.c_void_p]
+            L.or_besthit_step.restype = C.c_int
+            L.or_besthit_step.argtypes = [C.POINTER(FitCfg), C.POINTER(BuildCfg), C.POINTER(Surf), C.POINTER(Layer),
+                                          _D, _D, C.c_int, _D, C.POINTER(StepRec)]
+            L.or_window.restype = None
+            L.or_window.argtypes = [_D, _D, C.POINTER(Surf), C.c_double, C.c_int, _D, _D]
             L.or_update2d.restype = C.c_int
             L.or_update2d.argtypes = [_D, _D, _D, C.POINTER(Surf), _D]
             L.or_refit_tracks.restype = None
@@ -211,6 +217,16 @@ def propagate(st, q, bz, surf, want_jac=True):
     rc = lib().or_propagate(_p(st, C.c_double), int(q), float(bz), sarr, _p(out, C.c_double),
                             _p(J, C.c_double) if want_jac else None)
     return rc, out, J.reshape(6, 6)
+
+
+def window(st, P, surf, nsigma=3.0, meas_model=0):
+    """Half widths (dphi, dz) of the build window around state st with covariance P (6x6)."""
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    dphi, dz = C.c_double(0.0), C.c_double(0.0)
+    lib().or_window(_p(st, C.c_double), _p(P, C.c_double), surfaces({"surfaces": [surf]}), float(nsigma),
+                    int(meas_model), C.byref(dphi), C.byref(dz))
+    return dphi.value, dz.value
 
 
 def highland(p, mass, t):
@@ -408,6 +424,31 @@ def build_besthit(geom, event, nsigma=3.0, chi2_cut=30.0, max_cand=32, seed_cov=
     _run_ranges(run, t0, t1, threads)
     if record:
         out["rec"] = rec
+    return out
+
+
+def besthit_step(geom, layer, st, P, q, nsigma=3.0, chi2_cut=30.0, max_cand=32, meas_model=0, seed_cov=1e4,
+                 ms_on=True):
+    """One best-hit step (window, candidates, chi2, best) on one binned layer (dict x, y, z, perm,
+    offsets, surf) from the predicted state st (6) and covariance P (6x6) given in FP64.
+    Returns the step record (STEP_DTYPE fields) with 'best' the best hit (no chi2 cut)."""
+    fc = fit_cfg(geom, seed_cov, ms_on, meas_model)
+    bc = BuildCfg(nsigma=float(nsigma), chi2_cut=float(chi2_cut), max_cand=int(min(max_cand, 1024)))
+    surf = surfaces(geom)
+    arrs = [np.ascontiguousarray(layer[k], dtype=np.float32) for k in ("x", "y", "z")]
+    perm = np.ascontiguousarray(layer["perm"], dtype=np.int32)
+    offs = np.ascontiguousarray(layer["offsets"], dtype=np.int32)
+    ly = Layer(n=len(arrs[0]), surf=int(layer["surf"]), x=_p(arrs[0], C.c_float), y=_p(arrs[1], C.c_float),
+               z=_p(arrs[2], C.c_float), perm=_p(perm, C.c_int32), offsets=_p(offs, C.c_int32))
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64).reshape(36)
+    rec = StepRec()
+    c2 = C.c_double(0.0)
+    best = lib().or_besthit_step(C.byref(fc), C.byref(bc), C.byref(surf[int(layer["surf"])]), C.byref(ly),
+                                 _p(st, C.c_double), _p(P, C.c_double), int(q), C.byref(c2), C.byref(rec))
+    out = {name: getattr(rec, name) for name, _ in StepRec._fields_}
+    out["pred"] = np.array(rec.pred)
+    out["best"] = int(best)
     return out
 
 

@@ -41,6 +41,7 @@
 #define OR_ST_NONFINITE 4u
 #define OR_ST_CAND_CAPPED 8u
 #define OR_ST_GRAZING 16u
+#define OR_ST_THETA_RANGE 32u
 
 /* One detector surface.  kind 0: barrel cylinder r = pos, |z| <= half_or_rin.
  * kind 1: disk z = pos, half_or_rin <= r <= r_out.
@@ -237,13 +238,18 @@ static void dxy_dc(const double st[6], double c, double s, double *dxdc, double 
  *   u = d out / d s,
  *   w = d s / d st from the surface condition g(out) = 0:
  *       w = -(dg/d st at fixed s) / (dg/ds).
- * J may be NULL.  Returns 0 or OR_ST_NO_INTERSECT. */
+ * J may be NULL.  Returns 0, OR_ST_NO_INTERSECT, or OR_ST_NO_INTERSECT |
+ * OR_ST_THETA_RANGE when theta is outside (0, pi). */
 int or_propagate(const double st[6], int q, double bz, const or_surf *sf, double out[6], double *J)
 {
     double c = or_curvature(st, q, bz);
     double alpha = -(double)q * OR_KAPPA * bz; /* dc / d(1/pT) */
     double s;
     int rc;
+    /* theta outside (0, pi): an update has carried the polar angle through the
+     * pole of the parametrisation, where dz/ds = cot(theta) diverges and changes
+     * sign.  Reading: the state has no next crossing and the track ends. */
+    if (!(sin(st[5]) > 0.0)) return (int)(OR_ST_NO_INTERSECT | OR_ST_THETA_RANGE);
     if (sf->kind == 0)
         rc = or_path_to_barrel(st, c, sf->pos, &s);
     else
@@ -892,12 +898,134 @@ typedef struct {
     int32_t status;
 } or_step_rec;
 
+/* Half widths of the candidate window of a build step around the predicted
+ * state st with covariance P on layer surface sf (a barrel of radius R):
+ *   phi: nsigma * sqrt(var(phi of the position) + (sig_rphi / R)^2), with the
+ *        variance of the azimuth of (x, y) to first order,
+ *        (y^2 P_xx + x^2 P_yy - 2 x y P_xy) / r^4;
+ *   z:   nsigma * sqrt(P_zz + sig_3^2).
+ * Measurement model 1 (hits within +-dr of the average radius): each widens by
+ * what the track sweeps while it crosses dr radially, with a the angle between
+ * the direction and the radial direction at the prediction:
+ *   dphi += dr tan(a) / R,  dz += dr |cot(theta)| / cos(a)
+ * (the whole layer when cos(a) <= 1e-3).  Reading of Sec. 3.1 / 4.1. */
+void or_window(const double st[6], const double P[36], const or_surf *sf, double nsigma, int meas_model,
+               double *dphi_out, double *dz_out)
+{
+    const double xp = st[0], yp = st[1], R = sf->pos, Lz = sf->half_or_rin;
+    const double r2 = xp * xp + yp * yp;
+    const double phip = atan2(yp, xp);
+    const double sphi2 = (yp * yp * P[0 * 6 + 0] + xp * xp * P[1 * 6 + 1] - 2.0 * xp * yp * P[0 * 6 + 1]) / (r2 * r2);
+    double dphi = nsigma * sqrt(sphi2 + (sf->sig_rphi / R) * (sf->sig_rphi / R));
+    double dz = nsigma * sqrt(P[2 * 6 + 2] + sf->sig_3 * sf->sig_3);
+    if (meas_model == 1 && sf->dr > 0.0) {
+        const double ca = fabs(cos(st[4] - phip)), sa = fabs(sin(st[4] - phip));
+        const double cot = cos(st[5]) / sin(st[5]);
+        if (ca > 1e-3) {
+            dphi += sf->dr * sa / (ca * R);
+            dz += sf->dr * fabs(cot) / ca;
+        } else {
+            dphi = OR_PI;
+            dz = 2.0 * Lz;
+        }
+    }
+    *dphi_out = dphi;
+    *dz_out = dz;
+}
+
 static int floor_clamp(double v, int lo, int hi)
 {
     double f = floor(v);
     if (f < lo) return lo;
     if (f > hi) return hi;
     return (int)f;
+}
+
+/* One best-hit step (reading of Sec. 2 "most likely continuation", Sec. 3.1
+ * binned hit selection) on layer ly, from the predicted state st and its 6x6
+ * covariance P on the layer's surface sf (after propagation and scattering
+ * noise): the window of or_window around the predicted position; its bins in
+ * order -- z ascending, phi from the low edge with wrap, each bin's hits in
+ * binned order -- at most max_cand candidates (capped beyond); the chi2 of
+ * each (measurement model 0: r^T S^-1 r with S = P_pos + R at the hit azimuth;
+ * model 1: carried on to the cylinder through the hit, 2-D there); the
+ * smallest, ties to the lower original index.  The chi2 cut is not applied
+ * here.  Fills rc (may be NULL).  Returns the best original index or -1, its
+ * chi2 in *chi2_best. */
+int or_besthit_step(const or_fit_cfg *fc, const or_build_cfg *bc, const or_surf *sf, const or_layer *ly,
+                    const double st[6], const double P[36], int q, double *chi2_best, or_step_rec *rc)
+{
+    const double Lz = sf->half_or_rin;
+    double phip, dphi, dz, bchi = 0.0, second = -1.0;
+    int phi_lo, phi_hi, nphi, z_lo, z_hi, zb, k, ncand = 0, capped = 0, best = -1;
+    int32_t cand[1024];
+    /* window (under model 1 widened by the sweep over +-dr) */
+    phip = atan2(st[1], st[0]);
+    or_window(st, P, sf, bc->nsigma, fc->meas_model, &dphi, &dz);
+    phi_lo = (int)floor(((phip - dphi + OR_PI) * 1024.0) / (2.0 * OR_PI));
+    phi_hi = (int)floor(((phip + dphi + OR_PI) * 1024.0) / (2.0 * OR_PI));
+    nphi = phi_hi - phi_lo + 1;
+    if (nphi > OR_NPHI) nphi = OR_NPHI;
+    z_lo = floor_clamp(((st[2] - dz + Lz) * 64.0) / (2.0 * Lz), 0, OR_NZ - 1);
+    z_hi = floor_clamp(((st[2] + dz + Lz) * 64.0) / (2.0 * Lz), 0, OR_NZ - 1);
+    /* enumerate candidates */
+    for (zb = z_lo; zb <= z_hi && !capped; ++zb) {
+        for (k = 0; k < nphi && !capped; ++k) {
+            int pb = ((phi_lo + k) % OR_NPHI + OR_NPHI) % OR_NPHI;
+            int key = zb * OR_NPHI + pb, j;
+            for (j = ly->offsets[key]; j < ly->offsets[key + 1]; ++j) {
+                if (ncand >= bc->max_cand) {
+                    capped = 1;
+                    break;
+                }
+                cand[ncand++] = ly->perm[j];
+            }
+        }
+    }
+    /* score */
+    for (k = 0; k < ncand; ++k) {
+        int h = cand[k];
+        double hit[3] = {(double)ly->x[h], (double)ly->y[h], (double)ly->z[h]};
+        double Rm[9], S[9], r[3], c2 = -1.0;
+        int a, b;
+        if (fc->meas_model == 1) {
+            /* second step: from the layer's average cylinder to the hit's own */
+            const or_surf hc = hit_cylinder(sf, hit);
+            double s2[6], P2[36], J2[36];
+            memcpy(P2, P, sizeof P2);
+            if (or_propagate(st, q, fc->bz, &hc, s2, J2) || (or_transport(J2, P2), or_chi2_2d(s2, P2, hit, &hc, &c2)))
+                c2 = -1.0;
+        } else {
+            or_meas_cov(sf, hit, Rm);
+            for (a = 0; a < 3; ++a) {
+                r[a] = hit[a] - st[a];
+                for (b = 0; b < 3; ++b) S[a * 3 + b] = P[a * 6 + b] + Rm[a * 3 + b];
+            }
+            if (or_chi2(S, r, &c2)) c2 = -1.0;
+        }
+        if (c2 < 0.0) continue;
+        if (best < 0 || c2 < bchi || (c2 == bchi && h < best)) {
+            if (best >= 0) second = bchi;
+            best = h;
+            bchi = c2;
+        } else if (second < 0.0 || c2 < second) {
+            second = c2;
+        }
+    }
+    if (rc) {
+        memcpy(rc->pred, st, 6 * sizeof(double));
+        rc->chi2_best = best >= 0 ? bchi : -1.0;
+        rc->chi2_second = second;
+        rc->phi_lo = phi_lo;
+        rc->phi_n = nphi;
+        rc->z_lo = z_lo;
+        rc->z_hi = z_hi;
+        rc->n_cand = ncand;
+        rc->capped = capped;
+        rc->status = 0;
+    }
+    *chi2_best = bchi;
+    return best;
 }
 
 /* Build one track.  Seed from its three seed hits (layers 0..2 of the
@@ -936,109 +1064,21 @@ unsigned or_build_one(const or_fit_cfg *fc, const or_build_cfg *bc, const or_sur
     for (L = 3; L < nlay; ++L) {
         const or_layer *ly = &lays[L];
         const or_surf *sf = &surfs[ly->surf];
-        double nx[6], J[36];
-        double R = sf->pos, Lz = sf->half_or_rin;
-        double xp, yp, r2, phip, sphi2, dphi, dz;
-        int phi_lo, phi_hi, nphi, z_lo, z_hi, zb, k, ncand = 0, capped = 0;
-        int32_t cand[1024];
-        double cchi[1024];
-        int best = -1;
-        double bchi = 0.0, second = -1.0;
-        or_step_rec *rc = rec ? &rec[L] : NULL;
+        double nx[6], J[36], bchi = 0.0;
+        int best;
+        or_step_rec local;
+        or_step_rec *rc = rec ? &rec[L] : &local;
         int prc = or_propagate(st, q, fc->bz, sf, nx, J);
         if (prc) {
             status |= (unsigned)prc;
-            if (rc) rc->status = prc;
+            rc->status = prc;
             break;
         }
         memcpy(st, nx, sizeof nx);
         or_transport(J, P);
         if (fc->ms_on) status |= (unsigned)or_ms_noise(st, fc->mass, sf, P);
-        /* window */
-        xp = st[0];
-        yp = st[1];
-        r2 = xp * xp + yp * yp;
-        phip = atan2(yp, xp);
-        sphi2 = (yp * yp * P[0 * 6 + 0] + xp * xp * P[1 * 6 + 1] - 2.0 * xp * yp * P[0 * 6 + 1]) / (r2 * r2);
-        dphi = bc->nsigma * sqrt(sphi2 + (sf->sig_rphi / R) * (sf->sig_rphi / R));
-        dz = bc->nsigma * sqrt(P[2 * 6 + 2] + sf->sig_3 * sf->sig_3);
-        if (fc->meas_model == 1 && sf->dr > 0.0) {
-            /* hits lie within +-dr of the average radius: the window widens by the
-             * azimuth and z the track sweeps over that radial distance */
-            const double ca = fabs(cos(st[4] - phip)), sa = fabs(sin(st[4] - phip));
-            const double cot = cos(st[5]) / sin(st[5]);
-            if (ca > 1e-3) {
-                dphi += sf->dr * sa / (ca * R);
-                dz += sf->dr * fabs(cot) / ca;
-            } else {
-                dphi = OR_PI;
-                dz = 2.0 * Lz;
-            }
-        }
-        phi_lo = (int)floor(((phip - dphi + OR_PI) * 1024.0) / (2.0 * OR_PI));
-        phi_hi = (int)floor(((phip + dphi + OR_PI) * 1024.0) / (2.0 * OR_PI));
-        nphi = phi_hi - phi_lo + 1;
-        if (nphi > OR_NPHI) nphi = OR_NPHI;
-        z_lo = floor_clamp(((st[2] - dz + Lz) * 64.0) / (2.0 * Lz), 0, OR_NZ - 1);
-        z_hi = floor_clamp(((st[2] + dz + Lz) * 64.0) / (2.0 * Lz), 0, OR_NZ - 1);
-        /* enumerate candidates */
-        for (zb = z_lo; zb <= z_hi && !capped; ++zb) {
-            for (k = 0; k < nphi && !capped; ++k) {
-                int pb = ((phi_lo + k) % OR_NPHI + OR_NPHI) % OR_NPHI;
-                int key = zb * OR_NPHI + pb, j;
-                for (j = ly->offsets[key]; j < ly->offsets[key + 1]; ++j) {
-                    if (ncand >= bc->max_cand) {
-                        capped = 1;
-                        break;
-                    }
-                    cand[ncand++] = ly->perm[j];
-                }
-            }
-        }
-        if (capped) status |= OR_ST_CAND_CAPPED;
-        /* score */
-        for (k = 0; k < ncand; ++k) {
-            int h = cand[k];
-            double hit[3] = {(double)ly->x[h], (double)ly->y[h], (double)ly->z[h]};
-            double Rm[9], S[9], r[3], c2 = -1.0;
-            int a, b;
-            if (fc->meas_model == 1) {
-                /* second step: from the layer's average cylinder to the hit's own */
-                const or_surf hc = hit_cylinder(sf, hit);
-                double s2[6], P2[36], J2[36];
-                memcpy(P2, P, sizeof P2);
-                if (or_propagate(st, q, fc->bz, &hc, s2, J2) || (or_transport(J2, P2), or_chi2_2d(s2, P2, hit, &hc, &c2)))
-                    c2 = -1.0;
-            } else {
-                or_meas_cov(sf, hit, Rm);
-                for (a = 0; a < 3; ++a) {
-                    r[a] = hit[a] - st[a];
-                    for (b = 0; b < 3; ++b) S[a * 3 + b] = P[a * 6 + b] + Rm[a * 3 + b];
-                }
-                if (or_chi2(S, r, &c2)) c2 = -1.0;
-            }
-            cchi[k] = c2;
-            if (c2 < 0.0) continue;
-            if (best < 0 || c2 < bchi || (c2 == bchi && h < best)) {
-                if (best >= 0) second = bchi;
-                best = h;
-                bchi = c2;
-            } else if (second < 0.0 || c2 < second) {
-                second = c2;
-            }
-        }
-        if (rc) {
-            memcpy(rc->pred, st, sizeof rc->pred);
-            rc->chi2_best = best >= 0 ? bchi : -1.0;
-            rc->chi2_second = second;
-            rc->phi_lo = phi_lo;
-            rc->phi_n = nphi;
-            rc->z_lo = z_lo;
-            rc->z_hi = z_hi;
-            rc->n_cand = ncand;
-            rc->capped = capped;
-            rc->status = 0;
-        }
+        best = or_besthit_step(fc, bc, sf, ly, st, P, q, &bchi, rc);
+        if (rc->capped) status |= OR_ST_CAND_CAPPED;
         if (best >= 0 && bchi < bc->chi2_cut) {
             double hit[3] = {(double)ly->x[best], (double)ly->y[best], (double)ly->z[best]};
             double Rm[9], c2;
@@ -1064,7 +1104,7 @@ unsigned or_build_one(const or_fit_cfg *fc, const or_build_cfg *bc, const or_sur
             nu += 1;
             idx[L] = best;
         }
-        if (rc) rc->best = idx[L];
+        rc->best = idx[L];
     }
     *ndof = 2 * nu - 5;
     for (i = 0; i < 6; ++i)
@@ -1220,12 +1260,12 @@ unsigned or_ckf_one(const or_fit_cfg *fc, const or_ckf_cfg *cc, const or_surf *s
     for (L = 3; L < nlay; ++L) {
         const or_layer *ly = &lays[L];
         const or_surf *sf = &surfs[ly->surf];
-        const double R = sf->pos, Lz = sf->half_or_rin;
+        const double Lz = sf->half_or_rin;
         int nk = 0, r, k, keep;
         for (r = 0; r < nc; ++r) {
             or_cand *c = &cands[r];
             or_cand *pr = &pred[r];
-            double nx[6], J[36], xp, yp, r2, phip, sphi2, dphi, dz, ulo, uhi, vlo, vhi;
+            double nx[6], J[36], phip, dphi, dz, ulo, uhi, vlo, vhi;
             int32_t cand[1024];
             int phi_lo, phi_hi, nphi, z_lo, z_hi, zb, ncand = 0, capped = 0, prc;
             unsigned step = 0;
@@ -1253,15 +1293,9 @@ unsigned or_ckf_one(const or_fit_cfg *fc, const or_ckf_cfg *cc, const or_surf *s
             memcpy(pr->st, nx, sizeof nx);
             or_transport(J, pr->P);
             if (fc->ms_on) step |= (unsigned)or_ms_noise(pr->st, fc->mass, sf, pr->P);
-            /* window, as in best-hit building */
-            xp = pr->st[0];
-            yp = pr->st[1];
-            r2 = xp * xp + yp * yp;
-            phip = atan2(yp, xp);
-            sphi2 = (yp * yp * pr->P[0 * 6 + 0] + xp * xp * pr->P[1 * 6 + 1] - 2.0 * xp * yp * pr->P[0 * 6 + 1]) /
-                    (r2 * r2);
-            dphi = cc->nsigma * sqrt(sphi2 + (sf->sig_rphi / R) * (sf->sig_rphi / R));
-            dz = cc->nsigma * sqrt(pr->P[2 * 6 + 2] + sf->sig_3 * sf->sig_3);
+            /* window, as in best-hit building (measurement model 0) */
+            phip = atan2(pr->st[1], pr->st[0]);
+            or_window(pr->st, pr->P, sf, cc->nsigma, 0, &dphi, &dz);
             ulo = ((phip - dphi + OR_PI) * 1024.0) / (2.0 * OR_PI);
             uhi = ((phip + dphi + OR_PI) * 1024.0) / (2.0 * OR_PI);
             vlo = ((pr->st[2] - dz + Lz) * 64.0) / (2.0 * Lz);

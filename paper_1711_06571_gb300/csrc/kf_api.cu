@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <mutex>
 #include <string>
@@ -51,6 +52,12 @@ struct kf_ctx {
     Buf host_ws;
     cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
     std::mutex host_mu;
+    // kf_fit_timing: a ring of event triples around the phase kernels of the
+    // grid-schedule kf_fit calls since timing was enabled
+    static constexpr int TRING = 1024;
+    std::vector<std::array<cudaEvent_t, 3>> tev;
+    int tcalls = 0;  // timed calls since enabled
+    bool timing = false;
 };
 
 namespace {
@@ -73,7 +80,9 @@ int cuda_fail(kf_ctx *c, cudaError_t e, const char *what)
     return fail(c, KF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-bool is_device_ptr(const void *p)
+// device memory of GPU dev (where the context's kernels run) or managed memory;
+// another GPU's memory is refused: without peer access the kernels would fault on it
+bool is_device_ptr_on(const void *p, int dev)
 {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -81,16 +90,16 @@ bool is_device_ptr(const void *p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
 }
 
 #define NEED_DEV(ptr, name)                                                                 \
     do {                                                                                    \
-        if (!is_device_ptr(ptr)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
+        if (!is_device_ptr_on(ptr, ctx->device)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
     } while (0)
 #define OPT_DEV(ptr, name)                                                                  \
     do {                                                                                    \
-        if ((ptr) && !is_device_ptr(ptr)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
+        if ((ptr) && !is_device_ptr_on(ptr, ctx->device)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
     } while (0)
 
 int to_geom(kf_ctx *ctx, const kf_geometry *g, Geom &G)
@@ -177,7 +186,7 @@ int check_fit_params(kf_ctx *ctx, const kf_fit_params *p, kf_fit_params &q)
     q.ms_on = 1;
     q.schedule = KF_SCHED_GRID;
     q.meas_model = KF_MEAS_LAYER;
-    q.pad_ = 0;
+    q.seed_update = KF_SEED_UD_DF;
     if (!p) return KF_OK;
     q = *p;
     if (q.precision != KF_PREC_MIXED && q.precision != KF_PREC_FP64)
@@ -188,6 +197,8 @@ int check_fit_params(kf_ctx *ctx, const kf_fit_params *p, kf_fit_params &q)
         return fail(ctx, KF_EINVAL, "schedule must be KF_SCHED_GRID or KF_SCHED_PERSISTENT");
     if (q.meas_model != KF_MEAS_LAYER && q.meas_model != KF_MEAS_HIT_2D)
         return fail(ctx, KF_EINVAL, "meas_model must be KF_MEAS_LAYER or KF_MEAS_HIT_2D");
+    if (q.seed_update != KF_SEED_UD_DF && q.seed_update != KF_SEED_JOSEPH_FP64)
+        return fail(ctx, KF_EINVAL, "seed_update must be KF_SEED_UD_DF or KF_SEED_JOSEPH_FP64");
     if (q.meas_model == KF_MEAS_HIT_2D && q.schedule != KF_SCHED_GRID)
         return fail(ctx, KF_EINVAL, "meas_model KF_MEAS_HIT_2D runs on the grid schedule");
     return KF_OK;
@@ -255,7 +266,55 @@ void kf_ctx_destroy(kf_ctx *c)
     if (c->host_ws.p) cudaFree(c->host_ws.p);
     for (int i = 0; i < 3; ++i)
         if (c->hs[i]) cudaStreamDestroy(c->hs[i]);
+    for (auto &t : c->tev)
+        for (cudaEvent_t ev : t)
+            if (ev) cudaEventDestroy(ev);
     delete c;
+}
+
+int kf_fit_timing(kf_ctx *ctx, int enable)
+{
+    if (!ctx) return KF_EINVAL;
+    int rc = set_dev(ctx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (enable && ctx->tev.empty()) {
+        ctx->tev.resize(kf_ctx::TRING, std::array<cudaEvent_t, 3>{nullptr, nullptr, nullptr});
+        for (auto &t : ctx->tev)
+            for (cudaEvent_t &ev : t)
+                if (cudaEventCreate(&ev) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ctx, KF_ECUDA, "cudaEventCreate");
+                }
+    }
+    ctx->timing = enable != 0;
+    ctx->tcalls = 0;
+    return KF_OK;
+}
+
+int kf_fit_phase_times(kf_ctx *ctx, int32_t *n_calls, double *ms_phase1, double *ms_phase2)
+{
+    if (!ctx || !n_calls || !ms_phase1 || !ms_phase2) return KF_EINVAL;
+    int rc = set_dev(ctx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const int m = std::min(ctx->tcalls, kf_ctx::TRING);
+    if (m == 0) return fail(ctx, KF_EINVAL, "no timed kf_fit since kf_fit_timing(ctx, 1)");
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const auto &t = ctx->tev[(ctx->tcalls - 1 - i) % kf_ctx::TRING];
+        float a = 0.f, b = 0.f;
+        cudaError_t e = cudaEventSynchronize(t[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, t[0], t[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, t[1], t[2]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kf_fit_phase_times");
+        s1 += a;
+        s2 += b;
+    }
+    *n_calls = m;
+    *ms_phase1 = s1 / m;
+    *ms_phase2 = s2 / m;
+    return KF_OK;
 }
 
 const char *kf_ctx_last_error(const kf_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -313,6 +372,7 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     a.t_begin = 0;
     a.count = n;
     a.n64 = P.n_fp64_updates;
+    a.seed_df = P.seed_update == KF_SEED_UD_DF;
     a.seed_cov = P.seed_cov;
     a.ms_on = P.ms_on;
     a.meas_model = P.meas_model;
@@ -333,14 +393,22 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     const bool fp64 = P.precision == KF_PREC_FP64;
     // processing order (both schedules): tracks bucketed by hit count and seed 1/pT
     const size_t nhist = order_scratch_ints();
-    const size_t need = (nhist + 64) * sizeof(int32_t) + (size_t)n * sizeof(int32_t) + 256;
+    const size_t order_bytes = (((nhist + 64) * sizeof(int32_t) + (size_t)n * sizeof(int32_t)) + 255) & ~(size_t)255;
+    const size_t need = order_bytes + (fp64 ? 0 : fit_carry_bytes(n)) + 256;
     void *wsp = nullptr;
     if ((rc = ws_get(ctx, st, need, &wsp))) return rc;
     int32_t *hist = reinterpret_cast<int32_t *>(wsp);
     int32_t *queue = hist + nhist;
     int32_t *order = queue + 64;
     a.order = order;
+    // the mixed fit hands each track from its phase-1 kernel to its phase-2 kernel here
+    if (!fp64 && !p0) fit_carve_carry(a.carry, static_cast<char *>(wsp) + order_bytes, n);
     if (P.schedule == KF_SCHED_GRID && !force) {
+        if (ctx->timing) {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            a.timing_events = ctx->tev[ctx->tcalls % kf_ctx::TRING].data();
+            ++ctx->tcalls;
+        }
         cudaError_t e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hist, order, st);
         if (e == cudaSuccess) e = launch_fit(G, a, fp64, 128, st);
         return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "fit kernel");
@@ -519,11 +587,23 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
     // device layout
     const size_t nhist = order_scratch_ints();
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // Three streams in turn, so that one chunk's copy in, another's fit and a
+    // third's copy out overlap; the first and last chunks are half as large as the
+    // others, since their copy in (resp. out) has nothing to overlap with.
+    const int64_t wsum = 2 * (int64_t)C - 2;  // chunk weights 1, 2, ..., 2, 1
+    auto bound = [&](int c) -> int {
+        if (C == 1) return c == 0 ? 0 : n;
+        const int64_t w = c == 0 ? 0 : (c == C ? wsum : 2 * (int64_t)c - 1);
+        return (int)((int64_t)n * w / wsum);
+    };
+    int cmax = 0;  // the largest chunk: the size of each stream's phase-1 -> phase-2 carry
+    for (int c = 0; c < C; ++c) cmax = std::max(cmax, bound(c + 1) - bound(c));
+    const size_t carry_b = P.precision == KF_PREC_FP64 ? 0 : al(fit_carry_bytes(cmax));
     size_t o_off = 0, o_lay = o_off + al((size_t)(n + 1) * 4), o_x = o_lay + al((size_t)nh), o_y = o_x + al(nh * 4),
            o_z = o_y + al(nh * 4), o_seed = o_z + al(nh * 4), o_q = o_seed + al((size_t)6 * n * 4),
            o_st = o_q + al((size_t)n), o_cov = o_st + al((size_t)6 * n * 8), o_chi = o_cov + al((size_t)21 * n * 8),
            o_nd = o_chi + al((size_t)n * 8), o_sts = o_nd + al((size_t)n * 4), o_ord = o_sts + al((size_t)n * 4),
-           total = o_ord + 3 * al((nhist + (size_t)n) * 4);
+           o_carry = o_ord + 3 * al((nhist + (size_t)n) * 4), total = o_carry + 3 * carry_b;
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         for (int i = 0; i < 3; ++i)
@@ -561,15 +641,6 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
     uint32_t *d_sts = reinterpret_cast<uint32_t *>(base + o_sts);
     const bool fp64 = P.precision == KF_PREC_FP64;
     cudaError_t e = cudaSuccess;
-    // Three streams in turn, so that one chunk's copy in, another's fit and a
-    // third's copy out overlap; the first and last chunks are half as large as the
-    // others, since their copy in (resp. out) has nothing to overlap with.
-    const int64_t wsum = 2 * (int64_t)C - 2;  // chunk weights 1, 2, ..., 2, 1
-    auto bound = [&](int c) -> int {
-        if (C == 1) return c == 0 ? 0 : n;
-        const int64_t w = c == 0 ? 0 : (c == C ? wsum : 2 * (int64_t)c - 1);
-        return (int)((int64_t)n * w / wsum);
-    };
     for (int c = 0; c < C && e == cudaSuccess; ++c) {
         const int t0 = bound(c), t1 = bound(c + 1);
         const int cnt = t1 - t0;
@@ -594,6 +665,7 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             a.t_begin = t0;
             a.count = cnt;
             a.n64 = P.n_fp64_updates;
+            a.seed_df = P.seed_update == KF_SEED_UD_DF;
             a.seed_cov = P.seed_cov;
             a.ms_on = P.ms_on;
             a.meas_model = P.meas_model;
@@ -610,6 +682,7 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             a.o_ndof = d_nd;
             a.o_status = d_sts;
             a.order = order;
+            if (!fp64) fit_carve_carry(a.carry, base + o_carry + (c % 3) * carry_b, cnt);
             e = launch_fit(G, a, fp64, 128, st);
         }
         // results of this range back to the host: the range of every state and
@@ -841,13 +914,14 @@ static int check_events(kf_ctx *ctx, const kf_geometry *geom, int n_events, int 
             return fail(ctx, KF_EINVAL, "layer %d: surface index out of range", i);
         if (geom->surfaces[L.surface].kind != 0) return fail(ctx, KF_EINVAL, "layer %d: building needs barrels", i);
         if (i % n_layers >= 3 && L.n_hits > 0) {
-            if (!is_device_ptr(L.packed) || !is_device_ptr(L.offsets))
+            if (!is_device_ptr_on(L.packed, ctx->device) || !is_device_ptr_on(L.offsets, ctx->device))
                 return fail(ctx, KF_EINVAL, "layer %d: packed and offsets must be device memory", i);
-        } else if (i % n_layers >= 3 && !is_device_ptr(L.offsets)) {
+        } else if (i % n_layers >= 3 && !is_device_ptr_on(L.offsets, ctx->device)) {
             return fail(ctx, KF_EINVAL, "layer %d: offsets must be device memory", i);
         }
         if (need_xyz && i % n_layers >= 3 && L.n_hits > 0 &&
-            (!is_device_ptr(L.x) || !is_device_ptr(L.y) || !is_device_ptr(L.z)))
+            (!is_device_ptr_on(L.x, ctx->device) || !is_device_ptr_on(L.y, ctx->device) ||
+             !is_device_ptr_on(L.z, ctx->device)))
             return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory", i);
     }
     return KF_OK;
@@ -866,7 +940,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     if ((rc = to_geom(ctx, geom, G))) return rc;
     if ((rc = set_dev(ctx))) return rc;
     if ((rc = check_events(ctx, geom, n_events, n_layers, layers, event_offsets, false))) return rc;
-    kf_build_params B = {3.0, 30.0, 32, 0};
+    kf_build_params B = {3.0, 30.0, 32, 0, nullptr};
     if (bp) B = *bp;
     if (!(B.nsigma > 0) || !(B.chi2_cut > 0) || B.max_cand < 1 || B.max_cand > 64)
         return fail(ctx, KF_EINVAL, "build params: nsigma > 0, chi2_cut > 0, 1 <= max_cand <= 64");
@@ -882,6 +956,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     OPT_DEV(out->chi2, "out.chi2");
     OPT_DEV(out->ndof, "out.ndof");
     OPT_DEV(out->status, "out.status");
+    OPT_DEV(B.debug_pred, "debug_pred");
     cudaStream_t st = (cudaStream_t)stream;
     void *rest = nullptr;
     LayerDev *dl = nullptr;
@@ -902,6 +977,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     a.n_events = n_events;
     a.n_layers = n_layers;
     a.n64 = P.n_fp64_updates;
+    a.seed_df = P.seed_update == KF_SEED_UD_DF;
     a.seed_cov = P.seed_cov;
     a.ms_on = P.ms_on;
     a.meas_model = P.meas_model;
@@ -920,6 +996,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     a.o_chi2 = out->chi2;
     a.o_ndof = out->ndof;
     a.o_status = out->status;
+    a.dbg_pred = B.debug_pred;
     cudaError_t e = launch_build(G, a, P.precision == KF_PREC_FP64, B.warp_coop != 0, st);
     return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "build kernel");
 }
@@ -943,7 +1020,7 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
     if ((rc = to_geom(ctx, geom, G))) return rc;
     if ((rc = set_dev(ctx))) return rc;
     if ((rc = check_events(ctx, geom, n_events, n_layers, layers, event_offsets, false))) return rc;
-    kf_build_params B = {3.0, 30.0, 32, 0};
+    kf_build_params B = {3.0, 30.0, 32, 0, nullptr};
     if (bp) B = *bp;
     if (!(B.nsigma > 0) || !(B.chi2_cut > 0) || B.max_cand < 1 || B.max_cand > 64)
         return fail(ctx, KF_EINVAL, "build params: nsigma > 0, chi2_cut > 0, 1 <= max_cand <= 64");
@@ -979,6 +1056,7 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
     a.n_events = n_events;
     a.n_layers = n_layers;
     a.n64 = P.n_fp64_updates;
+    a.seed_df = P.seed_update == KF_SEED_UD_DF;
     a.seed_cov = P.seed_cov;
     a.ms_on = P.ms_on;
     a.meas_model = P.meas_model;
@@ -1015,7 +1093,8 @@ int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_bin
                     KF_MAX_SURFACES);
     for (int i = 0; i < n_events * n_layers; ++i)
         if (i % n_layers >= 3 && layers[i].n_hits > 0 &&
-            (!is_device_ptr(layers[i].x) || !is_device_ptr(layers[i].y) || !is_device_ptr(layers[i].z)))
+            (!is_device_ptr_on(layers[i].x, ctx->device) || !is_device_ptr_on(layers[i].y, ctx->device) ||
+             !is_device_ptr_on(layers[i].z, ctx->device)))
             return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory", i);
     const int n = event_offsets[n_events];
     NEED_DEV(offsets_out, "offsets_out");

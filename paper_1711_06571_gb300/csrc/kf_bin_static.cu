@@ -12,8 +12,6 @@
 // kernels read is written earlier in the same call (the per-bin counts live
 // in the caller's offsets array, which the call clears).  Calls whose work
 // overlaps on the GPU (two streams, or two threads) race on the array.
-#include <mutex>
-
 #include "kf_internal.h"
 
 namespace {
@@ -24,32 +22,30 @@ constexpr size_t STATIC_SCRATCH_INTS = 2 * (size_t)STATIC_MAX_HITS + KF_NBINS;
 
 static __device__ __align__(256) int32_t g_bin_scratch[STATIC_SCRATCH_INTS];
 
-std::mutex g_mu;
-void *g_addr[KF_MAX_DEVICES] = {nullptr};
-
-// Device address of the array on the current device, looked up once per device
-// (host code cannot use g_bin_scratch's name as a device address).
-cudaError_t scratch_address(int dev, void **out)
+// Device address of the array on the current device.  Host code cannot use
+// g_bin_scratch's name as a device address; cudaGetSymbolAddress gives it with
+// the device current.  It is looked up on every call (cheap once the library's
+// module is loaded on the device): a cached address would go stale after a
+// cudaDeviceReset, when the module is loaded again and the array may move.
+cudaError_t scratch_address(void **out)
 {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
-bool on_device(const void *p)
+// device memory of GPU dev, or managed memory (another GPU's memory is refused:
+// without peer access the kernels would fault on it)
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -59,17 +55,17 @@ extern "C" int kf_bin_hits_static(int32_t n_hits, const float *x, const float *y
 {
     if (n_hits < 0 || !(half_len > 0)) return KF_EINVAL;
     if (n_hits > STATIC_MAX_HITS) return KF_ESIZE;
-    if (!on_device(offsets_out)) return KF_EINVAL;
-    if (n_hits > 0 && (!on_device(x) || !on_device(y) || !on_device(z) || !on_device(perm_out) ||
-                       (packed_out && !on_device(packed_out))))
-        return KF_EINVAL;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= KF_MAX_DEVICES) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return KF_ECUDA;
     }
+    if (!on_device(offsets_out, dev)) return KF_EINVAL;
+    if (n_hits > 0 && (!on_device(x, dev) || !on_device(y, dev) || !on_device(z, dev) || !on_device(perm_out, dev) ||
+                       (packed_out && !on_device(packed_out, dev))))
+        return KF_EINVAL;
     void *scratch = nullptr;
-    if (scratch_address(dev, &scratch) != cudaSuccess) {
+    if (scratch_address(&scratch) != cudaSuccess) {
         cudaGetLastError();
         return KF_ECUDA;
     }

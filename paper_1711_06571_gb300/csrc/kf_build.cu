@@ -17,6 +17,7 @@
 //     picks each track's minimum, so a warp costs ceil(total/32) rounds
 //     instead of max-over-lanes candidates.
 #include "kf_internal.h"
+#include "kf_df.cuh"
 #include "kf_track.cuh"
 
 namespace kfd {
@@ -199,7 +200,20 @@ struct StepKnobs {
     int max_cand;
     float nsigma;
     float chi2_cut;
+    double *dbg;     // diagnostics: this (layer, track)'s predicted state and covariance, or null
+    int dbg_stride;  // planes of dbg are dbg_stride doubles apart
 };
+
+// the predicted state (6) and covariance (21) of a build step, before the hit is
+// chosen (kf_build_params.debug_pred)
+template <class T, class P, class C>
+__device__ __forceinline__ void debug_pred_put(const StepKnobs &a, const Track<T, P> &st, const C pc[21])
+{
+    if (!a.dbg) return;
+    const double sv[6] = {to_d(st.x), to_d(st.y), to_d(st.z), (double)st.ip, to_d(st.phi), to_d(st.th)};
+    for (int i = 0; i < 6; ++i) a.dbg[(size_t)i * a.dbg_stride] = sv[i];
+    for (int i = 0; i < 21; ++i) a.dbg[(size_t)(6 + i) * a.dbg_stride] = (double)pc[i];
+}
 
 // One build layer for one track with per-thread scoring: propagate, transport,
 // scattering noise, window, candidates, update.  JOSEPH selects the covariance
@@ -218,12 +232,13 @@ __device__ __forceinline__ StepOut layer_step_thread(Track<T, P> &st, C pc[21], 
     StepOut o{-1, false};
     Jac<T> J;
     if (!propagate(st, alpha, sf, J)) {
-        status |= KF_ST_NO_INTERSECT;
+        status |= reach_bits(st);
         alive = false;
         return o;
     }
     transport<C>(pc, JacAs<C>::get(J));
     if (a.ms_on) status |= ms_noise<T, C>(st, sf, J.cphi1, J.sphi1, mass2, pc);
+    debug_pred_put(a, st, pc);
     float pw[21];
 #pragma unroll
     for (int i = 0; i < 21; ++i) pw[i] = (float)pc[i];
@@ -476,7 +491,36 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
     for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
     const int n1 = min(a.n64, 3);
     int k = 0;
-    for (; k < n1 && alive; ++k) {
+    bool in_pc = false;  // phase 1 ran in double-float and left its covariance in pc
+    if constexpr (!FP64) {
+        if (a.seed_df && n1 > 0) {
+            // the first n1 updates in double-float on the FP32 pipe (kf_df.cuh)
+            df pq[21];
+            df_seed_cov(pq, a.seed_cov);
+            df c2 = df(0.f);
+            for (; k < n1 && alive; ++k) {
+                const Surf &sf = s_surf[lays[k].surface];
+                const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
+                            hz = a.seed_hits[(3 * k + 2) * n + t];
+                bool ok;
+                if (M1 && k > 0 && sf.kind == 0)
+                    ok = df_step_on<true>(st, pq, k, alpha, mass2, a.ms_on, hit_surface(sf, hx, hy), hx, hy, hz, c2,
+                                          status, k == 1);
+                else
+                    ok = df_step_on<false>(st, pq, k, alpha, mass2, a.ms_on, sf, hx, hy, hz, c2, status, k == 1);
+                if (!ok) {
+                    alive = false;
+                    break;
+                }
+                ++used;
+            }
+            chi2 += df_to_d(c2);
+#pragma unroll
+            for (int i = 0; i < 21; ++i) pc[i] = pq[i].hi;
+            in_pc = true;
+        }
+    }
+    for (; !in_pc && k < n1 && alive; ++k) {
         const Surf &sf = s_surf[lays[k].surface];
         const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
                     hz = a.seed_hits[(3 * k + 2) * n + t];
@@ -497,7 +541,7 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         if (k > 0) {
             Jac<T> J;
             if (!propagate(st, alpha, sf, J)) {
-                status |= KF_ST_NO_INTERSECT;
+                status |= reach_bits(st);
                 alive = false;
                 break;
             }
@@ -520,8 +564,10 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         }
         ++used;
     }
+    if (!in_pc) {
 #pragma unroll
-    for (int i = 0; i < 21; ++i) pc[i] = (C)pd[i];
+        for (int i = 0; i < 21; ++i) pc[i] = (C)pd[i];
+    }
     for (; k < 3 && alive; ++k) {
         const Surf &sf = s_surf[lays[k].surface];
         const float hx = a.seed_hits[(3 * k + 0) * n + t], hy = a.seed_hits[(3 * k + 1) * n + t],
@@ -539,7 +585,7 @@ __device__ __forceinline__ bool seed_fit(const BuildArgs &a, const Surf *s_surf,
         if (k > 0) {
             Jac<T> J;
             if (!propagate(st, alpha, sf, J)) {
-                status |= KF_ST_NO_INTERSECT;
+                status |= reach_bits(st);
                 alive = false;
                 break;
             }
@@ -677,7 +723,7 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
     int used = 0;
     bool alive = active;
     C pc[21];
-    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
+    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut, nullptr, n};
     if constexpr (FP64) {
         alive = seed_fit<FP64, M1>(a, s_surf, lays, n, t, st, pc, alpha, mass2, status, chi2, used, alive);
     } else {  // the pre-pass's seed fit
@@ -701,6 +747,8 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
     for (int L = 3; L < a.n_layers; ++L) {
         const LayerDev ly = lays[L];
         const Surf &sf = s_surf[ly.surface];
+        StepKnobs knl = kn;
+        if (a.dbg_pred && active) knl.dbg = a.dbg_pred + (size_t)L * 27 * n + t;
         StepOut so{-1, false};
         bool near_tangent = false;
         if constexpr (!FP64) near_tangent = alive && crossing_sine(st, alpha, sf) > 0.8f;
@@ -709,7 +757,7 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
                 Fp64LayerIO io;
                 mixed_pack(io.m, st, pc, chi2, status);
                 io.alive = alive;
-                io = layer_step_fp64_out_of_line<M1>(io, alphad, g.mass2d, kn, &sf, ly);
+                io = layer_step_fp64_out_of_line<M1>(io, alphad, g.mass2d, knl, &sf, ly);
                 mixed_unpack(io.m, st, pc, chi2, status);
                 alive = io.alive != 0;
                 so = io.o;
@@ -720,19 +768,20 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
         const bool coop = COOP && !M1 && sf.var_rad == sf.var_rphi;
         if (!coop) {
             if (alive && !near_tangent)
-                so = layer_step_thread<false, M1>(st, pc, alpha, mass2, kn, sf, ly, chi2, status, alive);
+                so = layer_step_thread<false, M1>(st, pc, alpha, mass2, knl, sf, ly, chi2, status, alive);
         } else {
             // every lane of the warp takes part in the shuffles, stepping or not
             bool do_step = alive && !near_tangent;
             if (do_step) {
                 Jac<T> J;
                 if (!propagate(st, alpha, sf, J)) {
-                    status |= KF_ST_NO_INTERSECT;
+                    status |= reach_bits(st);
                     alive = false;
                     do_step = false;
                 } else {
                     transport<C>(pc, JacAs<C>::get(J));
                     if (a.ms_on) status |= ms_noise<T, C>(st, sf, J.cphi1, J.sphi1, mass2, pc);
+                    debug_pred_put(knl, st, pc);
                 }
             }
             float pw[21];
@@ -999,7 +1048,7 @@ __global__ void __launch_bounds__(128, 4) ckf_kernel(const Geom g, const CkfArgs
             }
         }
         if (stop_now) {
-            step |= KF_ST_NO_INTERSECT;
+            step |= reach_bits(st);
             search = false;
         }
         const bool pass = alive && (stopped || stop_now);  // carried unchanged

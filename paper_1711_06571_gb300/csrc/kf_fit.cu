@@ -5,6 +5,7 @@
 // a known hit list with no branching between tracks; Sec. 4.3: one track per
 // thread, structure-of-arrays inputs and outputs so neighbouring threads touch
 // neighbouring addresses).
+#include "kf_df.cuh"
 #include "kf_internal.h"
 #include "kf_track.cuh"
 
@@ -208,6 +209,20 @@ static __device__ __noinline__ MixedIO fp64_step_out_of_line(MixedIO m, int k, d
     return m;
 }
 
+// A near-tangent crossing of the FP32 layer loop: the step in double-float U-D
+// form (df_step_from_f32), out of line (about 2% of the steps)
+template <bool M1>
+static __device__ __noinline__ MixedIO df_step_out_of_line(MixedIO m, float alpha, float mass2, int ms_on,
+                                                           const Surf *sf, float hx, float hy, float hz)
+{
+    if (M1 && sf->kind == 0)
+        m.ok = df_step_from_f32<true>(m.st, m.p, alpha, mass2, ms_on, hit_surface(*sf, hx, hy), hx, hy, hz, m.chi2,
+                                      m.status);
+    else
+        m.ok = df_step_from_f32<false>(m.st, m.p, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
+    return m;
+}
+
 // A near-tangent crossing inside the FP64 phase (the covariance already FP64):
 // the propagation in FP64 too, out of line.  A track fitted inwards meets its
 // near-tangent crossings first, while the seed covariance is still large.
@@ -251,17 +266,74 @@ __device__ __forceinline__ void store_cov(double *o_cov, int n, int t, const C p
     for (int i = 0; i < 21; ++i) o_cov[(size_t)i * n + t] = (double)p[i];
 }
 
-// P0: the initial covariance is a.p0_scale * a.p0 (the refit), not seed_cov * I;
-// a separate instance, so that the plain fit does not carry the general first update.
 template <bool FP64, bool M1 = false, bool P0 = false>
 __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *surf, float kb, float mass2f,
-                                          double kbd, double mass2d)
+                                          double kbd, double mass2d);
+
+// A track that crosses one surface twice in a row (it turns back through a layer
+// near its apex, the second crossing close to tangent) has a step that
+// amplifies the mixed path's rounding about tenfold: the whole track is fitted
+// in FP64, out of line (it is rare, and its code stays out of the FP32 loop's).
+template <bool M1, bool P0>
+static __device__ __noinline__ void fit_track_fp64_out_of_line(int t, const FitArgs *a, const Surf *surf,
+                                                               double kbd, double mass2d)
+{
+    fit_track<true, M1, P0>(t, *a, surf, (float)kbd, (float)mass2d, kbd, mass2d);
+    if (a->o_status) a->o_status[t] |= KF_ST_FP64_TRACK;
+}
+
+// A track between the two phases of the fit: phase 1 (the first updates from
+// the seed, with an extended-precision covariance) leaves it here for phase 2
+// (the rest of the hits, covariance in T).
+template <bool FP64>
+struct Phase {
+    Track<typename FitTypes<FP64>::T, typename FitTypes<FP64>::P> st;
+    typename FitTypes<FP64>::T pf[21];
+    double chi2;
+    unsigned status;
+    int used, k;
+};
+
+template <class T, class P>
+__device__ __forceinline__ void write_outputs(const FitArgs &a, int t, const Track<T, P> &st, double chi2, int used,
+                                              unsigned status)
+{
+    const int n = a.n;
+    double sv[6] = {to_d(st.x), to_d(st.y), to_d(st.z), (double)st.ip, to_d(st.phi), to_d(st.th)};
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(sv[i])) status |= KF_ST_NONFINITE;
+    if (a.o_state) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) a.o_state[(size_t)i * n + t] = sv[i];
+    }
+    if (a.o_chi2) a.o_chi2[t] = chi2;
+    if (a.o_ndof) a.o_ndof[t] = 2 * used - 5;
+    if (a.o_status) a.o_status[t] = status;
+}
+
+// Phase 1 of track t: from the seed, the first n1 updates with an extended-
+// precision covariance.  Returns true with ph filled when phase 2 has hits to
+// fit; false when the track is finished here (its outputs written).
+// P0: the initial covariance is a.p0_scale * a.p0 (the refit), not seed_cov * I;
+// a separate instance, so that the plain fit does not carry the general first update.
+template <bool FP64, bool M1, bool P0>
+__device__ __forceinline__ bool fit_phase1(int t, const FitArgs &a, const Surf *surf, float kb, float mass2f,
+                                           double kbd, double mass2d, Phase<FP64> &ph)
 {
     using T = typename FitTypes<FP64>::T;
     using P = typename FitTypes<FP64>::P;
     const int n = a.n;
     const int o0 = a.off[t], nh = a.off[t + 1] - o0;
-    Track<T, P> st;
+    if constexpr (!FP64) {
+        bool recross = false;
+        for (int j = 1; j < nh; ++j) recross |= a.layer[o0 + j] == a.layer[o0 + j - 1];
+        if (recross) {
+            fit_track_fp64_out_of_line<M1, P0>(t, &a, surf, kbd, mass2d);
+            return false;
+        }
+    }
+    Track<T, P> &st = ph.st;
     st.x = from_f<P>(a.seed_state[0 * n + t]);
     st.y = from_f<P>(a.seed_state[1 * n + t]);
     st.z = from_f<P>(a.seed_state[2 * n + t]);
@@ -285,7 +357,7 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
 #pragma unroll
         for (int i = 0; i < 6; ++i) pd[pk(i, i)] = a.seed_cov;
     }
-    // phase 1: the first n64 updates with an FP64 covariance, Joseph form, and
+    // phase 1: the first n64 updates with an extended-precision covariance, and
     // at least until the third seed hit (the seed-hit rule) has been used: a
     // disk/barrel overlap can put two of the first hits a fraction of a mm
     // apart, and the curvature is only pinned by the third distinct point
@@ -295,7 +367,48 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         n1 = max(n1, s2 + 1);
     }
     n1 = min(n1, nh);
-    if (n1 > 0) {
+    // the covariance after phase 1: in ph.pf (T) when the seed phase ran in
+    // double-float, else in pd (FP64)
+    T *pf = ph.pf;
+    bool in_pf = false;
+    // A disk hit among the seed-phase hits: a steep track whose curvature rests
+    // on short transverse lever arms.  Its seed phase runs wholly in FP64,
+    // propagation included: neither 48 bits (double-float) in the covariance
+    // update nor the FP32 propagation and Jacobian are enough there.
+    bool disk_seed = false;
+    if constexpr (!FP64 && !P0)
+        for (int j = 0; j < n1; ++j) disk_seed |= surf[a.layer[o0 + j]].kind == 1;
+    if constexpr (!FP64 && !P0) {
+        // double-float U-D for seed phases on barrels
+        if (a.seed_df && n1 > 0 && !disk_seed) {
+            // phase 1 in double-float on the FP32 pipe: the closed-form update
+            // at the seed hit, then U-D factored updates
+            df pq[21];
+            df_seed_cov(pq, a.seed_cov);
+            df c2 = df(0.f);
+            for (; k < n1; ++k) {
+                const int h = o0 + k;
+                const Surf &sf = surf[a.layer[h]];
+                const float hx = a.hx[h], hy = a.hy[h], hz = a.hz[h];
+                bool ok;
+                if (M1 && k > 0 && sf.kind == 0)
+                    ok = df_step_on<true>(st, pq, k, alpha, mass2, a.ms_on, hit_surface(sf, hx, hy), hx, hy, hz, c2,
+                                          status, k == 1);
+                else
+                    ok = df_step_on<false>(st, pq, k, alpha, mass2, a.ms_on, sf, hx, hy, hz, c2, status, k == 1);
+                if (!ok) {
+                    alive = false;
+                    break;
+                }
+                ++used;
+            }
+            chi2 += df_to_d(c2);
+#pragma unroll
+            for (int i = 0; i < 21; ++i) pf[i] = pq[i].hi;
+            in_pf = true;
+        }
+    }
+    if (!in_pf && n1 > 0) {
         // the seed hit: no propagation, the structured first update
         const Surf &sf = surf[a.layer[o0]];
         T cphi, sphi;
@@ -314,14 +427,15 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
             alive = false;
         }
     }
-    for (; alive && k < n1; ++k) {
+    for (; !in_pf && alive && k < n1; ++k) {
         const int h = o0 + k;
         const Surf &sf = surf[a.layer[h]];
         bool ok;
         // the refit meets a track's near-tangent crossings (its outer end) among its
-        // first updates: there the FP64-covariance step also propagates in FP64
-        if constexpr (!FP64 && P0) {
-            if (grazing_crossing<M1>(st, alpha, sf, a.hx[h], a.hy[h])) {
+        // first updates, and a steep track its seed-phase disks: there the
+        // FP64-covariance step also propagates in FP64
+        if constexpr (!FP64) {
+            if (P0 ? grazing_crossing<M1>(st, alpha, sf, a.hx[h], a.hy[h]) : disk_seed) {
                 MixedIOD m;
                 m.st = st;
 #pragma unroll
@@ -338,7 +452,7 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
                 ok = m.ok != 0;
             } else {
                 ok = fit_step<true, double, M1>(st, pd, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h],
-                                                chi2, status);
+                                                chi2, status, !P0 && k == 1);
             }
         } else {
             // k == 1 after the structured seed-hit update: the transport skips its zero blocks
@@ -352,45 +466,163 @@ __device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *s
         ++used;
     }
     if (alive && k < nh) {
-        // phase 2: the rest in T (FP32 on the mixed path), standard form
-        T pf[21];
+        if (!in_pf) {
 #pragma unroll
-        for (int i = 0; i < 21; ++i) pf[i] = to_t(pd[i], T(0));
-        for (; k < nh; ++k) {
-            const int h = o0 + k;
-            const Surf &sf = surf[a.layer[h]];
-            bool near_tangent = false;
-            if constexpr (!FP64) near_tangent = grazing_crossing<M1>(st, alpha, sf, a.hx[h], a.hy[h]);
-            if (near_tangent) {
-                // near-tangent crossing: the whole step in FP64 (Joseph form)
-                if constexpr (!FP64) {
-                    MixedIO m;
-                    mixed_pack(m, st, pf, chi2, status);
-                    m = fp64_step_out_of_line<M1>(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
-                                              a.hz[h]);
-                    if (!mixed_unpack(m, st, pf, chi2, status)) break;
-                }
-            } else if (!fit_step<false, T, M1>(st, pf, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h],
-                                               chi2, status)) {
-                break;
-            }
-            ++used;
+            for (int i = 0; i < 21; ++i) pf[i] = to_t(pd[i], T(0));
         }
-        store_cov(a.o_cov, n, t, pf);
-    } else {
-        store_cov(a.o_cov, n, t, pd);
+        ph.chi2 = chi2;
+        ph.status = status;
+        ph.used = used;
+        ph.k = k;
+        return true;
     }
-    double sv[6] = {to_d(st.x), to_d(st.y), to_d(st.z), (double)st.ip, to_d(st.phi), to_d(st.th)};
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        if (!isfinite(sv[i])) status |= KF_ST_NONFINITE;
-    if (a.o_state) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) a.o_state[(size_t)i * n + t] = sv[i];
+    if (in_pf) store_cov(a.o_cov, n, t, pf);
+    else store_cov(a.o_cov, n, t, pd);
+    write_outputs(a, t, st, chi2, used, status);
+    return false;
+}
+
+// Phase 2 of track t: its hits from ph.k on, the covariance in T (FP32 on the
+// mixed path, standard form; FP64 steps at near-tangent crossings and for
+// strongly informative updates), then its outputs.
+template <bool FP64, bool M1>
+__device__ __forceinline__ void fit_phase2(int t, const FitArgs &a, const Surf *surf, float kb, float mass2f,
+                                           double kbd, double mass2d, Phase<FP64> &ph)
+{
+    using T = typename FitTypes<FP64>::T;
+    const int n = a.n;
+    const int o0 = a.off[t], nh = a.off[t + 1] - o0;
+    const int q = a.q[t];
+    const T alpha = FP64 ? T(-q * kbd) : T(-q) * T(kb);
+    const T mass2 = FP64 ? T(mass2d) : T(mass2f);
+    auto &st = ph.st;
+    T *pf = ph.pf;
+    double chi2 = ph.chi2;
+    unsigned status = ph.status;
+    int used = ph.used, k = ph.k;
+    for (; k < nh; ++k) {
+        const int h = o0 + k;
+        const Surf &sf = surf[a.layer[h]];
+        bool near_tangent = false;
+        if constexpr (!FP64) near_tangent = grazing_crossing<M1>(st, alpha, sf, a.hx[h], a.hy[h]);
+        if (near_tangent) {
+            // near-tangent crossing: the transport and update in double-float U-D form
+            if constexpr (!FP64) {
+                MixedIO m;
+                mixed_pack(m, st, pf, chi2, status);
+                m = df_step_out_of_line<M1>(m, alpha, mass2, a.ms_on, &sf, a.hx[h], a.hy[h], a.hz[h]);
+                if (!mixed_unpack(m, st, pf, chi2, status)) break;
+            }
+        } else if (!fit_step<false, T, M1>(st, pf, k, alpha, mass2, a.ms_on, sf, a.hx[h], a.hy[h], a.hz[h], chi2,
+                                           status)) {
+            break;
+        }
+        ++used;
     }
-    if (a.o_chi2) a.o_chi2[t] = chi2;
-    if (a.o_ndof) a.o_ndof[t] = 2 * used - 5;
-    if (a.o_status) a.o_status[t] = status;
+    store_cov(a.o_cov, n, t, pf);
+    write_outputs(a, t, st, chi2, used, status);
+}
+
+template <bool FP64, bool M1, bool P0>
+__device__ __forceinline__ void fit_track(int t, const FitArgs &a, const Surf *surf, float kb, float mass2f,
+                                          double kbd, double mass2d)
+{
+    Phase<FP64> ph;
+    if (fit_phase1<FP64, M1, P0>(t, a, surf, kb, mass2f, kbd, mass2d, ph))
+        fit_phase2<FP64, M1>(t, a, surf, kb, mass2f, kbd, mass2d, ph);
+}
+
+// ------------------------------------------------------------------ the mixed fit in two kernels
+// Phase 1 (double-float or FP64 seed phase: long straight-line code) and phase
+// 2 (the FP32 layer loop) run as two kernels, so that the warps of each run
+// one compact piece of code and the instruction cache holds it; each track is
+// handed over in the carry buffer at its processing position i (coalesced in
+// both kernels).
+__device__ __forceinline__ void carry_put(const FitCarry &c, int i, const Phase<false> &ph)
+{
+    const int m = c.m;
+    const float w[11] = {ph.st.x.hi, ph.st.x.lo, ph.st.y.hi, ph.st.y.lo, ph.st.z.hi, ph.st.z.lo, ph.st.phi.hi,
+                         ph.st.phi.lo, ph.st.th.hi, ph.st.th.lo, ph.st.ip};
+#pragma unroll
+    for (int j = 0; j < 11; ++j) c.st[(size_t)j * m + i] = w[j];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) c.cov[(size_t)j * m + i] = ph.pf[j];
+    c.chi2[i] = ph.chi2;
+    c.k[i] = ph.k;
+    c.used[i] = ph.used;
+    c.status[i] = ph.status;
+}
+__device__ __forceinline__ void carry_get(const FitCarry &c, int i, Phase<false> &ph)
+{
+    const int m = c.m;
+    float w[11];
+#pragma unroll
+    for (int j = 0; j < 11; ++j) w[j] = c.st[(size_t)j * m + i];
+    ph.st.x = ff{w[0], w[1]};
+    ph.st.y = ff{w[2], w[3]};
+    ph.st.z = ff{w[4], w[5]};
+    ph.st.phi = ff{w[6], w[7]};
+    ph.st.th = ff{w[8], w[9]};
+    ph.st.ip = w[10];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) ph.pf[j] = c.cov[(size_t)j * m + i];
+    ph.chi2 = c.chi2[i];
+    ph.k = c.k[i];
+    ph.used = c.used[i];
+    ph.status = c.status[i];
+}
+
+size_t fit_carry_bytes(int m)
+{
+    const size_t M = (size_t)max(m, 0);
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return al(11 * 4 * M) + al(21 * 4 * M) + al(8 * M) + 3 * al(4 * M) + 256;
+}
+void fit_carve_carry(FitCarry &c, void *p, int m)
+{
+    const size_t M = (size_t)max(m, 0);
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    char *q = static_cast<char *>(p);
+    c.m = m;
+    c.st = reinterpret_cast<float *>(q);
+    q += al(11 * 4 * M);
+    c.cov = reinterpret_cast<float *>(q);
+    q += al(21 * 4 * M);
+    c.chi2 = reinterpret_cast<double *>(q);
+    q += al(8 * M);
+    c.k = reinterpret_cast<int32_t *>(q);
+    q += al(4 * M);
+    c.used = reinterpret_cast<int32_t *>(q);
+    q += al(4 * M);
+    c.status = reinterpret_cast<uint32_t *>(q);
+}
+
+// phase 1 of the mixed fit, one thread per track in processing order
+template <bool M1>
+__global__ void __launch_bounds__(128) fit_seed_kernel(const Geom g, const FitArgs a)
+{
+    __shared__ Surf s_surf[MAX_SURF];
+    load_geom(g, s_surf);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.count) return;
+    const int t = a.t_begin + (a.order ? a.order[i] : i);
+    Phase<false> ph;
+    if (fit_phase1<false, M1, false>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d, ph)) carry_put(a.carry, i, ph);
+    else a.carry.k[i] = -1;  // finished in phase 1
+}
+
+// phase 2 of the mixed fit, grid schedule
+template <bool M1>
+__global__ void __launch_bounds__(128, 4) fit_loop_kernel(const Geom g, const FitArgs a)
+{
+    __shared__ Surf s_surf[MAX_SURF];
+    load_geom(g, s_surf);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.count || a.carry.k[i] < 0) return;
+    const int t = a.t_begin + (a.order ? a.order[i] : i);
+    Phase<false> ph;
+    carry_get(a.carry, i, ph);
+    fit_phase2<false, M1>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d, ph);
 }
 
 // Mixed path: four blocks of 128 per SM (at most 128 registers a thread, a few
@@ -434,6 +666,32 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) fit_persistent_kernel(cons
         for (int i = base + (int)threadIdx.x; i < end; i += BLOCK) {
             const int t = a.t_begin + (a.order ? a.order[i] : i);
             fit_track<FP64>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d);
+        }
+    }
+}
+
+// phase 2 of the mixed fit in the persistent form (the work queue of
+// fit_persistent_kernel over processing positions; phase 1 ran as a grid)
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) fit_loop_persistent_kernel(const Geom g, const FitArgs a)
+{
+    __shared__ Surf s_surf[MAX_SURF];
+    __shared__ int s_base;
+    load_geom(g, s_surf);
+    const int per = BLOCK * a.chunk;
+    for (;;) {
+        if (threadIdx.x == 0) s_base = atomicAdd(a.queue, per);
+        __syncthreads();
+        const int base = s_base;
+        __syncthreads();  // every thread has read s_base before thread 0 writes the next one
+        if (base >= a.count) break;
+        const int end = min(base + per, a.count);
+        for (int i = base + (int)threadIdx.x; i < end; i += BLOCK) {
+            if (a.carry.k[i] < 0) continue;
+            const int t = a.t_begin + (a.order ? a.order[i] : i);
+            Phase<false> ph;
+            carry_get(a.carry, i, ph);
+            fit_phase2<false, false>(t, a, s_surf, g.kb, g.mass2, g.kbd, g.mass2d, ph);
         }
     }
 }
@@ -547,6 +805,18 @@ cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cu
     const int b = 128;
     const int grid = (a.count + b - 1) / b;
     const bool m1 = a.meas_model == 1, p0 = a.p0 != nullptr;
+    cudaEvent_t *ev = static_cast<cudaEvent_t *>(a.timing_events);
+    if (ev) cudaEventRecord(ev[0], st);
+    if (!fp64 && !p0) {  // the mixed fit: phase 1, then phase 2 (carry in a.carry)
+        if (!a.carry.k || a.carry.m < a.count) return cudaErrorInvalidValue;
+        if (m1) fit_seed_kernel<true><<<grid, b, 0, st>>>(g, a);
+        else fit_seed_kernel<false><<<grid, b, 0, st>>>(g, a);
+        if (ev) cudaEventRecord(ev[1], st);
+        if (m1) fit_loop_kernel<true><<<grid, b, 0, st>>>(g, a);
+        else fit_loop_kernel<false><<<grid, b, 0, st>>>(g, a);
+        if (ev) cudaEventRecord(ev[2], st);
+        return cudaGetLastError();
+    }
     if (p0) {  // the refit
         if (m1) {
             if (fp64) fit_kernel<true, true, true><<<grid, b, 0, st>>>(g, a);
@@ -556,23 +826,13 @@ cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cu
             else fit_kernel<false, false, true><<<grid, b, 0, st>>>(g, a);
         }
     } else if (m1) {
-        if (fp64) fit_kernel<true, true, false><<<grid, b, 0, st>>>(g, a);
-        else fit_kernel<false, true, false><<<grid, b, 0, st>>>(g, a);
+        fit_kernel<true, true, false><<<grid, b, 0, st>>>(g, a);
     } else {
-        if (fp64) fit_kernel<true, false, false><<<grid, b, 0, st>>>(g, a);
-        else fit_kernel<false, false, false><<<grid, b, 0, st>>>(g, a);
+        fit_kernel<true, false, false><<<grid, b, 0, st>>>(g, a);
     }
-    return cudaGetLastError();
-}
-
-template <bool FP64>
-static cudaError_t launch_pers(const Geom &g, const FitArgs &a, int block, int grid, cudaStream_t st)
-{
-    switch (block) {
-    case 64: fit_persistent_kernel<FP64, 64><<<grid, 64, 0, st>>>(g, a); break;
-    case 128: fit_persistent_kernel<FP64, 128><<<grid, 128, 0, st>>>(g, a); break;
-    case 256: fit_persistent_kernel<FP64, 256><<<grid, 256, 0, st>>>(g, a); break;
-    default: return cudaErrorInvalidValue;
+    if (ev) {
+        cudaEventRecord(ev[1], st);
+        cudaEventRecord(ev[2], st);
     }
     return cudaGetLastError();
 }
@@ -582,7 +842,25 @@ cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, in
     if (a.count <= 0) return cudaSuccess;
     // model 1 and the refit's initial covariance run on the grid schedule
     if (a.meas_model != 0 || a.p0) return cudaErrorInvalidValue;
-    return fp64 ? launch_pers<true>(g, a, block, grid, st) : launch_pers<false>(g, a, block, grid, st);
+    if (fp64) {
+        switch (block) {
+        case 64: fit_persistent_kernel<true, 64><<<grid, 64, 0, st>>>(g, a); break;
+        case 128: fit_persistent_kernel<true, 128><<<grid, 128, 0, st>>>(g, a); break;
+        case 256: fit_persistent_kernel<true, 256><<<grid, 256, 0, st>>>(g, a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    // mixed: phase 1 as a grid, phase 2 from the work queue
+    if (!a.carry.k || a.carry.m < a.count) return cudaErrorInvalidValue;
+    if (block != 64 && block != 128 && block != 256) return cudaErrorInvalidValue;
+    fit_seed_kernel<false><<<(a.count + 127) / 128, 128, 0, st>>>(g, a);
+    switch (block) {
+    case 64: fit_loop_persistent_kernel<64><<<grid, 64, 0, st>>>(g, a); break;
+    case 128: fit_loop_persistent_kernel<128><<<grid, 128, 0, st>>>(g, a); break;
+    default: fit_loop_persistent_kernel<256><<<grid, 256, 0, st>>>(g, a); break;
+    }
+    return cudaGetLastError();
 }
 
 // resident blocks per SM of the persistent kernel at this block size
@@ -593,15 +871,15 @@ int persistent_blocks_per_sm(bool fp64, int block)
     switch (block) {
     case 64:
         e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<true, 64>, 64, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<false, 64>, 64, 0);
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_loop_persistent_kernel<64>, 64, 0);
         break;
     case 128:
         e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<true, 128>, 128, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<false, 128>, 128, 0);
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_loop_persistent_kernel<128>, 128, 0);
         break;
     case 256:
         e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<true, 256>, 256, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_persistent_kernel<false, 256>, 256, 0);
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fit_loop_persistent_kernel<256>, 256, 0);
         break;
     default: return 0;
     }

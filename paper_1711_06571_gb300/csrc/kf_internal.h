@@ -8,6 +8,23 @@
 
 namespace kfd {
 
+// A track handed from phase 1 of the mixed fit to phase 2, at its processing
+// position i ([k][m] planes): state as float-float (x, y, z, phi, theta; hi then
+// lo) and 1/pT, the FP32 covariance, chi2, the next hit k (-1: finished in
+// phase 1), hits used, status.
+struct FitCarry {
+    float *st;       // [11][m]
+    float *cov;      // [21][m]
+    double *chi2;    // [m]
+    int32_t *k;      // [m]
+    int32_t *used;   // [m]
+    uint32_t *status;
+    int m;
+    int pad_;
+};
+size_t fit_carry_bytes(int m);
+void fit_carve_carry(FitCarry &c, void *p, int m);
+
 struct FitArgs {
     int n;            // plane stride of seeds and outputs ([k][n] arrays)
     int t_begin;      // first track of this launch
@@ -15,7 +32,7 @@ struct FitArgs {
     int n64;          // updates carried in FP64 (Joseph form) from the seed
     double seed_cov;
     int ms_on;
-    int pad_;
+    int seed_df;      // mixed path: the first n64 updates in double-float, U-D form (else FP64 Joseph)
     const float *seed_state;  // [6][n]
     const int8_t *q;          // [n]
     const int32_t *off;       // [n+1]
@@ -34,6 +51,12 @@ struct FitArgs {
     // initial covariance: p0_scale * p0 ([21][n] FP64) instead of seed_cov * I when p0 is set
     const double *p0;
     double p0_scale;
+    // the mixed fit (not the refit): phase 1 -> phase 2 hand-over, m >= count
+    FitCarry carry;
+    // host side only: null, or three cudaEvent_t recorded before phase 1, between the
+    // phases and after phase 2 (launch_fit; the one-kernel forms record the second
+    // and third together)
+    void *timing_events;
 };
 
 // kf_fit.cu
@@ -96,10 +119,13 @@ struct BuildArgs {
     int32_t *o_ndof;
     uint32_t *o_status;
     int meas_model;  // as FitArgs::meas_model (per-thread scoring only)
-    int pad_;
+    int seed_df;     // as FitArgs::seed_df
     // mixed path: device scratch of build_seed_scratch_bytes(n) bytes, where a
     // pre-pass kernel leaves each track's seed fit for the layer kernel
     void *seed_scratch;
+    // diagnostics (kf_build_params.debug_pred): [n_layers][27][n] predicted
+    // state and covariance per build step, or null
+    double *dbg_pred;
 };
 size_t build_seed_scratch_bytes(int n);
 cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp_coop, cudaStream_t st);

@@ -401,11 +401,12 @@ size_t kf_server::event_bytes(int n, int L, int64_t hb) const
     b += al(24 * (size_t)n) + al((size_t)n);                    // final-fit seeds
     b += al(48 * (size_t)n) + al(168 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * (size_t)n);  // outputs
     b += build_seed_scratch_bytes(n);                           // seed fits of the build
+    b += fit_carry_bytes(n);                                    // final fit: phase 1 -> phase 2
     b += al(sizeof(LayerDev) * (size_t)L) + al(sizeof(SegIn) * nseg) + al(sizeof(EvIO));  // tables
-    // a merged batch rounds each of its ~40 arrays up once: an event's share of
-    // that rounding is below 40 * 256 bytes, so the sum over a batch's events
-    // bounds the batch's allocation
-    return b + 40 * 256;
+    // a merged batch rounds each of its (under 48) arrays up once: an event's
+    // share of that rounding is below 48 * 256 bytes, so the sum over a batch's
+    // events bounds the batch's allocation
+    return b + 48 * 256;
 }
 
 // Page-locked bytes of a one-event batch (tables, staged results; a bound).
@@ -452,7 +453,8 @@ int kf_server::launch(Batch &b)
                  d_gz = take(4 * (size_t)L * N), d_gsc = take(gather_scratch_bytes(N)), d_fseed = take(24 * (size_t)N),
                  d_fq = take(N), d_ord2 = take(4 * (order_scratch_ints() + N)), d_st = take(48 * (size_t)N),
                  d_cov = take(168 * (size_t)N), d_chi = take(8 * (size_t)N), d_nd = take(4 * (size_t)N),
-                 d_sts = take(4 * (size_t)N), d_bseed = take(build_seed_scratch_bytes((int)N));
+                 d_sts = take(4 * (size_t)N), d_bseed = take(build_seed_scratch_bytes((int)N)),
+                 d_carry = take(fit_carry_bytes((int)N));
     // ---- page-locked host: the tables, then staged results of events the kernels cannot write directly
     size_t h = tables;
     b.staged_res.assign(E, SIZE_MAX);
@@ -579,6 +581,7 @@ int kf_server::launch(Batch &b)
         a.n_events = E;
         a.n_layers = L;
         a.n64 = p.fit.n_fp64_updates;
+        a.seed_df = p.fit.seed_update == KF_SEED_UD_DF;
         a.seed_cov = p.fit.seed_cov;
         a.ms_on = p.fit.ms_on;
         a.meas_model = p.fit.meas_model;
@@ -616,6 +619,7 @@ int kf_server::launch(Batch &b)
         a.t_begin = 0;
         a.count = N;
         a.n64 = p.fit.n_fp64_updates;
+        a.seed_df = p.fit.seed_update == KF_SEED_UD_DF;
         a.seed_cov = p.fit.seed_cov;
         a.ms_on = p.fit.ms_on;
         a.meas_model = p.fit.meas_model;
@@ -632,6 +636,7 @@ int kf_server::launch(Batch &b)
         a.o_ndof = reinterpret_cast<int32_t *>(dp(d_nd));
         a.o_status = reinterpret_cast<uint32_t *>(dp(d_sts));
         a.order = ord2 + order_scratch_ints();
+        if (p.fit.precision != KF_PREC_FP64) fit_carve_carry(a.carry, dp(d_carry), N);
         e = launch_fit(geom, a, p.fit.precision == KF_PREC_FP64, 128, st);
     }
     // results: every event's slice into its arrays
@@ -831,7 +836,8 @@ int kf_server_create(kf_ctx *ctx, const kf_geometry *geom, const kf_server_param
     int rc = ctx_fit_params(ctx, P.fit.seed_cov == 0 ? nullptr : &Fin, F);
     if (rc) return rc;
     P.fit = F;
-    if (P.build.nsigma == 0) P.build = kf_build_params{3.0, 30.0, 32, 0};
+    if (P.build.nsigma == 0) P.build = kf_build_params{3.0, 30.0, 32, 0, nullptr};
+    P.build.debug_pred = nullptr;  // a diagnostic of kf_build_besthit calls, not of the server
     if (!(P.build.nsigma > 0) || !(P.build.chi2_cut > 0) || P.build.max_cand < 1 || P.build.max_cand > 64)
         return ctx_fail(ctx, KF_EINVAL, "build params: nsigma > 0, chi2_cut > 0, 1 <= max_cand <= 64");
     Geom G;

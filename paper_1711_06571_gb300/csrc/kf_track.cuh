@@ -95,6 +95,9 @@ __device__ __forceinline__ bool propagate_from(Track<T, P> &st, T alpha, const S
 {
     T c = alpha * st.ip;
     const T sphi = d.sphi, cphi = d.cphi, sth = d.sth, cth = d.cth;
+    // theta outside (0, pi): an update has carried the polar angle through the
+    // pole of the parametrisation, where cot(theta) diverges; the track ends
+    if (!(sth > T(0))) return false;
     T cot = cth / sth;
     T s;
     const T X = lead(st.x), Y = lead(st.y);
@@ -189,6 +192,16 @@ __device__ __forceinline__ bool propagate(Track<T, P> &st, T alpha, const Surf &
     return propagate_from(st, alpha, sf, J, direction(st));
 }
 
+// status bits of a track whose propagation failed (st as it was): the surface
+// is out of reach, and theta has left (0, pi) if that is why
+template <class T, class P>
+__device__ __forceinline__ unsigned reach_bits(const Track<T, P> &st)
+{
+    T sth, cth;
+    sincos_pos(st.th, sth, cth);
+    return KF_ST_NO_INTERSECT | (sth > T(0) ? 0u : KF_ST_THETA_RANGE);
+}
+
 // Sine of the angle between track and radial direction where the helix meets
 // the cylinder R, from the state before propagation: for the helix circle
 // (radius 1/|c|, centre C) and the cylinder, the triangle origin-C-crossing
@@ -213,8 +226,10 @@ __device__ __forceinline__ T crossing_sine(const Track<T, P> &st, T alpha, const
 // P <- J P J^T with J = A + u w^T, as A P A^T + a u^T + u a^T + gamma u u^T,
 // y = P w, a = A y, gamma = w.y; A has six off-diagonal entries and u two
 // structural zeros, so the product costs ~150 FMA instead of ~430 dense.
-template <class T>
-__device__ __forceinline__ void transport(T p[21], const Jac<T> &J)
+// JT: type of the Jacobian's entries (the FP32 Jacobian of the mixed path may
+// transport a wider covariance T)
+template <class T, class JT = T>
+__device__ __forceinline__ void transport(T p[21], const Jac<JT> &J)
 {
     T y[6];
 #pragma unroll
@@ -246,7 +261,7 @@ __device__ __forceinline__ void transport(T p[21], const Jac<T> &J)
         B[4][j] = p4 + J.ap3 * p3;
         B[5][j] = p5;
     }
-    const T u[6] = {J.u0, J.u1, J.u2, T(0), J.u4, T(0)};
+    const JT u[6] = {J.u0, J.u1, J.u2, JT(0), J.u4, JT(0)};
     // C = B A^T (lower triangle) plus the rank-2 terms
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -272,8 +287,8 @@ __device__ __forceinline__ void transport(T p[21], const Jac<T> &J)
 // u a^T + a u^T + gamma u u^T as in transport, with A P A^T written out for this
 // P (A = I + N, N's entries ax3, ax4, ay3, ay4, az5, ap3 all in columns 3..5):
 // about 90 FMA instead of 180.
-template <class T>
-__device__ __forceinline__ void transport_seeded(T p[21], const Jac<T> &J)
+template <class T, class JT = T>
+__device__ __forceinline__ void transport_seeded(T p[21], const Jac<JT> &J)
 {
     const T d3 = p[pk(3, 3)], d4 = p[pk(4, 4)], d5 = p[pk(5, 5)];
     T y[6];
@@ -316,7 +331,7 @@ __device__ __forceinline__ void transport_seeded(T p[21], const Jac<T> &J)
     c[pk(5, 3)] = T(0);
     c[pk(5, 4)] = T(0);
     c[pk(5, 5)] = d5;
-    const T u[6] = {J.u0, J.u1, J.u2, T(0), J.u4, T(0)};
+    const JT u[6] = {J.u0, J.u1, J.u2, JT(0), J.u4, JT(0)};
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
 #pragma unroll
@@ -867,7 +882,7 @@ __device__ __forceinline__ bool fit_step_on(Track<T, P> &st, C p[21], int k, T a
     if (k > 0) {
         Jac<T> J;
         if (!propagate(st, alpha, sf, J)) {
-            status |= KF_ST_NO_INTERSECT;
+            status |= reach_bits(st);
             return false;
         }
         if (SEEDED || seeded) transport_seeded<C>(p, JacAs<C>::get(J));

@@ -32,6 +32,8 @@ KF_ST_CHOL_FAIL = 2
 KF_ST_NONFINITE = 4
 KF_ST_CAND_CAPPED = 8
 KF_ST_GRAZING = 16
+KF_ST_THETA_RANGE = 32
+KF_ST_FP64_TRACK = 64
 
 KF_PREC_MIXED = 0
 KF_PREC_FP64 = 1
@@ -39,6 +41,8 @@ KF_SCHED_GRID = 0
 KF_SCHED_PERSISTENT = 1
 KF_MEAS_LAYER = 0
 KF_MEAS_HIT_2D = 1
+KF_SEED_UD_DF = 0
+KF_SEED_JOSEPH_FP64 = 1
 KF_MAX_SURFACES = 64
 KF_NPHI = 1024
 KF_NZ = 64
@@ -64,7 +68,8 @@ class kf_geometry(C.Structure):
 
 class kf_fit_params(C.Structure):
     _fields_ = [("precision", C.c_int32), ("n_fp64_updates", C.c_int32), ("seed_cov", C.c_double),
-                ("ms_on", C.c_int32), ("schedule", C.c_int32), ("meas_model", C.c_int32), ("pad_", C.c_int32)]
+                ("ms_on", C.c_int32), ("schedule", C.c_int32), ("meas_model", C.c_int32),
+                ("seed_update", C.c_int32)]
 
 
 class kf_seeds(C.Structure):
@@ -88,7 +93,7 @@ class kf_binned_layer(C.Structure):
 
 class kf_build_params(C.Structure):
     _fields_ = [("nsigma", C.c_double), ("chi2_cut", C.c_double), ("max_cand", C.c_int32),
-                ("warp_coop", C.c_int32)]
+                ("warp_coop", C.c_int32), ("debug_pred", C.c_void_p)]
 
 
 class kf_server_params(C.Structure):
@@ -137,6 +142,9 @@ _SIGS = {
                                   C.c_double, C.POINTER(kf_tracks_out), C.c_void_p]),
     "kf_fit_host": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
                               C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out), C.c_int32]),
+    "kf_fit_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "kf_fit_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
     "kf_autotune_fit": (C.c_int, [C.c_void_p, C.POINTER(kf_geometry), C.POINTER(kf_fit_params), C.c_int32,
                                   C.POINTER(kf_seeds), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_out),
                                   C.c_void_p, C.c_char_p, C.c_size_t]),
@@ -234,9 +242,10 @@ def make_geometry(geom: dict):
 
 
 def fit_params(precision=KF_PREC_MIXED, n_fp64_updates=3, seed_cov=1e4, ms_on=True, schedule=KF_SCHED_GRID,
-               meas_model=KF_MEAS_LAYER):
+               meas_model=KF_MEAS_LAYER, seed_update=KF_SEED_UD_DF):
     return kf_fit_params(precision=int(precision), n_fp64_updates=int(n_fp64_updates), seed_cov=float(seed_cov),
-                         ms_on=int(bool(ms_on)), schedule=int(schedule), meas_model=int(meas_model))
+                         ms_on=int(bool(ms_on)), schedule=int(schedule), meas_model=int(meas_model),
+                         seed_update=int(seed_update))
 
 
 # ---------------------------------------------------------------- entry points (same names as kf.h)
@@ -312,6 +321,18 @@ def kf_fit_host(ctx, geom, params, n, offsets, layer, x, y, z, out_state=None, o
     _check(ctx, load().kf_fit_host(ctx, C.byref(g), C.byref(p), int(n), C.byref(h), C.byref(o), int(n_chunks)))
 
 
+def kf_fit_timing(ctx, enable=True):
+    _check(ctx, load().kf_fit_timing(ctx, int(bool(enable))))
+
+
+def kf_fit_phase_times(ctx):
+    """(timed calls, mean phase-1 ms, mean phase-2 ms) of the grid-schedule kf_fit calls
+    timed on ctx since kf_fit_timing(ctx, True)."""
+    m, a, b = C.c_int32(0), C.c_double(0.0), C.c_double(0.0)
+    _check(ctx, load().kf_fit_phase_times(ctx, C.byref(m), C.byref(a), C.byref(b)))
+    return m.value, a.value, b.value
+
+
 def kf_autotune_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, out_state=None,
                     out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None) -> str:
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
@@ -361,9 +382,12 @@ def binned_layers(layer_dicts):
     return arr
 
 
-def build_params(nsigma=3.0, chi2_cut=30.0, max_cand=32, warp_coop=False):
+def build_params(nsigma=3.0, chi2_cut=30.0, max_cand=32, warp_coop=False, debug_pred=None):
+    """debug_pred: None, or a CUDA FP64 tensor of n_layers * 27 * n values (kf_build_besthit
+    writes each track's predicted state and covariance per build layer into it)."""
     return kf_build_params(nsigma=float(nsigma), chi2_cut=float(chi2_cut), max_cand=int(max_cand),
-                           warp_coop=int(bool(warp_coop)))
+                           warp_coop=int(bool(warp_coop)),
+                           debug_pred=None if debug_pred is None else debug_pred.data_ptr())
 
 
 def kf_build_besthit(ctx, geom, fit, bp, n_events, n_layers, layers, event_offsets, seed_state, seed_q, seed_hits,

@@ -52,9 +52,9 @@ def make_seeds(ctx, geom, dh, stream=None):
 
 
 def fit(ctx, geom, dh, seeds, out, precision=kf.KF_PREC_MIXED, n_fp64=3, ms_on=True,
-        schedule=kf.KF_SCHED_GRID, stream=None, meas_model=kf.KF_MEAS_LAYER):
+        schedule=kf.KF_SCHED_GRID, stream=None, meas_model=kf.KF_MEAS_LAYER, seed_update=kf.KF_SEED_UD_DF):
     p = kf.fit_params(precision=precision, n_fp64_updates=n_fp64, ms_on=ms_on, schedule=schedule,
-                      meas_model=meas_model)
+                      meas_model=meas_model, seed_update=seed_update)
     kf.kf_fit(ctx, geom, p, dh["n"], seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
               out["state"], out["cov"], out["chi2"], out["ndof"], out["status"], stream=stream)
 
@@ -73,14 +73,14 @@ def unpack_cov(cov21: np.ndarray) -> np.ndarray:
 
 
 def fit_numpy(ctx, geom, tk, precision=kf.KF_PREC_MIXED, n_fp64=3, ms_on=True, schedule=kf.KF_SCHED_GRID,
-              meas_model=kf.KF_MEAS_LAYER):
+              meas_model=kf.KF_MEAS_LAYER, seed_update=kf.KF_SEED_UD_DF):
     """End to end on numpy CSR hits: seeds + fit on the GPU; numpy results (track-major)."""
     g = kf.make_geometry(geom)
     dh = hits_to_device(tk)
     seeds = make_seeds(ctx, g, dh)
     out = alloc_fit_out(dh["n"])
     fit(ctx, g, dh, seeds, out, precision=precision, n_fp64=n_fp64, ms_on=ms_on, schedule=schedule,
-        meas_model=meas_model)
+        meas_model=meas_model, seed_update=seed_update)
     torch.cuda.synchronize()
     return dict(seed=seeds[0].t().double().cpu().numpy(), q=seeds[1].cpu().numpy(),
                 state=out["state"].t().cpu().numpy(), cov=unpack_cov(out["cov"].cpu().numpy()),
@@ -121,9 +121,11 @@ def seeds_from_seed_hits(ctx, geom, seed_hits_np, device="cuda", stream=None):
 
 
 def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, nsigma=3.0, chi2_cut=30.0,
-                max_cand=32, n_slots=0, meas_model=kf.KF_MEAS_LAYER):
+                max_cand=32, n_slots=0, meas_model=kf.KF_MEAS_LAYER, record_pred=False):
     """Bin every event's layers, seed, and run best-hit building of all events in one
-    launch; returns numpy idx (n, n_layers) and fitted tracks (track-major)."""
+    launch; returns numpy idx (n, n_layers) and fitted tracks (track-major).  record_pred
+    (best-hit only): also 'pred' (n, n_layers, 27), each build step's predicted state and
+    packed covariance (NaN where a track did not get to the layer)."""
     g = kf.make_geometry(geom)
     binned = [bin_event(ctx, geom, ev) for ev in events]
     n_layers = len(events[0]["layers"])
@@ -141,12 +143,17 @@ def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, 
                         n_slots, len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
                         out["chi2"], out["ndof"], out["status"])
     else:
+        pred = torch.full((n_layers * 27 * n,), float("nan"), dtype=torch.float64, device="cuda") \
+            if record_pred else None
         kf.kf_build_besthit(ctx, g, kf.fit_params(precision=precision, meas_model=meas_model),
-                            kf.build_params(nsigma, chi2_cut, max_cand, warp_coop),
+                            kf.build_params(nsigma, chi2_cut, max_cand, warp_coop, debug_pred=pred),
                             len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
                             out["chi2"], out["ndof"], out["status"])
     torch.cuda.synchronize()
-    return dict(idx=idx.t().cpu().numpy(), state=out["state"].t().cpu().numpy(),
+    extra = {}
+    if not n_slots and record_pred:
+        extra["pred"] = pred.view(n_layers, 27, n).permute(2, 0, 1).cpu().numpy()
+    return dict(extra, idx=idx.t().cpu().numpy(), state=out["state"].t().cpu().numpy(),
                 cov=unpack_cov(out["cov"].cpu().numpy()), chi2=out["chi2"].cpu().numpy(),
                 ndof=out["ndof"].cpu().numpy(), status=out["status"].cpu().numpy().astype(np.uint32),
                 q=q.cpu().numpy(), binned=binned, layers=layers, eoff=eoff, sh9=sh9, idx_dev=idx)

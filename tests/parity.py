@@ -81,18 +81,22 @@ def summary(res):
             f"max dchi2/chi2={res['chi2rel'].max():.3e} max dcov={res['dcov'].max():.3e}")
 
 
-def oracle_self_noise(oracle_mod, geom, tk, orc, kinds, eps=1e-14):
-    """Per-track numerical resolution of the FP64 oracle itself: max |dp|/sigma between
-    the oracle's fit and the same fit with its seed phi moved by eps rad.  Under the
-    1e4 seed covariance the covariance-form update amplifies rounding by up to ~1e9
-    in the first updates; on most tracks the result moves by ~1e-7 sigma, on rare
-    tracks (a disk hit next to a barrel hit among the first hits) by up to ~5e-3 sigma.
-    No implementation can be compared more finely than this."""
-    s = orc["seed"].copy()
-    s[:, 4] += eps
-    o2 = oracle_mod.fit(geom, tk, seeds=s, q=orc["q"])
+def oracle_self_noise(oracle_mod, geom, tk, orc, kinds, eps=1e-14, threads=4):
+    """Per-track numerical resolution of the FP64 oracle itself: the largest max |dp|/sigma
+    between the oracle's fit and the same fit from a seed moved by a rounding-sized step,
+    over eight directions (phi and theta by +-eps rad, 1/pT and z by +-eps relative).  Under the
+    1e4 seed covariance the covariance-form update amplifies rounding by up to ~1e9 in
+    the first updates; on most tracks the result moves by ~1e-7 sigma, on rare steep
+    barrel+disk tracks by up to ~5e-3 sigma, and one direction alone can miss a track's
+    sensitivity by an order of magnitude.  No implementation can be compared more finely
+    than this."""
     ok = (orc["status"] & 7) == 0
-    res = compare_fits(o2, orc, kinds, ok)
     noise = np.zeros(len(ok))
-    noise[ok] = res["max_pull"]
+    for comp, relative in ((4, False), (5, False), (3, True), (2, True)):
+        for sgn in (1.0, -1.0):
+            s = orc["seed"].copy()
+            s[:, comp] += sgn * eps * (np.abs(s[:, comp]) if relative else 1.0)
+            o2 = oracle_mod.fit(geom, tk, seeds=s, q=orc["q"], threads=threads)
+            res = compare_fits(o2, orc, kinds, ok)
+            noise[ok] = np.maximum(noise[ok], res["max_pull"])
     return noise

@@ -91,15 +91,65 @@ def test_fit_parity_17_layers_ragged(ctx, oracle_mod, precision):
     _check_fit(tk, orc, gpu, g, label=f"barrel17 prec={precision}")
 
 
-def test_fit_parity_cylinder_with_lids(ctx, oracle_mod):
+@pytest.mark.parametrize("precision,seed_update", [(kf.KF_PREC_MIXED, kf.KF_SEED_UD_DF),
+                                                   (kf.KF_PREC_MIXED, kf.KF_SEED_JOSEPH_FP64),
+                                                   (kf.KF_PREC_FP64, kf.KF_SEED_UD_DF)])
+def test_fit_parity_cylinder_with_lids(ctx, oracle_mod, precision, seed_update):
+    """The barrel closed by end-cap disks (Sec. 4.1), |eta| < 2.5, 20,000 tracks: every
+    track within max(1e-3 sigma, 3 x the oracle's own resolution), tracks that cross a
+    layer twice in a row fitted in FP64 (KF_ST_FP64_TRACK), tracks whose theta left
+    (0, pi) ended with KF_ST_THETA_RANGE on both sides."""
     g = synth.geometry("lids")
-    tk = synth.gen_tracks(g, 3000, synth.BASE_SEED + 4, eta_max=2.5, min_hits=4)
-    orc = oracle_mod.fit(g, tk)
+    tk = synth.gen_tracks(g, 20000, synth.BASE_SEED + 4, eta_max=2.5, min_hits=4)
+    orc = oracle_mod.fit(g, tk, threads=4)
     kinds = np.array([g["surfaces"][s]["kind"] for s in parity.last_surface(tk, orc["ndof"])])
     noise = parity.oracle_self_noise(oracle_mod, g, tk, orc, kinds)
-    for prec in (kf.KF_PREC_MIXED, kf.KF_PREC_FP64):
-        gpu = run.fit_numpy(ctx, g, tk, precision=prec)
-        _check_fit(tk, orc, gpu, g, label=f"lids prec={prec}", noise=noise)
+    gpu = run.fit_numpy(ctx, g, tk, precision=precision, seed_update=seed_update)
+    np.testing.assert_array_equal(gpu["status"] & kf.KF_ST_THETA_RANGE, orc["status"] & kf.KF_ST_THETA_RANGE)
+    off = tk["offsets"]
+    recross = np.array([np.any(tk["layer"][off[t] + 1:off[t + 1]] == tk["layer"][off[t]:off[t + 1] - 1])
+                        for t in range(tk["n"])])
+    if precision == kf.KF_PREC_MIXED:
+        np.testing.assert_array_equal((gpu["status"] & kf.KF_ST_FP64_TRACK) != 0, recross)
+    print(f"lids: {recross.sum()} tracks cross a layer twice in a row, "
+          f"{np.sum((orc['status'] & kf.KF_ST_THETA_RANGE) != 0)} leave (0, pi)")
+    _check_fit(tk, orc, gpu, g, label=f"lids prec={precision} seed={seed_update}", noise=noise)
+
+
+def test_fit_parity_uneven_batch_persistent_sampled(ctx, oracle_mod):
+    """The uneven batch at its own size: 2,000,000 barrel+disk tracks (4 to 26 hits)
+    in the autotuned persistent launch replayed as a CUDA graph, as the benchmark
+    times it; the oracle checks a sample of 2,000 tracks with the bound of the
+    barrel+disk test."""
+    g = synth.geometry("lids")
+    gg = kf.make_geometry(g)
+    tkd = synth.gen_tracks(g, 2_000_000, synth.BASE_SEED + 4, eta_max=2.5, min_hits=4, device="cuda")
+    n = tkd["n"]
+    dh = run.hits_to_device(tkd)
+    seeds = run.make_seeds(ctx, gg, dh)
+    out = run.alloc_fit_out(n)
+    p = kf.fit_params(schedule=kf.KF_SCHED_PERSISTENT)
+    kf.kf_autotune_fit(ctx, gg, p, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                       out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+    for _ in range(2):  # graph capture, then a replay
+        kf.kf_fit(ctx, gg, p, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                  out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+    torch.cuda.synchronize()
+    tk = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in tkd.items()}
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(n, 2000, replace=False))
+    off = tk["offsets"]
+    rows = np.concatenate([np.arange(off[t], off[t + 1]) for t in idx])
+    sub = dict(offsets=np.concatenate([[0], np.cumsum(np.diff(off)[idx])]).astype(np.int32),
+               layer=tk["layer"][rows], x=tk["x"][rows], y=tk["y"][rows], z=tk["z"][rows], n=len(idx))
+    orc = oracle_mod.fit(g, sub, threads=4)
+    kinds = np.array([g["surfaces"][s]["kind"] for s in parity.last_surface(sub, orc["ndof"])])
+    noise = parity.oracle_self_noise(oracle_mod, g, sub, orc, kinds)
+    gpu = dict(seed=seeds[0].t().double().cpu().numpy()[idx], q=seeds[1].cpu().numpy()[idx],
+               state=out["state"].t().cpu().numpy()[idx], cov=run.unpack_cov(out["cov"][:, idx].cpu().numpy()),
+               chi2=out["chi2"].cpu().numpy()[idx], ndof=out["ndof"].cpu().numpy()[idx],
+               status=out["status"].cpu().numpy().astype(np.uint32)[idx])
+    _check_fit(sub, orc, gpu, g, label="uneven 2e6 persistent sampled", noise=noise)
 
 
 @pytest.mark.parametrize("precision", [kf.KF_PREC_MIXED, kf.KF_PREC_FP64])

@@ -829,3 +829,123 @@ def test_model1_reduces_to_model0_on_the_ideal_barrel(oracle_mod):
     assert np.median(res["max_pull"]) < 1e-4, parity.summary(res)
     assert np.percentile(res["max_pull"], 99) < 1e-2, parity.summary(res)
     assert np.median(res["chi2rel"]) < 1e-4, parity.summary(res)
+
+
+# ---------------------------------------------------------------------- theta range (reading of the parametrisation's pole)
+
+def test_propagation_refused_outside_theta_range(oracle_mod):
+    """A state whose theta has left (0, pi) is not propagated: the (.., phi, theta)
+    parametrisation has its pole there (dz/ds = cot(theta) diverges and changes sign)."""
+    surf = _barrel(10.0)
+    start = np.array([4.0, 0.0, 0.0, 0.2, 0.0, 0.0])
+    for th, want in ((0.05, 0), (math.pi - 0.05, 0), (-0.05, 1 | 32), (math.pi + 0.05, 1 | 32), (0.0, 1 | 32)):
+        st = start.copy()
+        st[5] = th
+        rc, out, _ = oracle_mod.propagate(st, 1, BZ, surf)
+        assert rc == want, (th, rc)
+        if want == 0:
+            assert math.hypot(out[0], out[1]) == pytest.approx(10.0, abs=1e-9)
+
+
+def test_fit_ends_when_an_update_crosses_the_theta_pole(oracle_mod):
+    """Hits far above a steep prediction pull theta through zero in the second
+    update; the fit keeps that update (its state is reported) and ends before the
+    next propagation, with NO_INTERSECT | THETA_RANGE.  Hits that keep theta in
+    range are all used."""
+    g = synth.geometry("barrel10")
+    hx = np.array([4.0, 8.0, 12.0, 16.0], np.float32)
+    hy = np.zeros(4, np.float32)
+    seed = np.array([4.0, 0.0, 0.0, 0.2, 0.0, 0.05])
+    far = oracle_mod.fit_one(g, [0, 1, 2, 3], hx, hy, np.array([0, 200, 400, 600], np.float32), seed, 1)
+    assert far["status"] & 32 and far["status"] & 1
+    assert far["n_used"] == 2 and far["ndof"] == -1
+    assert not (0.0 < far["state"][5] < math.pi)
+    near = oracle_mod.fit_one(g, [0, 1, 2, 3], hx, hy, np.array([0, 50, 100, 150], np.float32), seed, 1)
+    assert not (near["status"] & 33)
+    assert near["n_used"] == 4 and 0.0 < near["state"][5] < math.pi
+
+
+# ---------------------------------------------------------------------- build window (Sec. 3.1, 4.1)
+
+def _tangent_cov(phi0, sig_t, sig_z, rho_tz, sig_n=0.0, rho_nt=0.0):
+    """6x6 covariance whose position block has variance sig_t^2 along phi-hat at azimuth
+    phi0, sig_n^2 along r-hat, sig_z^2 along z, with correlations rho_tz (phi-hat, z) and
+    rho_nt (r-hat, phi-hat); the angle block is an arbitrary positive diagonal."""
+    rh = np.array([math.cos(phi0), math.sin(phi0), 0.0])
+    ph = np.array([-math.sin(phi0), math.cos(phi0), 0.0])
+    zh = np.array([0.0, 0.0, 1.0])
+    E = np.stack([rh, ph, zh], 1)
+    L = np.array([[sig_n ** 2, rho_nt * sig_n * sig_t, 0.0],
+                  [rho_nt * sig_n * sig_t, sig_t ** 2, rho_tz * sig_t * sig_z],
+                  [0.0, rho_tz * sig_t * sig_z, sig_z ** 2]])
+    P = np.diag([0.0, 0.0, 0.0, 1e-4, 1e-6, 1e-6])
+    P[:3, :3] = E @ L @ E.T
+    return P
+
+
+@pytest.mark.parametrize("case", ["x_axis", "y_axis", "diag45_correlated", "diag135_radial", "generic"])
+def test_window_widths_match_sampled_prediction_and_hit_scatter(oracle_mod, case):
+    """The window is nsigma times the spread of (hit - prediction): sample predicted
+    positions from N(pred, P_pos) and hits scattered by the resolution on the cylinder
+    (r-phi by sig_rphi, z by sig_z), and compare the sample std of the azimuth and z
+    differences with the oracle's half widths / nsigma.  Position blocks with an x-y
+    correlation (off the axes), a radial component and r-phi/z correlation make a sign
+    error on the x-y term, r^2 for r^4, or a dropped resolution term each fail."""
+    R = 30.0
+    surf = _barrel(R)
+    phi0, sig_t, sig_n, rho_nt = dict(x_axis=(0.0, 0.02, 0.0, 0.0), y_axis=(math.pi / 2, 0.02, 0.0, 0.0),
+                                      diag45_correlated=(math.pi / 4, 0.015, 0.01, 0.6),
+                                      diag135_radial=(3 * math.pi / 4, 0.012, 0.02, -0.5),
+                                      generic=(-2.2, 0.008, 0.004, 0.3))[case]
+    P = _tangent_cov(phi0, sig_t, 0.05, 0.4, sig_n, rho_nt)
+    st = np.array([R * math.cos(phi0), R * math.sin(phi0), 3.0, 0.3, phi0 + 0.2, 1.2])
+    dphi, dz = oracle_mod.window(st, P, surf, nsigma=3.0)
+    rng = np.random.default_rng(11)
+    N = 1_000_000
+    pos = rng.multivariate_normal(st[:3], P[:3, :3], size=N, method="eigh")
+    # hits: truth at the prediction's centre, scattered on the cylinder
+    a_hit = phi0 + rng.normal(0.0, surf["sig_rphi"], N) / R
+    z_hit = st[2] + rng.normal(0.0, surf["sig_3"], N)
+    dphi_s = (a_hit - np.arctan2(pos[:, 1], pos[:, 0]) + np.pi) % (2 * np.pi) - np.pi
+    dz_s = z_hit - pos[:, 2]
+    s_phi, s_z = np.std(dphi_s), np.std(dz_s)
+    # sampling error of a std over 1e6 draws ~ 0.07 %; curvature of atan2 ~ (sigma / R)^2
+    assert dphi / 3.0 == pytest.approx(s_phi, rel=4e-3), (dphi / 3.0, s_phi)
+    assert dz / 3.0 == pytest.approx(s_z, rel=4e-3), (dz / 3.0, s_z)
+
+
+def test_window_with_a_point_prediction_is_the_hit_resolution(oracle_mod):
+    """No prediction uncertainty: the window is nsigma times the hit's own scatter,
+    sig_rphi / R in azimuth and sig_z in z."""
+    for R in (4.0, 40.0, 100.0):
+        surf = _barrel(R)
+        st = np.array([0.0, R, -7.0, 0.5, 1.6, 1.0])
+        dphi, dz = oracle_mod.window(st, np.zeros((6, 6)), surf, nsigma=2.5)
+        assert dphi == pytest.approx(2.5 * 0.01 / R, rel=1e-12)
+        assert dz == pytest.approx(2.5 * 0.1, rel=1e-12)
+
+
+@pytest.mark.parametrize("a,theta", [(0.1, 1.2), (0.6, 0.8), (1.1, 2.0), (-0.8, 1.45)])
+def test_window_model1_widening_is_the_sweep_over_dr(oracle_mod, a, theta):
+    """Measurement model 1 widens the window by the azimuth and z that the track sweeps
+    while it crosses +-dr around the average radius.  Propagate the predicted state
+    (10 GeV, nearly straight) with the oracle's own helix to R - dr and R + dr and take
+    the mean of the two excursions of the position's azimuth and z (their first-order
+    part: the second-order terms, ~ (dr / R) tan^2(a), have opposite signs on the two
+    sides); it equals the widening."""
+    R, dr = 30.0, 0.25
+    surf = dict(_barrel(R), dr=dr)
+    phi_pos = 0.4
+    st = np.array([R * math.cos(phi_pos), R * math.sin(phi_pos), 2.0, 0.1, phi_pos + a, theta])
+    P = _tangent_cov(phi_pos, 0.02, 0.05, 0.0)
+    d0 = oracle_mod.window(st, P, surf, nsigma=3.0, meas_model=0)
+    d1 = oracle_mod.window(st, P, surf, nsigma=3.0, meas_model=1)
+    sweep_phi, sweep_z = [], []
+    for Rt in (R - dr, R + dr):
+        rc, out, _ = oracle_mod.propagate(st, 1, BZ, _barrel(Rt), want_jac=False)
+        assert rc == 0
+        sweep_phi.append(abs((math.atan2(out[1], out[0]) - phi_pos + math.pi) % (2 * math.pi) - math.pi))
+        sweep_z.append(abs(out[2] - st[2]))
+    # what is left: (dr / R)^2 terms and the helix's bend over the crossing, O(c dr)
+    assert d1[0] - d0[0] == pytest.approx(np.mean(sweep_phi), rel=3e-3)
+    assert d1[1] - d0[1] == pytest.approx(np.mean(sweep_z), rel=3e-3)
