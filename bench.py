@@ -31,19 +31,22 @@ N_TRACKS = 1_000_000
 WORKLOAD = ("KF fit of 1,000,000 tracks x 17 barrel layers (R 4-100 cm), Bz 3.8 T, x/X0 0.02, "
             "pT log-uniform 0.5-10 GeV, |eta|<1, seeds from 3 hits, seed cov 1e4")
 
-# Algorithmic work per unit, counted from the formulas the fit kernel evaluates:
-# FP64 FLOP of the seed phase per track (structured seed-hit update 187, the
-# first transport on the covariance that update leaves 151, the second 310, two
-# Joseph updates 2 x 542, noise 6) and of the
-# FP64 S solve per later update (LDL^T 29 + chi2 15); FP32 FLOP per later update
-# (propagation ~250, transport 310, noise ~25, update ~314).
-# DRAM bytes (read + write) of one fit-kernel launch on this workload, from an
-# ncu capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
-# set to None whenever the kernel changes until it is captured again
-FIT_KERNEL_DRAM_BYTES = 3.604e9
-FP64_FLOP_SEED_PHASE = 1738.0
+# Algorithmic work per unit, counted from the formulas the two fit kernels evaluate.
+# Phase 1 (fit_seed_kernel, per track with barrel seed hits): the first
+# transport in FP64 on the covariance the closed-form seed-hit update leaves
+# (151 FLOP) and the conversions of that covariance to FP64 and back (42 FLOP),
+# chi2 (1); the rest in double-float on the FP32 pipe.  Phase 2
+# (fit_loop_kernel, per later update): the FP64 S solve (LDL^T 29 + chi2 15);
+# FP32 (propagation ~250, transport 310, noise ~25, update ~314).
+# DRAM bytes (read + write) of one fit_loop_kernel launch on this workload, from
+# an ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); None whenever the kernel changes until it is captured again
+LOOP_KERNEL_DRAM_BYTES = 2.816e9
+FP64_FLOP_PHASE1_BARREL = 194.0
 FP64_FLOP_PER_FP32_UPDATE = 44.0
 FP32_FLOP_PER_FP32_UPDATE = 900.0
+# carry from phase 1 to phase 2 per track: state 11 + covariance 21 floats, chi2, k, used, status
+CARRY_BYTES_PER_TRACK = 4 * 11 + 4 * 21 + 8 + 3 * 4
 
 
 def parse():
@@ -620,6 +623,7 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kf.kf_fit_timing(ctx, True)  # events around the two fit kernels of every timed step (no sync)
     e0.record(stream)
     for k in range(args.steps):
         kf.kf_make_seeds(ctx, g, n, dh["offsets"], dh["x"], dh["y"], dh["z"], seeds[0], seeds[1])
@@ -631,34 +635,44 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
+    n_timed, ms_phase1, ms_phase2 = kf.kf_fit_phase_times(ctx)
+    kf.kf_fit_timing(ctx, False)
     ms_local = e0.elapsed_time(e1) / args.steps
     fit_ms = [a.elapsed_time(b) for a, b in ev]
     ms, total_updates, value = aggregate(ms_local, updates_per_step, world)
 
-    # roofline of the fit kernel: FP64 pipe (dominant), FP32 pipe, HBM
+    # roofline of the dominant kernel, phase 2 (fit_loop_kernel): FP64 pipe (its
+    # S solves), with the FP32 pipe and HBM beside it; phase 1 (fit_seed_kernel) apart
     nh = len(tk["x"])
     fp32_updates = updates_per_step - 3 * n
-    fp64_flop = FP64_FLOP_SEED_PHASE * n + FP64_FLOP_PER_FP32_UPDATE * fp32_updates
-    fp32_flop = FP32_FLOP_PER_FP32_UPDATE * fp32_updates
-    bytes_alg = 4 * (n + 1) + 13 * nh + 25 * n + (48 + 168 + 8 + 4 + 4) * n
+    fp64_flop2 = FP64_FLOP_PER_FP32_UPDATE * fp32_updates
+    fp32_flop2 = FP32_FLOP_PER_FP32_UPDATE * fp32_updates
+    fp64_flop1 = FP64_FLOP_PHASE1_BARREL * n
+    bytes_alg = 4 * (n + 1) + 13 * nh + 25 * n + (48 + 168 + 8 + 4 + 4) * n  # the whole fit
+    bytes2 = 4 * (n + 1) + 13 * (nh - 3 * n) + 4 * n + CARRY_BYTES_PER_TRACK * n + (48 + 168 + 8 + 4 + 4) * n
     fit_avg = float(np.mean(fit_ms))
     peak64 = kf.kf_measure_peak(ctx, 0)
     peak32 = kf.kf_measure_peak(ctx, 1)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    ach64 = fp64_flop / (fit_avg * 1e-3) / 1e12
-    roofline = dict(bound="alu", pipe="fp64", achieved=ach64, peak=peak64 / 1e12, unit="TFLOP/s",
-                    frac=ach64 / (peak64 / 1e12),
-                    traffic=FIT_KERNEL_DRAM_BYTES if n == N_TRACKS and FIT_KERNEL_DRAM_BYTES else None,
+    ach64 = fp64_flop2 / (ms_phase2 * 1e-3) / 1e12
+    roofline = dict(bound="alu", pipe="fp64", kernel="fit_loop_kernel (phase 2: the FP32 layer loop)",
+                    achieved=ach64, peak=peak64 / 1e12, unit="TFLOP/s", frac=ach64 / (peak64 / 1e12),
+                    traffic=LOOP_KERNEL_DRAM_BYTES if n == N_TRACKS and LOOP_KERNEL_DRAM_BYTES else None,
                     peak_source="kf_measure_peak FP64 FMA chains (measured in this run); nominal 152 SMs x 2 "
                                 "DFMA/clock x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s",
-                    fp32=dict(achieved=fp32_flop / (fit_avg * 1e-3) / 1e12, peak=peak32 / 1e12, unit="TFLOP/s",
-                              frac=fp32_flop / (fit_avg * 1e-3) / peak32),
-                    hbm=dict(achieved=bytes_alg / (fit_avg * 1e-3) / 1e9, peak=hbm, unit="GB/s",
-                             frac=bytes_alg / (fit_avg * 1e-3) / 1e9 / hbm, peak_source="MEASURED_PEAKS.json"),
-                    fit_ms_per_launch=fit_avg, fp64_flop_per_launch=fp64_flop, fp32_flop_per_launch=fp32_flop,
-                    bytes_per_launch=bytes_alg)
+                    kernel_ms_per_launch=ms_phase2, launches_timed=n_timed, fp64_flop_per_launch=fp64_flop2,
+                    fp32=dict(achieved=fp32_flop2 / (ms_phase2 * 1e-3) / 1e12, peak=peak32 / 1e12,
+                              unit="TFLOP/s", frac=fp32_flop2 / (ms_phase2 * 1e-3) / peak32,
+                              flop_per_launch=fp32_flop2),
+                    hbm=dict(achieved=bytes2 / (ms_phase2 * 1e-3) / 1e9, peak=hbm, unit="GB/s",
+                             frac=bytes2 / (ms_phase2 * 1e-3) / 1e9 / hbm, bytes_per_launch=bytes2,
+                             peak_source="MEASURED_PEAKS.json"),
+                    phase1=dict(kernel="fit_seed_kernel (seed phase: double-float U-D, FP64 first transport)",
+                                ms_per_launch=ms_phase1, fp64_flop_per_launch=fp64_flop1,
+                                fp64_achieved=fp64_flop1 / (ms_phase1 * 1e-3) / 1e12),
+                    fit_ms_per_launch=fit_avg, fit_bytes_per_launch=bytes_alg)
 
     if args.quick:
         if rank == 0:
@@ -784,7 +798,8 @@ def main():
                 ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
                 data="synthetic",
                 config=dict(workload=WORKLOAD, tracks_per_gpu=n, layers=17, updates_per_step=updates_per_step,
-                            precision="mixed: FP32 + FP64 S solve, FP64 seed phase",
+                            precision="mixed: FP32 layer loop with FP64 S solves; seed phase in double-float "
+                                      "U-D form (FP64 first transport)",
                             l2="inputs larger than L2 (hits 221 MB + outputs 232 MB per step)",
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 roofline=roofline, cpu_baseline=cpu_baseline,
@@ -792,7 +807,7 @@ def main():
                          ms_per_step=t_e2e * 1e3, api="kf_fit_host", host_matches_device=bool(same)),
                 fp64_path=dict(value=updates_per_step * world / (ms64 * 1e-3), unit=UNIT, fit_ms=ms64,
                                speedup_of_mixed=ms64 / fit_avg),
-                gpu_launches=5 * args.steps, clocks=clk, parity_vs_oracle=parity, build=build, uneven_batch=uneven,
+                gpu_launches=6 * args.steps, clocks=clk, parity_vs_oracle=parity, build=build, uneven_batch=uneven,
                 refit_inward=refit_line, nonideal=nonideal, serving=serving)
     if rank == 0:
         print(json.dumps(line), flush=True)

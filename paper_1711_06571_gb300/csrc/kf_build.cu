@@ -349,6 +349,67 @@ static __device__ __noinline__ Fp64LayerIO layer_step_fp64_out_of_line(Fp64Layer
     return io;
 }
 
+// A near-tangent layer step of the mixed build under measurement model 0: FP32
+// propagation; the transport and the scattering noise in double-float (the
+// Jacobian grows like 1 / cos(alpha) and FP32 arithmetic cannot carry the
+// transport); window and candidate scores from that covariance rounded to FP32,
+// as in layer_step_thread; the update with the chosen hit in double-float U-D
+// form (kf_df.cuh).
+__device__ __forceinline__ StepOut layer_step_df(Track<float, ff> &st, float pc[21], float alpha, float mass2,
+                                                 const StepKnobs &a, const Surf &sf, const LayerDev &ly,
+                                                 double &chi2, unsigned &status, bool &alive)
+{
+    StepOut o{-1, false};
+    Jac<float> J;
+    if (!propagate(st, alpha, sf, J)) {
+        status |= reach_bits(st);
+        alive = false;
+        return o;
+    }
+    df p[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) p[i] = df(pc[i]);
+    transport<df>(p, J);
+    if (a.ms_on) status |= ms_noise<float, df>(st, sf, J.cphi1, J.sphi1, mass2, p);
+    float pw[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pw[i] = p[i].hi;
+    debug_pred_put(a, st, pw);
+    const Window w = make_window(st, pw, sf, a.nsigma);
+    const bool shared = sf.var_rad == sf.var_rphi;
+    Ldl3 fs{0, 0, 0, 0, 0, 0};
+    if (shared && !shared_factor(pw, sf, fs)) {
+        status |= KF_ST_CHOL_FAIL;
+        alive = false;
+        return o;
+    }
+    int best = -1;
+    double bchi = 0.0;
+    float4 bhit = make_float4(0.f, 0.f, 0.f, 0.f);
+    score_own<false>(st, pw, pw, alpha, sf, ly, w, shared, fs, a.max_cand, best, bchi, bhit, o.capped);
+    if (best >= 0 && bchi < (double)a.chi2_cut) {
+        df c2 = df(0.f);
+        if (ud_update3(st, p, bhit.x, bhit.y, bhit.z, sf, c2)) {
+            chi2 += df_to_d(c2);
+            o.chosen = best;
+        } else {
+            status |= KF_ST_CHOL_FAIL;
+            alive = false;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 21; ++i) pc[i] = p[i].hi;
+    return o;
+}
+static __device__ __noinline__ Fp64LayerIO layer_step_df_out_of_line(Fp64LayerIO io, float alpha, float mass2,
+                                                                     StepKnobs kn, const Surf *sf, LayerDev ly)
+{
+    bool alive = io.alive != 0;
+    io.o = layer_step_df(io.m.st, io.m.p, alpha, mass2, kn, *sf, ly, io.m.chi2, io.m.status, alive);
+    io.alive = alive;
+    return io;
+}
+
 // Warp-cooperative scoring of one layer: every lane of the warp calls it; lanes
 // with do_step == false contribute no candidates.  Lanes list their window's
 // candidates as consecutive items of one warp-wide list; each round every lane
@@ -757,7 +818,9 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
                 Fp64LayerIO io;
                 mixed_pack(io.m, st, pc, chi2, status);
                 io.alive = alive;
-                io = layer_step_fp64_out_of_line<M1>(io, alphad, g.mass2d, knl, &sf, ly);
+                // model 0: the double-float step; model 1 (two propagations per step) in FP64
+                if constexpr (M1) io = layer_step_fp64_out_of_line<M1>(io, alphad, g.mass2d, knl, &sf, ly);
+                else io = layer_step_df_out_of_line(io, alpha, mass2, knl, &sf, ly);
                 mixed_unpack(io.m, st, pc, chi2, status);
                 alive = io.alive != 0;
                 so = io.o;
@@ -905,39 +968,23 @@ __global__ void __launch_bounds__(128) ckf_seed_kernel(const Geom g, const CkfAr
     c.seed_alive[t] = alive ? 1 : 0;
 }
 
-// prediction of a near-tangent crossing in FP64, out of line
-static __device__ __noinline__ MixedIO ckf_predict_fp64(MixedIO m, double alpha, double mass2, int ms_on,
-                                                       const Surf *sf)
+// prediction of a near-tangent crossing with the transport and scattering
+// noise in double-float (FP32 propagation), out of line
+static __device__ __noinline__ MixedIO ckf_predict_df(MixedIO m, float alpha, float mass2, int ms_on,
+                                                     const Surf *sf)
 {
-    Track<double, double> sd;
-    sd.x = to_d(m.st.x);
-    sd.y = to_d(m.st.y);
-    sd.z = to_d(m.st.z);
-    sd.phi = to_d(m.st.phi);
-    sd.th = to_d(m.st.th);
-    sd.ip = m.st.ip;
-    double pd[21];
-#pragma unroll
-    for (int i = 0; i < 21; ++i) pd[i] = f2d(m.p[i]);
-    Jac<double> J;
-    if (!propagate(sd, alpha, *sf, J)) {
+    Jac<float> J;
+    if (!propagate(m.st, alpha, *sf, J)) {
         m.ok = 0;
         return m;
     }
-    transport<double>(pd, J);
-    if (ms_on) m.status |= ms_noise<double, double>(sd, *sf, J.cphi1, J.sphi1, mass2, pd);
-    auto f = [](double d) {
-        const float h = (float)d;
-        return ff{h, (float)(d - (double)h)};
-    };
-    m.st.x = f(sd.x);
-    m.st.y = f(sd.y);
-    m.st.z = f(sd.z);
-    m.st.phi = f(sd.phi);
-    m.st.th = f(sd.th);
-    m.st.ip = (float)sd.ip;
+    df p[21];
 #pragma unroll
-    for (int i = 0; i < 21; ++i) m.p[i] = d2f(pd[i]);
+    for (int i = 0; i < 21; ++i) p[i] = df(m.p[i]);
+    transport<df>(p, J);
+    if (ms_on) m.status |= ms_noise<float, df>(m.st, *sf, J.cphi1, J.sphi1, mass2, p);
+#pragma unroll
+    for (int i = 0; i < 21; ++i) m.p[i] = p[i].hi;
     m.ok = 1;
     return m;
 }
@@ -996,8 +1043,7 @@ __global__ void __launch_bounds__(128, 4) ckf_kernel(const Geom g, const CkfArgs
     const LayerDev *lays = a.layers + (size_t)e * a.n_layers;
     const int q = a.q[t];
     const float alpha = float(-q) * g.kb;
-    const double alphad = -q * g.kbd;
-    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut};
+    const StepKnobs kn{a.ms_on, a.max_cand, a.nsigma, a.chi2_cut, nullptr, n};
     // the seed's candidate in slot 0; the other slots start empty
     Track<float, ff> st;
     st.x = ff{c.seed_st[0 * (size_t)n + t], c.seed_st[1 * (size_t)n + t]};
@@ -1028,7 +1074,7 @@ __global__ void __launch_bounds__(128, 4) ckf_kernel(const Geom g, const CkfArgs
             if (crossing_sine(st, alpha, sf) > 0.8f) {
                 MixedIO m;
                 mixed_pack(m, st, pc, chi2, 0u);
-                m = ckf_predict_fp64(m, alphad, g.mass2d, a.ms_on, &sf);
+                m = ckf_predict_df(m, alpha, g.mass2, a.ms_on, &sf);
                 if (m.ok) {
                     unsigned s2;
                     double c2;
