@@ -210,17 +210,22 @@ __device__ __forceinline__ unsigned reach_bits(const Track<T, P> &st)
 // the surface-constrained Jacobian grows like 1 / cos(alpha) and FP32 loses
 // the covariance transport.
 template <class T, class P>
-__device__ __forceinline__ T crossing_sine(const Track<T, P> &st, T alpha, const Surf &sf)
+__device__ __forceinline__ T crossing_sine(const Track<T, P> &st, T alpha, const Surf &sf, T sphi, T cphi)
 {
     T c = alpha * st.ip;
-    T sphi, cphi;
-    sincos_pos(st.phi, sphi, cphi);
     const T X = lead(st.x), Y = lead(st.y);
     const T R = spos<T>(sf);
     const T g0 = surf_excess(st.x, st.y, sf);
     const T pn = -X * sphi + Y * cphi;
     T sg = c > T(0) ? T(1) : (c < T(0) ? T(-1) : T(0));
     return (fabs(c) * (-g0) - T(2) * sg * pn) / (T(2) * R);
+}
+template <class T, class P>
+__device__ __forceinline__ T crossing_sine(const Track<T, P> &st, T alpha, const Surf &sf)
+{
+    T sphi, cphi;
+    sincos_pos(st.phi, sphi, cphi);
+    return crossing_sine(st, alpha, sf, sphi, cphi);
 }
 
 // P <- J P J^T with J = A + u w^T, as A P A^T + a u^T + u a^T + gamma u u^T,
@@ -873,15 +878,16 @@ __device__ __forceinline__ bool kf_seed_update(Track<T, Pp> &st, double p[21], f
 // (model 1, sf the hit's own cylinder).
 // SEEDED, or seeded at run time: P is the one left by the structured first
 // update (transport_seeded).
+// dir: the direction's sines and cosines of st when the caller has them, else null
 template <bool JOSEPH, class C, bool TWO_D, bool SEEDED = false, class T, class P>
 __device__ __forceinline__ bool fit_step_on(Track<T, P> &st, C p[21], int k, T alpha, T mass2, int ms_on,
                                             const Surf &sf, float hx, float hy, float hz, double &chi2,
-                                            unsigned &status, bool seeded = false)
+                                            unsigned &status, bool seeded = false, const Dir<T> *dir = nullptr)
 {
     T cphi, sphi;
     if (k > 0) {
         Jac<T> J;
-        if (!propagate(st, alpha, sf, J)) {
+        if (!(dir ? propagate_from(st, alpha, sf, J, *dir) : propagate(st, alpha, sf, J))) {
             status |= reach_bits(st);
             return false;
         }
