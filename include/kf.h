@@ -168,13 +168,19 @@ typedef struct {
 /* Fitted tracks, device outputs.  state [6][n] and cov [21][n] in FP64 storage
  * whatever the compute precision (the mixed path keeps the position and phi in
  * float-float, which FP32 storage would round away); chi2 [n]; ndof [n] =
- * 2 * (hits used) - 5; status [n] KF_ST_* bits.  Any pointer may be NULL. */
+ * 2 * (hits used) - 5; status [n] KF_ST_* bits.  cov_f32 [21][n]: the same
+ * covariance in FP32 storage, beside or instead of cov -- the mixed path
+ * carries the covariance in FP32, so rounding it there loses nothing when the
+ * last update ran in the FP32 layer loop, and it halves the covariance's bytes
+ * (84 instead of 168 per track; the all-FP64 path rounds its covariance).  Any
+ * pointer may be NULL. */
 typedef struct {
     double *state;
     double *cov;
     double *chi2;
     int32_t *ndof;
     uint32_t *status;
+    float *cov_f32;
 } kf_tracks_out;
 
 /* ---------------------------------------------------------------- context */

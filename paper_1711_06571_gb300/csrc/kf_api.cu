@@ -362,6 +362,7 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     NEED_DEV(hits->z, "hits.z");
     OPT_DEV(out->state, "out.state");
     OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->cov_f32, "out.cov_f32");
     OPT_DEV(out->chi2, "out.chi2");
     OPT_DEV(out->ndof, "out.ndof");
     OPT_DEV(out->status, "out.status");
@@ -385,13 +386,14 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     a.hz = hits->z;
     a.o_state = out->state;
     a.o_cov = out->cov;
+    a.o_cov32 = out->cov_f32;
     a.o_chi2 = out->chi2;
     a.o_ndof = out->ndof;
     a.o_status = out->status;
     a.p0 = p0;
     a.p0_scale = p0_scale;
     const bool fp64 = P.precision == KF_PREC_FP64;
-    // processing order (both schedules): tracks bucketed by hit count and seed 1/pT
+    // processing order (both schedules): tracks bucketed by hit count, seed phase and seed 1/pT
     const size_t nhist = order_scratch_ints();
     const size_t order_bytes = (((nhist + 64) * sizeof(int32_t) + (size_t)n * sizeof(int32_t)) + 255) & ~(size_t)255;
     const size_t need = order_bytes + (fp64 ? 0 : fit_carry_bytes(n)) + 256;
@@ -401,6 +403,7 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     int32_t *queue = hist + nhist;
     int32_t *order = queue + 64;
     a.order = order;
+    const int nseed = std::max(3, P.n_fp64_updates);  // hits whose surfaces set the order's disk bit
     // the mixed fit hands each track from its phase-1 kernel to its phase-2 kernel here
     if (!fp64 && !p0) fit_carve_carry(a.carry, static_cast<char *>(wsp) + order_bytes, n);
     if (P.schedule == KF_SCHED_GRID && !force) {
@@ -409,7 +412,7 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
             a.timing_events = ctx->tev[ctx->tcalls % kf_ctx::TRING].data();
             ++ctx->tcalls;
         }
-        cudaError_t e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hist, order, st);
+        cudaError_t e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hits->layer, &G, nseed, hist, order, st);
         if (e == cudaSuccess) e = launch_fit(G, a, fp64, 128, st);
         return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "fit kernel");
     }
@@ -427,7 +430,7 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     a.chunk = tu.chunk;
     if (force) {
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
-        if (e == cudaSuccess) e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hist, order, st);
+        if (e == cudaSuccess) e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hits->layer, &G, nseed, hist, order, st);
         if (e == cudaSuccess) e = launch_fit_persistent(G, a, fp64, tu.block, tu.grid, st);
         return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "persistent fit");
     }
@@ -447,7 +450,7 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
         cudaError_t e1 = cudaMemsetAsync(queue, 0, sizeof(int32_t), cs);
-        if (e1 == cudaSuccess) e1 = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hist, order, cs);
+        if (e1 == cudaSuccess) e1 = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hits->layer, &G, nseed, hist, order, cs);
         if (e1 == cudaSuccess) e1 = launch_fit_persistent(G, a, fp64, tu.block, tu.grid, cs);
         e = cudaStreamEndCapture(cs, &graph);
         if (e1 != cudaSuccess || e != cudaSuccess) {
@@ -498,6 +501,7 @@ int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     if (!(cov_scale > 0)) return fail(ctx, KF_EINVAL, "cov_scale must be > 0");
     OPT_DEV(out->state, "out.state");
     OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->cov_f32, "out.cov_f32");
     OPT_DEV(out->chi2, "out.chi2");
     OPT_DEV(out->ndof, "out.ndof");
     OPT_DEV(out->status, "out.status");
@@ -540,7 +544,7 @@ int kf_refit_inward(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     const kf_track_hits H{roff, rl, rx, ry, rz};
     rc = fit_impl(ctx, geom, &P, n, &S, &H, out, stream, nullptr, rcov, cov_scale);
     if (rc == KF_OK) {
-        e = launch_unreverse(n, out->state, out->cov, st);
+        e = launch_unreverse(n, out->state, out->cov, out->cov_f32, st);
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "turning the results back");
     }
     cudaFreeAsync(buf, st);
@@ -573,7 +577,7 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
     if (!is_host_ptr(hits->offsets) || !is_host_ptr(hits->layer) || !is_host_ptr(hits->x) ||
         !is_host_ptr(hits->y) || !is_host_ptr(hits->z))
         return fail(ctx, KF_EINVAL, "kf_fit_host: hits must be host memory");
-    const void *outs[5] = {out->state, out->cov, out->chi2, out->ndof, out->status};
+    const void *outs[6] = {out->state, out->cov, out->chi2, out->ndof, out->status, out->cov_f32};
     for (const void *o : outs)
         if (o && !is_host_ptr(o)) return fail(ctx, KF_EINVAL, "kf_fit_host: outputs must be host memory");
     if (n_chunks < 0 || n_chunks > 64) return fail(ctx, KF_EINVAL, "n_chunks must be 0..64");
@@ -603,7 +607,8 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
            o_z = o_y + al(nh * 4), o_seed = o_z + al(nh * 4), o_q = o_seed + al((size_t)6 * n * 4),
            o_st = o_q + al((size_t)n), o_cov = o_st + al((size_t)6 * n * 8), o_chi = o_cov + al((size_t)21 * n * 8),
            o_nd = o_chi + al((size_t)n * 8), o_sts = o_nd + al((size_t)n * 4), o_ord = o_sts + al((size_t)n * 4),
-           o_carry = o_ord + 3 * al((nhist + (size_t)n) * 4), total = o_carry + 3 * carry_b;
+           o_carry = o_ord + 3 * al((nhist + (size_t)n) * 4), o_c32 = o_carry + 3 * carry_b,
+           total = o_c32 + (out->cov_f32 ? al((size_t)21 * n * 4) : 0);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         for (int i = 0; i < 3; ++i)
@@ -636,6 +641,7 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
     int8_t *d_q = reinterpret_cast<int8_t *>(base + o_q);
     double *d_st = reinterpret_cast<double *>(base + o_st);
     double *d_cov = reinterpret_cast<double *>(base + o_cov);
+    float *d_c32 = reinterpret_cast<float *>(base + o_c32);
     double *d_chi = reinterpret_cast<double *>(base + o_chi);
     int32_t *d_nd = reinterpret_cast<int32_t *>(base + o_nd);
     uint32_t *d_sts = reinterpret_cast<uint32_t *>(base + o_sts);
@@ -657,7 +663,8 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             if (e == cudaSuccess) e = cudaMemcpyAsync(d_z + h0, hits->z + h0, (size_t)(h1 - h0) * 4, cudaMemcpyHostToDevice, st);
         }
         if (e == cudaSuccess) e = launch_seeds(G, cnt, n, t0, d_off, d_x, d_y, d_z, d_seed, d_q, st);
-        if (e == cudaSuccess) e = launch_order(cnt, d_off + t0, d_seed + 3 * (size_t)n + t0, hist, order, st);
+        if (e == cudaSuccess) e = launch_order(cnt, d_off + t0, d_seed + 3 * (size_t)n + t0, d_lay, &G, std::max(3, P.n_fp64_updates),
+                                               hist, order, st);
         if (e == cudaSuccess) {
             FitArgs a;
             memset(&a, 0, sizeof a);
@@ -678,6 +685,7 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             a.hz = d_z;
             a.o_state = d_st;
             a.o_cov = out->cov ? d_cov : nullptr;
+            a.o_cov32 = out->cov_f32 ? d_c32 : nullptr;
             a.o_chi2 = d_chi;
             a.o_ndof = d_nd;
             a.o_status = d_sts;
@@ -692,6 +700,9 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
                                   cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && out->cov)
             e = cudaMemcpy2DAsync(out->cov + t0, (size_t)n * 8, d_cov + t0, (size_t)n * 8, (size_t)cnt * 8, 21,
+                                  cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->cov_f32)
+            e = cudaMemcpy2DAsync(out->cov_f32 + t0, (size_t)n * 4, d_c32 + t0, (size_t)n * 4, (size_t)cnt * 4, 21,
                                   cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && out->chi2)
             e = cudaMemcpyAsync(out->chi2 + t0, d_chi + t0, (size_t)cnt * 8, cudaMemcpyDeviceToHost, st);
@@ -953,6 +964,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     NEED_DEV(hit_idx_out, "hit_idx_out");
     OPT_DEV(out->state, "out.state");
     OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->cov_f32, "out.cov_f32");
     OPT_DEV(out->chi2, "out.chi2");
     OPT_DEV(out->ndof, "out.ndof");
     OPT_DEV(out->status, "out.status");
@@ -968,7 +980,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
         return rc;
     int32_t *hist = reinterpret_cast<int32_t *>(rest);
     int32_t *order = hist + nhist;
-    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, hist, order, st);
+    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, nullptr, 0, hist, order, st);
     if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
     BuildArgs a;
     memset(&a, 0, sizeof a);
@@ -993,6 +1005,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     a.order = order;
     a.o_state = out->state;
     a.o_cov = out->cov;
+    a.o_cov32 = out->cov_f32;
     a.o_chi2 = out->chi2;
     a.o_ndof = out->ndof;
     a.o_status = out->status;
@@ -1033,6 +1046,7 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
     NEED_DEV(hit_idx_out, "hit_idx_out");
     OPT_DEV(out->state, "out.state");
     OPT_DEV(out->cov, "out.cov");
+    OPT_DEV(out->cov_f32, "out.cov_f32");
     OPT_DEV(out->chi2, "out.chi2");
     OPT_DEV(out->ndof, "out.ndof");
     OPT_DEV(out->status, "out.status");
@@ -1047,7 +1061,7 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
         return rc;
     int32_t *hist = reinterpret_cast<int32_t *>(rest);
     int32_t *order = hist + nhist;
-    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, hist, order, st);
+    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, nullptr, 0, hist, order, st);
     if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
     CkfArgs c;
     memset(&c, 0, sizeof c);
@@ -1072,6 +1086,7 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
     a.order = order;
     a.o_state = out->state;
     a.o_cov = out->cov;
+    a.o_cov32 = out->cov_f32;
     a.o_chi2 = out->chi2;
     a.o_ndof = out->ndof;
     a.o_status = out->status;

@@ -889,6 +889,8 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
         for (int i = 0; i < 6; ++i) a.o_state[(size_t)i * n + t] = sv[i];
     if (a.o_cov)
         for (int i = 0; i < 21; ++i) a.o_cov[(size_t)i * n + t] = (double)pc[i];
+    if (a.o_cov32)
+        for (int i = 0; i < 21; ++i) a.o_cov32[(size_t)i * n + t] = (float)pc[i];
     if (a.o_chi2) a.o_chi2[t] = chi2;
     if (a.o_ndof) a.o_ndof[t] = 2 * used - 5;
     if (a.o_status) a.o_status[t] = status;
@@ -1250,6 +1252,8 @@ __global__ void __launch_bounds__(128, 4) ckf_kernel(const Geom g, const CkfArgs
         for (int k = 0; k < 6; ++k) a.o_state[(size_t)k * n + t] = sv[k];
     if (a.o_cov)
         for (int k = 0; k < 21; ++k) a.o_cov[(size_t)k * n + t] = (double)pc[k];
+    if (a.o_cov32)
+        for (int k = 0; k < 21; ++k) a.o_cov32[(size_t)k * n + t] = (float)pc[k];
     if (a.o_chi2) a.o_chi2[t] = chi2;
     if (a.o_ndof) a.o_ndof[t] = 2 * nu - 5;
     if (a.o_status) a.o_status[t] = status;

@@ -204,10 +204,23 @@ __device__ __forceinline__ bool df_seed_update(Track<float, ff> &st, df p[21], f
 // strict upper triangle of U (i < j), column-major: column j holds rows 0..j-1
 __host__ __device__ constexpr int uk(int i, int j) { return j * (j - 1) / 2 + i; }
 
-struct UD {
-    df u[15];
-    df d[6];
+// The U-D update below is written once for double-float (D = df: the seed
+// phase, the near-tangent steps) and plain float (D = float); these are its
+// scalar operations for both.
+__device__ __forceinline__ df ud_fma(df a, df b, df c) { return df_fma(a, b, c); }
+__device__ __forceinline__ df ud_fma(df a, float b, df c) { return df_fma(a, b, c); }
+__device__ __forceinline__ float ud_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ df ud_rcp(df a) { return df_rcp(a); }
+__device__ __forceinline__ float ud_rcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ float ud_lead(df a) { return a.hi; }
+__device__ __forceinline__ float ud_lead(float a) { return a; }
+
+template <class D>
+struct UDT {
+    D u[15];
+    D d[6];
 };
+using UD = UDT<df>;
 
 // the position frame: barrel, (cn, sn) the radial unit vector at the predicted point
 struct PosFrame {
@@ -232,27 +245,28 @@ __device__ __forceinline__ PosFrame pos_frame(const Track<float, ff> &st, const 
 __device__ __forceinline__ int normal_index(const PosFrame &f) { return f.barrel ? 3 : 5; }
 
 // native packed P -> A, U-D order in the position frame, the normal's row zero
-__device__ __forceinline__ void ud_arrange(const df p[21], const PosFrame &fr, df a[21])
+template <class D>
+__device__ __forceinline__ void ud_arrange(const D p[21], const PosFrame &fr, D a[21])
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) a[pk(i, j)] = p[pk(i + 3, j + 3)];
-    const df zero = df(0.f);
+    const D zero = D(0.f);
     if (fr.barrel) {
         const float c = fr.cn, s = fr.sn;  // t = -s x + c y
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             a[pk(3, j)] = zero;
-            a[pk(4, j)] = df_fma(p[pk(1, j + 3)], c, p[pk(0, j + 3)] * (-s));
+            a[pk(4, j)] = ud_fma(p[pk(1, j + 3)], c, p[pk(0, j + 3)] * (-s));
             a[pk(5, j)] = p[pk(2, j + 3)];
         }
         a[pk(3, 3)] = zero;
         a[pk(4, 3)] = zero;
         a[pk(5, 3)] = zero;
         // P_tt = s^2 Pxx - 2 s c Pxy + c^2 Pyy
-        a[pk(4, 4)] = df_fma(p[pk(1, 1)] * c, c, df_fma(p[pk(1, 0)] * mul_rn(-2.f, s), c, p[pk(0, 0)] * s * s));
-        a[pk(5, 4)] = df_fma(p[pk(2, 1)], c, p[pk(2, 0)] * (-s));
+        a[pk(4, 4)] = ud_fma(p[pk(1, 1)] * c, c, ud_fma(p[pk(1, 0)] * mul_rn(-2.f, s), c, p[pk(0, 0)] * s * s));
+        a[pk(5, 4)] = ud_fma(p[pk(2, 1)], c, p[pk(2, 0)] * (-s));
         a[pk(5, 5)] = p[pk(2, 2)];
     } else {
 #pragma unroll
@@ -271,7 +285,8 @@ __device__ __forceinline__ void ud_arrange(const df p[21], const PosFrame &fr, d
 }
 
 // A (U-D order, frame; the normal's row zero) -> native packed P
-__device__ __forceinline__ void ud_unarrange(const df a[21], const PosFrame &fr, df p[21])
+template <class D>
+__device__ __forceinline__ void ud_unarrange(const D a[21], const PosFrame &fr, D p[21])
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -285,7 +300,7 @@ __device__ __forceinline__ void ud_unarrange(const df a[21], const PosFrame &fr,
             p[pk(1, j + 3)] = a[pk(4, j)] * c;
             p[pk(2, j + 3)] = a[pk(5, j)];
         }
-        const df tt = a[pk(4, 4)];
+        const D tt = a[pk(4, 4)];
         p[pk(0, 0)] = tt * s * s;
         p[pk(1, 0)] = -(tt * s * c);
         p[pk(1, 1)] = tt * c * c;
@@ -297,49 +312,50 @@ __device__ __forceinline__ void ud_unarrange(const df a[21], const PosFrame &fr,
         for (int j = 0; j < 3; ++j) {
             p[pk(0, j + 3)] = a[pk(3, j)];
             p[pk(1, j + 3)] = a[pk(4, j)];
-            p[pk(2, j + 3)] = df(0.f);
+            p[pk(2, j + 3)] = D(0.f);
         }
         p[pk(0, 0)] = a[pk(3, 3)];
         p[pk(1, 0)] = a[pk(4, 3)];
         p[pk(1, 1)] = a[pk(4, 4)];
-        p[pk(2, 0)] = df(0.f);
-        p[pk(2, 1)] = df(0.f);
-        p[pk(2, 2)] = df(0.f);
+        p[pk(2, 0)] = D(0.f);
+        p[pk(2, 1)] = D(0.f);
+        p[pk(2, 2)] = D(0.f);
     }
 }
 
 // A = U D U^T (A in U-D order, overwritten), factored from the last index down;
 // ZERO is the normal's index: pivot and column zero.  A pivot that rounding has
 // left at or below zero is taken as zero with its column.
-template <int ZERO>
-__device__ __forceinline__ void ud_factor(df a[21], UD &f)
+template <int ZERO, class D>
+__device__ __forceinline__ void ud_factor(D a[21], UDT<D> &f)
 {
 #pragma unroll
     for (int j = 5; j >= 0; --j) {
-        const df dj = a[pk(j, j)];
-        if (j != ZERO && dj.hi > 0.f) {
+        const D dj = a[pk(j, j)];
+        if (j != ZERO && ud_lead(dj) > 0.f) {
             f.d[j] = dj;
-            const df inv = df_rcp(dj);
+            const D inv = ud_rcp(dj);
 #pragma unroll
             for (int i = 0; i < j; ++i) f.u[uk(i, j)] = a[pk(j, i)] * inv;
             // downdate of the leading block: a_ik -= a_ij u_kj (i >= k, both < j)
 #pragma unroll
             for (int i = 0; i < j; ++i)
 #pragma unroll
-                for (int k = 0; k <= i; ++k) a[pk(i, k)] = df_fma(-a[pk(j, i)], f.u[uk(k, j)], a[pk(i, k)]);
+                for (int k = 0; k <= i; ++k) a[pk(i, k)] = ud_fma(-a[pk(j, i)], f.u[uk(k, j)], a[pk(i, k)]);
         } else {
-            f.d[j] = df(0.f);
+            f.d[j] = D(0.f);
 #pragma unroll
-            for (int i = 0; i < j; ++i) f.u[uk(i, j)] = df(0.f);
+            for (int i = 0; i < j; ++i) f.u[uk(i, j)] = D(0.f);
         }
     }
 }
 
 // A (U-D order) = U D U^T
-__device__ __forceinline__ void ud_compose(const UD &f, df a[21])
+template <class D>
+__device__ __forceinline__ void ud_compose(const UDT<D> &f, D a[21])
 {
     // W = U D (strict upper part; the diagonal of W is d)
-    df w[15];
+    D w[15];
 #pragma unroll
     for (int j = 1; j < 6; ++j)
 #pragma unroll
@@ -349,9 +365,9 @@ __device__ __forceinline__ void ud_compose(const UD &f, df a[21])
 #pragma unroll
         for (int j = i; j < 6; ++j) {
             // A_ij = sum_{k >= j} W_ik U_jk, U_jj = 1
-            df v = i == j ? f.d[j] : w[uk(i, j)];
+            D v = i == j ? f.d[j] : w[uk(i, j)];
 #pragma unroll
-            for (int k = j + 1; k < 6; ++k) v = df_fma(w[uk(i, k)], f.u[uk(j, k)], v);
+            for (int k = j + 1; k < 6; ++k) v = ud_fma(w[uk(i, k)], f.u[uk(j, k)], v);
             a[pk(j, i)] = v;
         }
 }
@@ -361,37 +377,37 @@ __device__ __forceinline__ void ud_compose(const UD &f, df a[21])
 // and innovation nu = m - h . x.  Updates U and D in place, returns the gain K
 // (U-D order) through k and 1 / alpha, alpha = h P h^T + r the innovation
 // variance.
-template <int FIRST>
-__device__ __forceinline__ void ud_scalar(UD &f, float h3, float h4, float h5, float r, df k[6], df &ialpha)
+template <int FIRST, class D>
+__device__ __forceinline__ void ud_scalar(UDT<D> &f, float h3, float h4, float h5, float r, D k[6], D &ialpha)
 {
-    df fv[6], v[6];
-    if (FIRST <= 3) fv[3] = df(h3);
-    if (FIRST <= 4) fv[4] = FIRST <= 3 ? df_fma(f.u[uk(3, 4)], h3, df(h4)) : df(h4);
+    D fv[6], v[6];
+    if (FIRST <= 3) fv[3] = D(h3);
+    if (FIRST <= 4) fv[4] = FIRST <= 3 ? ud_fma(f.u[uk(3, 4)], h3, D(h4)) : D(h4);
     {
-        df t = df(h5);
-        if (FIRST <= 4) t = df_fma(f.u[uk(4, 5)], h4, t);
-        if (FIRST <= 3) t = df_fma(f.u[uk(3, 5)], h3, t);
+        D t = D(h5);
+        if (FIRST <= 4) t = ud_fma(f.u[uk(4, 5)], h4, t);
+        if (FIRST <= 3) t = ud_fma(f.u[uk(3, 5)], h3, t);
         fv[5] = t;
     }
 #pragma unroll
     for (int j = FIRST; j < 6; ++j) v[j] = f.d[j] * fv[j];
-    df b[6];
+    D b[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) b[i] = df(0.f);
-    df al = df(r), ibeta = df_rcp(al);
+    for (int i = 0; i < 6; ++i) b[i] = D(0.f);
+    D al = D(r), ibeta = ud_rcp(al);
 #pragma unroll
     for (int j = FIRST; j < 6; ++j) {
-        const df beta = al;
-        al = df_fma(v[j], fv[j], beta);
-        const df ia = df_rcp(al);
-        const df lam = -(fv[j] * ibeta);
+        const D beta = al;
+        al = ud_fma(v[j], fv[j], beta);
+        const D ia = ud_rcp(al);
+        const D lam = -(fv[j] * ibeta);
         f.d[j] = f.d[j] * beta * ia;
 #pragma unroll
         for (int i = 0; i < j; ++i) {
-            const df uo = f.u[uk(i, j)];
+            const D uo = f.u[uk(i, j)];
             if (j > FIRST) {
-                f.u[uk(i, j)] = df_fma(b[i], lam, uo);
-                b[i] = df_fma(uo, v[j], b[i]);
+                f.u[uk(i, j)] = ud_fma(b[i], lam, uo);
+                b[i] = ud_fma(uo, v[j], b[i]);
             } else {
                 b[i] = uo * v[j];  // b is still zero: this column of U stays
             }
@@ -407,24 +423,25 @@ __device__ __forceinline__ void ud_scalar(UD &f, float h3, float h4, float h5, f
 // Apply one scalar measurement: gain, chi2 term, state increment dx (U-D
 // order) and the innovations of the measurements still to come (direction
 // components in the frame: a, b).
-template <int FIRST>
-__device__ __forceinline__ void ud_measure(UD &f, float h3, float h4, float h5, float r, df nu, df dx[6], df &chi2,
-                                           df &nu_a, float a3, float a4, float a5, df &nu_b, float b3, float b4,
+template <int FIRST, class D, class C>
+__device__ __forceinline__ void ud_measure(UDT<D> &f, float h3, float h4, float h5, float r, D nu, D dx[6], C &chi2,
+                                           D &nu_a, float a3, float a4, float a5, D &nu_b, float b3, float b4,
                                            float b5)
 {
-    df k[6], ial;
+    D k[6], ial;
     ud_scalar<FIRST>(f, h3, h4, h5, r, k, ial);
     chi2 += nu * nu * ial;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dx[i] = df_fma(k[i], nu, dx[i]);
+    for (int i = 0; i < 6; ++i) dx[i] = ud_fma(k[i], nu, dx[i]);
     // the state moved by k nu: the later innovations m - h' . x move by -h' . k nu
-    const df kn3 = k[3] * nu, kn4 = k[4] * nu, kn5 = k[5] * nu;
+    const D kn3 = k[3] * nu, kn4 = k[4] * nu, kn5 = k[5] * nu;
     nu_a = nu_a - (kn3 * a3 + kn4 * a4 + kn5 * a5);
     nu_b = nu_b - (kn3 * b3 + kn4 * b4 + kn5 * b5);
 }
 
 // state increment dx (U-D order, frame) onto the track
-__device__ __forceinline__ void ud_apply_state(Track<float, ff> &st, const df dx[6], const PosFrame &fr)
+template <class D>
+__device__ __forceinline__ void ud_apply_state(Track<float, ff> &st, const D dx[6], const PosFrame &fr)
 {
     add_inc(st.ip, dx[0]);
     add_inc(st.phi, dx[1]);
@@ -447,21 +464,22 @@ __device__ __forceinline__ void ud_apply_state(Track<float, ff> &st, const df dx
 // are taken), which gives the same posterior and chi2 = r^T S^-1 r as the joint
 // update.  The measurement along the surface normal meets a zero prior
 // variance: it adds its chi2 term and moves nothing.
-__device__ __forceinline__ bool ud_update3(Track<float, ff> &st, df p[21], float hx, float hy, float hz,
-                                           const Surf &sf, df &chi2)
+template <class D, class C>
+__device__ __forceinline__ bool ud_update3(Track<float, ff> &st, D p[21], float hx, float hy, float hz,
+                                           const Surf &sf, C &chi2)
 {
     const float r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);
     const float va = sf.var_rad, vb = sf.var_rphi, vz = sf.var_zz;
     if (!(va > 0.f) || !(vb > 0.f) || !(vz > 0.f)) return false;
     const PosFrame fr = pos_frame(st, sf);
-    df a[21];
+    D a[21];
     ud_arrange(p, fr, a);
-    UD f;
+    UDT<D> f;
     if (fr.barrel) ud_factor<3>(a, f);
     else ud_factor<5>(a, f);
-    df dx[6];
+    D dx[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dx[i] = df(0.f);
+    for (int i = 0; i < 6; ++i) dx[i] = D(0.f);
     const bool iso = va == vb;
     float c1 = 1.f, s1 = 0.f;  // e1 = (c1, s1) with variance va, e2 = (-s1, c1) with vb
     if (iso && fr.barrel) {
@@ -472,8 +490,8 @@ __device__ __forceinline__ bool ud_update3(Track<float, ff> &st, df p[21], float
         c1 = __fdiv_rn(hx, rh);
         s1 = __fdiv_rn(hy, rh);
     }
-    df n1 = df_fma(df(r1), s1, df(r0) * c1), n2 = df_fma(df(r1), c1, df(r0) * (-s1)), nz = df(r2);
-    df dummy = df(0.f);
+    D n1 = ud_fma(D(r1), s1, D(r0) * c1), n2 = ud_fma(D(r1), c1, D(r0) * (-s1)), nz = D(r2);
+    D dummy = D(0.f);
     if (fr.barrel) {
         // frame components of e1, e2; with iso they are n and t themselves
         float e1n = 1.f, e1t = 0.f, e2n = 0.f, e2t = 1.f;
@@ -486,13 +504,13 @@ __device__ __forceinline__ bool ud_update3(Track<float, ff> &st, df p[21], float
         ud_measure<5>(f, 0.f, 0.f, 1.f, vz, nz, dx, chi2, n2, e2n, e2t, 0.f, n1, e1n, e1t, 0.f);
         if (iso) {
             ud_measure<4>(f, 0.f, 1.f, 0.f, vb, n2, dx, chi2, n1, 1.f, 0.f, 0.f, dummy, 0.f, 0.f, 0.f);
-            chi2 += n1 * n1 * df_rcp(df(va));  // the normal: zero prior variance
+            chi2 += n1 * n1 * ud_rcp(D(va));  // the normal: zero prior variance
         } else {
             ud_measure<3>(f, e2n, e2t, 0.f, vb, n2, dx, chi2, n1, e1n, e1t, 0.f, dummy, 0.f, 0.f, 0.f);
             ud_measure<3>(f, e1n, e1t, 0.f, va, n1, dx, chi2, dummy, 0.f, 0.f, 0.f, dummy, 0.f, 0.f, 0.f);
         }
     } else {
-        chi2 += nz * nz * df_rcp(df(vz));  // the disk normal z: zero prior variance
+        chi2 += nz * nz * ud_rcp(D(vz));  // the disk normal z: zero prior variance
         if (s1 == 0.f) {  // e2 = +-y-hat
             ud_measure<4>(f, 0.f, c1, 0.f, vb, n2, dx, chi2, n1, c1, s1, 0.f, dummy, 0.f, 0.f, 0.f);
         } else {
@@ -510,8 +528,9 @@ __device__ __forceinline__ bool ud_update3(Track<float, ff> &st, df p[21], float
 // plane, sf the cylinder through the hit): r-phi along t_h = (-sin a, cos a)
 // with sig_rphi^2 and z with sig_z^2, a the hit azimuth; two scalar
 // measurements.
-__device__ __forceinline__ bool ud_update2(Track<float, ff> &st, df p[21], float hx, float hy, float hz,
-                                           const Surf &sf, df &chi2)
+template <class D, class C>
+__device__ __forceinline__ bool ud_update2(Track<float, ff> &st, D p[21], float hx, float hy, float hz,
+                                           const Surf &sf, C &chi2)
 {
     const float r0 = resid(hx, st.x), r1 = resid(hy, st.y), r2 = resid(hz, st.z);
     const float vt = sf.var_rphi, vz = sf.var_zz;
@@ -519,16 +538,16 @@ __device__ __forceinline__ bool ud_update2(Track<float, ff> &st, df p[21], float
     const float rh = hypot_rn(hx, hy);
     const float ca = __fdiv_rn(hx, rh), sa = __fdiv_rn(hy, rh);
     const PosFrame fr = pos_frame(st, sf);
-    df a[21];
+    D a[21];
     ud_arrange(p, fr, a);
-    UD f;
+    UDT<D> f;
     ud_factor<3>(a, f);
-    df dx[6];
+    D dx[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dx[i] = df(0.f);
+    for (int i = 0; i < 6; ++i) dx[i] = D(0.f);
     // t_h in the frame (n, t)
     const float hn = dot2_rn(fr.sn, ca, -fr.cn, sa), ht = dot2_rn(fr.cn, ca, fr.sn, sa);
-    df nt = df_fma(df(r1), ca, df(r0) * (-sa)), nz = df(r2), dummy = df(0.f);
+    D nt = ud_fma(D(r1), ca, D(r0) * (-sa)), nz = D(r2), dummy = D(0.f);
     ud_measure<5>(f, 0.f, 0.f, 1.f, vz, nz, dx, chi2, nt, hn, ht, 0.f, dummy, 0.f, 0.f, 0.f);
     ud_measure<3>(f, hn, ht, 0.f, vt, nt, dx, chi2, dummy, 0.f, 0.f, 0.f, dummy, 0.f, 0.f, 0.f);
     ud_compose(f, a);
@@ -601,6 +620,33 @@ __device__ __forceinline__ bool df_step_from_f32(Track<float, ff> &st, float pf[
     chi2 += df_to_d(c2);
 #pragma unroll
     for (int i = 0; i < 21; ++i) pf[i] = p[i].hi;
+    return true;
+}
+
+// A step of the FP32 layer loop at a near-tangent barrel crossing that is not
+// steep: FP32 propagation, transport and noise, then the update in U-D form in
+// FP32 (the standard-form FP32 update loses the covariance there; the U-D form,
+// with the normal's row zeroed, keeps it).  TWO_D: the 2-D update on sf.
+// Returns false when the track ends here (status set).
+template <bool TWO_D>
+__device__ __forceinline__ bool ud32_step(Track<float, ff> &st, float pf[21], float alpha, float mass2, int ms_on,
+                                          const Surf &sf, float hx, float hy, float hz, double &chi2,
+                                          unsigned &status)
+{
+    Jac<float> J;
+    if (!propagate(st, alpha, sf, J)) {
+        status |= reach_bits(st);
+        return false;
+    }
+    transport<float>(pf, J);
+    if (ms_on) status |= ms_noise<float, float>(st, sf, J.cphi1, J.sphi1, mass2, pf);
+    bool ok;
+    if constexpr (TWO_D) ok = ud_update2(st, pf, hx, hy, hz, sf, chi2);
+    else ok = ud_update3(st, pf, hx, hy, hz, sf, chi2);
+    if (!ok) {
+        status |= KF_ST_CHOL_FAIL;
+        return false;
+    }
     return true;
 }
 

@@ -141,36 +141,48 @@ __device__ __forceinline__ bool fit_step(Track<T, P> &st, C p[21], int k, T alph
                                          dir);
 }
 
-// Sine of the crossing angle above which a mixed-path step runs in FP64:
-// cos(alpha) < 0.6 (about 2% of steps on the 17-layer barrel: low-pT tracks
-// meeting a layer close to their apex).
+// Crossings that leave the plain FP32 step (a mixed-path step): barrel, the
+// helix meets the cylinder close to its apex, sine of the transverse crossing
+// angle above 0.8 (cos < 0.6: about 2% of the steps on the 17-layer barrel,
+// low-pT tracks); disk, the direction close to the disk plane, incidence cosine
+// |cos(theta)| below 0.5.  There the surface-constrained Jacobian grows like
+// 1 / cos(alpha) and the gain of the standard-form FP32 update, formed from the
+// transported covariance, loses the covariance.
 constexpr float NEAR_TANGENT_SINE = 0.8f;
+constexpr float NEAR_TANGENT_DISK_COS = 0.5f;
+// A near-tangent barrel crossing whose 3-D incidence cosine sin(theta) cos(alpha)
+// is above this takes the FP32 U-D update (FP32 transport); the steeper ones and
+// the disk crossings take the double-float step.
+constexpr float UD32_MIN_COS = 0.2f;
 
-// A crossing where FP32 cannot carry the transport: barrel, the helix meets the
-// cylinder close to its apex; disk, the direction is close to the disk plane
-// (the incidence cosine is cos(theta)).  Both: cos(alpha) < 0.6.
-__device__ __forceinline__ bool grazing_crossing(const Track<float, ff> &st, float alpha, const Surf &sf)
+// the crossing kind of a mixed-path step: 0 plain FP32, 1 FP32 U-D update,
+// 2 double-float step
+__device__ __forceinline__ int crossing_kind(const Track<float, ff> &st, float alpha, const Surf &sf,
+                                             const Dir<float> &d)
 {
-    if (sf.kind == 0) return crossing_sine(st, alpha, sf) > NEAR_TANGENT_SINE;
-    float sth, cth;
-    sincos_pos(st.th, sth, cth);
-    return fabsf(cth) < 0.6f;
+    if (sf.kind == 0) {
+        const float s = crossing_sine(st, alpha, sf, d.sphi, d.cphi);
+        if (!(s > NEAR_TANGENT_SINE)) return 0;
+        const float c = __fmul_rn(d.sth, __fsqrt_rn(fmaxf(0.f, __fmaf_rn(-s, s, 1.f))));
+        return c > UD32_MIN_COS ? 1 : 2;
+    }
+    return fabsf(d.cth) < NEAR_TANGENT_DISK_COS ? 2 : 0;
 }
-// the same from the direction's sines and cosines
-__device__ __forceinline__ bool grazing_crossing(const Track<float, ff> &st, float alpha, const Surf &sf,
-                                                 const Dir<float> &d)
+// the same on the surface the hit is measured on
+template <bool M1>
+__device__ __forceinline__ int crossing_kind(const Track<float, ff> &st, float alpha, const Surf &sf, float hx,
+                                             float hy, const Dir<float> &d)
 {
-    if (sf.kind == 0) return crossing_sine(st, alpha, sf, d.sphi, d.cphi) > NEAR_TANGENT_SINE;
-    return fabsf(d.cth) < 0.6f;
+    if constexpr (M1)
+        if (sf.kind == 0) return crossing_kind(st, alpha, hit_surface(sf, hx, hy), d);
+    return crossing_kind(st, alpha, sf, d);
 }
-// the same test on the surface the hit is measured on
+// whether the crossing leaves the plain FP32 step
 template <bool M1>
 __device__ __forceinline__ bool grazing_crossing(const Track<float, ff> &st, float alpha, const Surf &sf, float hx,
                                                  float hy)
 {
-    if constexpr (M1)
-        if (sf.kind == 0) return grazing_crossing(st, alpha, hit_surface(sf, hx, hy));
-    return grazing_crossing(st, alpha, sf);
+    return crossing_kind<M1>(st, alpha, sf, hx, hy, direction(st)) != 0;
 }
 
 __device__ __forceinline__ ff ff_from_d(double d)
@@ -231,6 +243,20 @@ static __device__ __noinline__ MixedIO df_step_out_of_line(MixedIO m, float alph
     return m;
 }
 
+// A near-tangent barrel crossing that is not steep: FP32 propagation, transport
+// and noise, then the update in FP32 U-D form (out of line)
+template <bool M1>
+static __device__ __noinline__ MixedIO ud32_step_out_of_line(MixedIO m, float alpha, float mass2, int ms_on,
+                                                             const Surf *sf, float hx, float hy, float hz)
+{
+    if (M1 && sf->kind == 0)
+        m.ok = ud32_step<true>(m.st, m.p, alpha, mass2, ms_on, hit_surface(*sf, hx, hy), hx, hy, hz, m.chi2,
+                               m.status);
+    else
+        m.ok = ud32_step<false>(m.st, m.p, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
+    return m;
+}
+
 // A near-tangent crossing inside the FP64 phase (the covariance already FP64):
 // the propagation in FP64 too, out of line.  A track fitted inwards meets its
 // near-tangent crossings first, while the seed covariance is still large.
@@ -266,12 +292,16 @@ static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int
     return m;
 }
 
+// the covariance into the FP64 and/or the FP32 output planes
 template <class C>
-__device__ __forceinline__ void store_cov(double *o_cov, int n, int t, const C p[21])
+__device__ __forceinline__ void store_cov(const FitArgs &a, int n, int t, const C p[21])
 {
-    if (!o_cov) return;
+    if (a.o_cov)
 #pragma unroll
-    for (int i = 0; i < 21; ++i) o_cov[(size_t)i * n + t] = (double)p[i];
+        for (int i = 0; i < 21; ++i) a.o_cov[(size_t)i * n + t] = (double)p[i];
+    if (a.o_cov32)
+#pragma unroll
+        for (int i = 0; i < 21; ++i) a.o_cov32[(size_t)i * n + t] = (float)p[i];
 }
 
 template <bool FP64, bool M1 = false, bool P0 = false>
@@ -484,8 +514,8 @@ __device__ __forceinline__ bool fit_phase1(int t, const FitArgs &a, const Surf *
         ph.k = k;
         return true;
     }
-    if (in_pf) store_cov(a.o_cov, n, t, pf);
-    else store_cov(a.o_cov, n, t, pd);
+    if (in_pf) store_cov(a, n, t, pf);
+    else store_cov(a, n, t, pd);
     write_outputs(a, t, st, chi2, used, status);
     return false;
 }
@@ -531,13 +561,15 @@ __device__ __forceinline__ void fit_phase2(int t, const FitArgs &a, const Surf *
         if constexpr (!FP64) {
             // the direction's sines and cosines, shared by the near-tangent test and the propagation
             const Dir<float> d = direction(st);
-            if constexpr (M1) near_tangent = grazing_crossing<M1>(st, alpha, sf, hx, hy);
-            else near_tangent = grazing_crossing(st, alpha, sf, d);
+            const int kind = crossing_kind<M1>(st, alpha, sf, hx, hy, d);
+            near_tangent = kind != 0;
             if (near_tangent) {
-                // near-tangent crossing: the transport and update in double-float U-D form
+                // near-tangent crossing: the update in U-D form, in FP32 (kind 1) or with
+                // the transport in double-float (kind 2)
                 MixedIO m;
                 mixed_pack(m, st, pf, chi2, status);
-                m = df_step_out_of_line<M1>(m, alpha, mass2, a.ms_on, &sf, hx, hy, hz);
+                if (kind == 1) m = ud32_step_out_of_line<M1>(m, alpha, mass2, a.ms_on, &sf, hx, hy, hz);
+                else m = df_step_out_of_line<M1>(m, alpha, mass2, a.ms_on, &sf, hx, hy, hz);
                 if (!mixed_unpack(m, st, pf, chi2, status)) break;
             } else if (!fit_step<false, T, M1>(st, pf, k, alpha, mass2, a.ms_on, sf, hx, hy, hz, chi2, status,
                                                false, &d)) {
@@ -548,7 +580,7 @@ __device__ __forceinline__ void fit_phase2(int t, const FitArgs &a, const Surf *
         }
         ++used;
     }
-    store_cov(a.o_cov, n, t, pf);
+    store_cov(a, n, t, pf);
     write_outputs(a, t, st, chi2, used, status);
 }
 
@@ -792,7 +824,7 @@ __global__ void reverse_seed_kernel(int n, const double *__restrict__ fwd, const
     rq[t] = (int8_t)(-q[t]);
 }
 
-__global__ void unreverse_kernel(int n, double *__restrict__ st, double *__restrict__ cov)
+__global__ void unreverse_kernel(int n, double *__restrict__ st, double *__restrict__ cov, float *__restrict__ cov32)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -804,6 +836,9 @@ __global__ void unreverse_kernel(int n, double *__restrict__ st, double *__restr
     if (cov)
 #pragma unroll
         for (int j = 0; j < 5; ++j) cov[(size_t)pk(5, j) * n + t] = -cov[(size_t)pk(5, j) * n + t];
+    if (cov32)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) cov32[(size_t)pk(5, j) * n + t] = -cov32[(size_t)pk(5, j) * n + t];
 }
 
 cudaError_t launch_used_counts(int n, const int32_t *off, const int32_t *fwd_ndof, int32_t *cnt, cudaStream_t st)
@@ -824,10 +859,10 @@ cudaError_t launch_reverse(int n, const int32_t *off, const int32_t *roff, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_unreverse(int n, double *state, double *cov, cudaStream_t st)
+cudaError_t launch_unreverse(int n, double *state, double *cov, float *cov32, cudaStream_t st)
 {
-    if (n <= 0 || (!state && !cov)) return cudaSuccess;
-    unreverse_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, state, cov);
+    if (n <= 0 || (!state && !cov && !cov32)) return cudaSuccess;
+    unreverse_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, state, cov, cov32);
     return cudaGetLastError();
 }
 
@@ -922,32 +957,52 @@ int persistent_blocks_per_sm(bool fp64, int block)
 // ------------------------------------------------------------------ processing order
 
 // Counting sort of the tracks into buckets of (hit count, descending) x (seed
-// |1/pT|, 64 bins of 1/32 GeV^-1, clamped, descending): a warp then takes 32
-// tracks that cross nearly the same layers and bend alike, so the layer loop and
-// the near-tangent FP64 steps (low-pT tracks at their apex) diverge little, and
-// the costliest tracks (most hits, then lowest pT: widest build windows, most
-// near-tangent steps) come first, so that the short ones fill the launch's tail.
-// The order inside a bucket is that of the atomics, which does not change any
-// track's result.
-constexpr int ORDER_BUCKETS = 65 * 64;
+// phase with a disk hit first) x (seed |1/pT|, 64 bins of 1/32 GeV^-1, clamped,
+// descending): a warp then takes tracks that cross nearly the same layers, bend
+// alike and run the same seed phase, so the layer loop, the seed phase (FP64 with
+// a disk hit, double-float without) and the near-tangent steps (low-pT tracks at
+// their apex) diverge little, and the costliest tracks (most hits, then the FP64
+// seed phase, then lowest pT: widest build windows, most near-tangent steps) come
+// first, so that the short ones fill the launch's tail.  The order inside a bucket
+// is that of the atomics, which does not change any track's result.
+//
+// Sorting groups of consecutive tracks instead (so that the per-track SoA outputs
+// of a group share 32-byte sectors) was measured: groups of 4 made the fit 1.9x
+// slower on the barrel and 4.7x on the barrel+disk batch, since a group mixes
+// tracks of different cost again.
+constexpr int ORDER_BUCKETS = 65 * 2 * 64;
 
-__device__ __forceinline__ int order_key(const int32_t *__restrict__ off, const float *__restrict__ ip, int t)
+struct OrderIn {
+    int n;
+    int nseed;                  // seed-phase hits whose surfaces decide the disk bit
+    const int32_t *off;         // CSR offsets, or null (key by 1/pT alone)
+    const float *ip;            // seed 1/pT [n]
+    const uint8_t *layer;       // surface of each hit, or null (no disk bit)
+    unsigned long long disk;    // bit s set: surface s is a disk
+};
+
+__device__ __forceinline__ int order_key(const OrderIn &in, int t)
 {
-    const int nh = off ? min(off[t + 1] - off[t], 64) : 0;
-    const int b = min((int)(fabsf(ip[t]) * 32.f), 63);
-    return (64 - nh) * 64 + (63 - b);
+    int nh = 0, disk = 0;
+    if (in.off) {
+        const int o = in.off[t];
+        nh = min(in.off[t + 1] - o, 64);
+        if (in.layer)
+            for (int j = 0; j < min(nh, in.nseed); ++j) disk |= (int)((in.disk >> in.layer[o + j]) & 1ull);
+    }
+    const int b = min((int)(fabsf(in.ip[t]) * 32.f), 63);
+    return ((64 - nh) * 2 + (1 - disk)) * 64 + (63 - b);
 }
 // Histogram and scatter count in shared memory per block and touch global
 // memory once per non-empty bucket and block: the keys of neighbouring tracks
 // repeat a lot, and per-track global atomics on them serialise.
-__global__ void __launch_bounds__(1024) order_hist_kernel(int n, const int32_t *__restrict__ off,
-                                                          const float *__restrict__ ip, int32_t *hist)
+__global__ void __launch_bounds__(1024) order_hist_kernel(OrderIn in, int32_t *hist)
 {
     __shared__ int32_t cnt[ORDER_BUCKETS];
     for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) atomicAdd(&cnt[order_key(off, ip, t)], 1);
+    if (t < in.n) atomicAdd(&cnt[order_key(in, t)], 1);
     __syncthreads();
     for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x)
         if (cnt[b]) atomicAdd(&hist[b], cnt[b]);
@@ -992,37 +1047,45 @@ __global__ void __launch_bounds__(1024) order_scan_kernel(int32_t *hist)
         acc += loc[j];
     }
 }
-__global__ void __launch_bounds__(1024) order_scatter_kernel(int n, const int32_t *__restrict__ off,
-                                                             const float *__restrict__ ip, int32_t *cursor,
-                                                             int32_t *order)
+__global__ void __launch_bounds__(1024) order_scatter_kernel(OrderIn in, int32_t *cursor, int32_t *order)
 {
     __shared__ int32_t cnt[ORDER_BUCKETS];
     for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int key = t < n ? order_key(off, ip, t) : 0;
+    const int key = t < in.n ? order_key(in, t) : 0;
     int local = 0;
-    if (t < n) local = atomicAdd(&cnt[key], 1);
+    if (t < in.n) local = atomicAdd(&cnt[key], 1);
     __syncthreads();
     // reserve this block's range in every bucket it uses
     for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x)
         if (cnt[b]) cnt[b] = atomicAdd(&cursor[b], cnt[b]);
     __syncthreads();
-    if (t < n) order[cnt[key] + local] = t;
+    if (t < in.n) order[cnt[key] + local] = t;
 }
 
 size_t order_scratch_ints() { return ORDER_BUCKETS; }
 
-cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, int32_t *hist, int32_t *order,
-                         cudaStream_t st)
+cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const uint8_t *layer,
+                         const Geom *g, int nseed, int32_t *hist, int32_t *order, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(hist, 0, ORDER_BUCKETS * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
+    OrderIn in;
+    in.n = n;
+    in.nseed = nseed;
+    in.off = off;
+    in.ip = seed_ip;
+    in.layer = off && g ? layer : nullptr;
+    in.disk = 0;
+    if (g)
+        for (int s = 0; s < g->n && s < 64; ++s)
+            if (g->s[s].kind == 1) in.disk |= 1ull << s;
     const int b = 1024, grid = (n + b - 1) / b;
-    order_hist_kernel<<<grid, b, 0, st>>>(n, off, seed_ip, hist);
+    order_hist_kernel<<<grid, b, 0, st>>>(in, hist);
     order_scan_kernel<<<1, 1024, 0, st>>>(hist);
-    order_scatter_kernel<<<grid, b, 0, st>>>(n, off, seed_ip, hist, order);
+    order_scatter_kernel<<<grid, b, 0, st>>>(in, hist, order);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ struct FitArgs {
     const float *hx, *hy, *hz;
     double *o_state;   // [6][n]
     double *o_cov;     // [21][n]
+    float *o_cov32;    // [21][n] FP32 copy of the covariance, or null
     double *o_chi2;
     int32_t *o_ndof;
     uint32_t *o_status;
@@ -66,8 +67,10 @@ cudaError_t launch_fit(const Geom &g, const FitArgs &a, bool fp64, int block, cu
 cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, int block, int grid, cudaStream_t st);
 int persistent_blocks_per_sm(bool fp64, int block);
 size_t order_scratch_ints();
-cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, int32_t *hist, int32_t *order,
-                         cudaStream_t st);
+// processing order: tracks bucketed by (hit count, a disk among the first nseed
+// hits' surfaces -- needs off, layer and g --, seed 1/pT); off null: by 1/pT alone
+cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const uint8_t *layer, const Geom *g,
+                         int nseed, int32_t *hist, int32_t *order, cudaStream_t st);
 
 // outward-inward refit (kf_fit.cu): cnt[t] = hits the forward fit used, then
 // (after an exclusive scan of cnt into roff) those hits reversed into roff's CSR
@@ -78,7 +81,7 @@ cudaError_t launch_reverse(int n, const int32_t *off, const int32_t *roff, const
                            cudaStream_t st);
 // exclusive scan of n counts into off_out[0..n] (kf_build.cu); bsum: n / 1024 + 2 ints
 cudaError_t launch_scan_counts(int n, const int32_t *cnt, int32_t *off_out, int32_t *bsum, cudaStream_t st);
-cudaError_t launch_unreverse(int n, double *state, double *cov, cudaStream_t st);
+cudaError_t launch_unreverse(int n, double *state, double *cov, float *cov32, cudaStream_t st);
 
 // kf_bin.cu
 size_t bin_scratch_bytes(int n_hits);
@@ -116,6 +119,7 @@ struct BuildArgs {
     int32_t *hit_idx;             // [n_layers][n]
     const int32_t *order;         // processing order (by seed 1/pT), or null
     double *o_state, *o_cov, *o_chi2;
+    float *o_cov32;  // [21][n] FP32 copy of the covariance, or null
     int32_t *o_ndof;
     uint32_t *o_status;
     int meas_model;  // as FitArgs::meas_model (per-thread scoring only)

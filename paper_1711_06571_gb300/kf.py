@@ -83,7 +83,7 @@ class kf_track_hits(C.Structure):
 
 class kf_tracks_out(C.Structure):
     _fields_ = [("state", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p), ("ndof", C.c_void_p),
-                ("status", C.c_void_p)]
+                ("status", C.c_void_p), ("cov_f32", C.c_void_p)]
 
 
 class kf_binned_layer(C.Structure):
@@ -279,22 +279,26 @@ def kf_make_seeds(ctx, geom, n, offsets, x, y, z, state_out, q_out, stream=None)
 
 
 def kf_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, out_state=None, out_cov=None,
-           out_chi2=None, out_ndof=None, out_status=None, stream=None):
+           out_chi2=None, out_ndof=None, out_status=None, stream=None,
+           out_cov_f32=None):
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
     p = params if params is not None else fit_params()
     s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
     h = kf_track_hits(_ptr(offsets), _ptr(layer), _ptr(x), _ptr(y), _ptr(z))
-    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status),
+                      _ptr(out_cov_f32))
     _check(ctx, load().kf_fit(ctx, C.byref(g), C.byref(p), int(n), C.byref(s), C.byref(h), C.byref(o),
                               _stream(stream)))
 
 
 def kf_refit_inward(ctx, geom, params, n, offsets, layer, x, y, z, fwd_state, fwd_cov, q, fwd_ndof, cov_scale=100.0,
-                    out_state=None, out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None):
+                    out_state=None, out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None,
+                    out_cov_f32=None):
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
     p = params if params is not None else fit_params()
     h = kf_track_hits(_ptr(offsets), _ptr(layer), _ptr(x), _ptr(y), _ptr(z))
-    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status),
+                      _ptr(out_cov_f32))
     _check(ctx, load().kf_refit_inward(ctx, C.byref(g), C.byref(p), int(n), C.byref(h), _ptr(fwd_state),
                                        _ptr(fwd_cov), _ptr(q), _ptr(fwd_ndof), float(cov_scale), C.byref(o),
                                        _stream(stream)))
@@ -313,11 +317,12 @@ def _hptr(t):
 
 
 def kf_fit_host(ctx, geom, params, n, offsets, layer, x, y, z, out_state=None, out_cov=None, out_chi2=None,
-                out_ndof=None, out_status=None, n_chunks=0):
+                out_ndof=None, out_status=None, n_chunks=0, out_cov_f32=None):
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
     p = params if params is not None else fit_params()
     h = kf_track_hits(_hptr(offsets), _hptr(layer), _hptr(x), _hptr(y), _hptr(z))
-    o = kf_tracks_out(_hptr(out_state), _hptr(out_cov), _hptr(out_chi2), _hptr(out_ndof), _hptr(out_status))
+    o = kf_tracks_out(_hptr(out_state), _hptr(out_cov), _hptr(out_chi2), _hptr(out_ndof), _hptr(out_status),
+                      _hptr(out_cov_f32))
     _check(ctx, load().kf_fit_host(ctx, C.byref(g), C.byref(p), int(n), C.byref(h), C.byref(o), int(n_chunks)))
 
 
@@ -334,12 +339,14 @@ def kf_fit_phase_times(ctx):
 
 
 def kf_autotune_fit(ctx, geom, params, n, seed_state, seed_q, offsets, layer, x, y, z, out_state=None,
-                    out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None) -> str:
+                    out_cov=None, out_chi2=None, out_ndof=None, out_status=None, stream=None,
+                    out_cov_f32=None) -> str:
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
     p = params if params is not None else fit_params()
     s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
     h = kf_track_hits(_ptr(offsets), _ptr(layer), _ptr(x), _ptr(y), _ptr(z))
-    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status),
+                      _ptr(out_cov_f32))
     buf = C.create_string_buffer(128)
     _check(ctx, load().kf_autotune_fit(ctx, C.byref(g), C.byref(p), int(n), C.byref(s), C.byref(h), C.byref(o),
                                        _stream(stream), buf, 128))
@@ -392,13 +399,14 @@ def build_params(nsigma=3.0, chi2_cut=30.0, max_cand=32, warp_coop=False, debug_
 
 def kf_build_besthit(ctx, geom, fit, bp, n_events, n_layers, layers, event_offsets, seed_state, seed_q, seed_hits,
                      hit_idx_out, out_state=None, out_cov=None, out_chi2=None, out_ndof=None, out_status=None,
-                     stream=None):
+                     stream=None, out_cov_f32=None):
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
     f = fit if fit is not None else fit_params()
     b = bp if bp is not None else build_params()
     eo = (C.c_int32 * (n_events + 1))(*[int(v) for v in event_offsets])
     s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
-    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status),
+                      _ptr(out_cov_f32))
     _check(ctx, load().kf_build_besthit(ctx, C.byref(g), C.byref(f), C.byref(b), int(n_events), int(n_layers),
                                         layers, eo, C.byref(s), _ptr(seed_hits), _ptr(hit_idx_out), C.byref(o),
                                         _stream(stream)))
@@ -406,13 +414,14 @@ def kf_build_besthit(ctx, geom, fit, bp, n_events, n_layers, layers, event_offse
 
 def kf_build_ckf(ctx, geom, fit, bp, n_slots, n_events, n_layers, layers, event_offsets, seed_state, seed_q,
                  seed_hits, hit_idx_out, out_state=None, out_cov=None, out_chi2=None, out_ndof=None, out_status=None,
-                 stream=None):
+                 stream=None, out_cov_f32=None):
     g = geom if isinstance(geom, kf_geometry) else make_geometry(geom)
     f = fit if fit is not None else fit_params()
     b = bp if bp is not None else build_params()
     eo = (C.c_int32 * (n_events + 1))(*[int(v) for v in event_offsets])
     s = kf_seeds(_ptr(seed_state), _ptr(seed_q))
-    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status))
+    o = kf_tracks_out(_ptr(out_state), _ptr(out_cov), _ptr(out_chi2), _ptr(out_ndof), _ptr(out_status),
+                      _ptr(out_cov_f32))
     _check(ctx, load().kf_build_ckf(ctx, C.byref(g), C.byref(f), C.byref(b), int(n_slots), int(n_events),
                                     int(n_layers), layers, eo, C.byref(s), _ptr(seed_hits), _ptr(hit_idx_out),
                                     C.byref(o), _stream(stream)))

@@ -121,11 +121,12 @@ def seeds_from_seed_hits(ctx, geom, seed_hits_np, device="cuda", stream=None):
 
 
 def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, nsigma=3.0, chi2_cut=30.0,
-                max_cand=32, n_slots=0, meas_model=kf.KF_MEAS_LAYER, record_pred=False):
+                max_cand=32, n_slots=0, meas_model=kf.KF_MEAS_LAYER, record_pred=False, cov_f32=False):
     """Bin every event's layers, seed, and run best-hit building of all events in one
     launch; returns numpy idx (n, n_layers) and fitted tracks (track-major).  record_pred
     (best-hit only): also 'pred' (n, n_layers, 27), each build step's predicted state and
-    packed covariance (NaN where a track did not get to the layer)."""
+    packed covariance (NaN where a track did not get to the layer).  cov_f32: also
+    'cov32' ([21][n]), the FP32 covariance output."""
     g = kf.make_geometry(geom)
     binned = [bin_event(ctx, geom, ev) for ev in events]
     n_layers = len(events[0]["layers"])
@@ -137,22 +138,25 @@ def build_numpy(ctx, geom, events, precision=kf.KF_PREC_MIXED, warp_coop=False, 
     n = int(eoff[-1])
     idx = torch.empty((n_layers, n), dtype=torch.int32, device="cuda")
     out = alloc_fit_out(n)
+    c32 = torch.full((21, n), float("nan"), dtype=torch.float32, device="cuda") if cov_f32 else None
     if n_slots:  # combinatorial building with n_slots candidates per seed
         kf.kf_build_ckf(ctx, g, kf.fit_params(precision=precision, meas_model=meas_model),
                         kf.build_params(nsigma, chi2_cut, max_cand),
                         n_slots, len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
-                        out["chi2"], out["ndof"], out["status"])
+                        out["chi2"], out["ndof"], out["status"], out_cov_f32=c32)
     else:
         pred = torch.full((n_layers * 27 * n,), float("nan"), dtype=torch.float64, device="cuda") \
             if record_pred else None
         kf.kf_build_besthit(ctx, g, kf.fit_params(precision=precision, meas_model=meas_model),
                             kf.build_params(nsigma, chi2_cut, max_cand, warp_coop, debug_pred=pred),
                             len(events), n_layers, layers, eoff, st, q, sh9, idx, out["state"], out["cov"],
-                            out["chi2"], out["ndof"], out["status"])
+                            out["chi2"], out["ndof"], out["status"], out_cov_f32=c32)
     torch.cuda.synchronize()
     extra = {}
     if not n_slots and record_pred:
         extra["pred"] = pred.view(n_layers, 27, n).permute(2, 0, 1).cpu().numpy()
+    if cov_f32:
+        extra["cov32"], extra["cov64"] = c32.cpu().numpy(), out["cov"].cpu().numpy()
     return dict(extra, idx=idx.t().cpu().numpy(), state=out["state"].t().cpu().numpy(),
                 cov=unpack_cov(out["cov"].cpu().numpy()), chi2=out["chi2"].cpu().numpy(),
                 ndof=out["ndof"].cpu().numpy(), status=out["status"].cpu().numpy().astype(np.uint32),

@@ -209,6 +209,66 @@ def test_fit_host_matches_device_path(ctx):
             np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{k} n_chunks={n_chunks} pinned={pinned}")
 
 
+def test_fp32_covariance_output(ctx):
+    """kf_tracks_out.cov_f32: the covariance in FP32 storage, beside or instead of
+    the FP64 one, from kf_fit (both precisions, both schedules), kf_fit_host,
+    kf_refit_inward and best-hit and combinatorial building -- each entry the FP64
+    output rounded to FP32 (the same value rounded once), and the other outputs
+    unchanged when only cov_f32 is asked for."""
+    g = synth.geometry("barrel17")
+    tk = synth.gen_tracks(g, 20001, synth.BASE_SEED + 27)
+    gg = kf.make_geometry(g)
+    dh = run.hits_to_device(tk)
+    seeds = run.make_seeds(ctx, gg, dh)
+    n = dh["n"]
+    for precision in (kf.KF_PREC_MIXED, kf.KF_PREC_FP64):
+        for schedule in (kf.KF_SCHED_GRID, kf.KF_SCHED_PERSISTENT):
+            p = kf.fit_params(precision=precision, schedule=schedule)
+            ref = run.alloc_fit_out(n)
+            c32 = torch.full((21, n), float("nan"), dtype=torch.float32, device="cuda")
+            kf.kf_fit(ctx, gg, p, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                      ref["state"], ref["cov"], ref["chi2"], ref["ndof"], ref["status"], out_cov_f32=c32)
+            alone = run.alloc_fit_out(n)
+            c32b = torch.full((21, n), float("nan"), dtype=torch.float32, device="cuda")
+            kf.kf_fit(ctx, gg, p, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"],
+                      alone["state"], None, alone["chi2"], alone["ndof"], alone["status"], out_cov_f32=c32b)
+            torch.cuda.synchronize()
+            want = ref["cov"].cpu().numpy().astype(np.float32)
+            np.testing.assert_array_equal(c32.cpu().numpy(), want, err_msg=f"prec={precision} sched={schedule}")
+            np.testing.assert_array_equal(c32b.cpu().numpy(), want)
+            for k in ("state", "chi2", "ndof", "status"):
+                assert torch.equal(alone[k], ref[k]), k
+    # host path: FP32 covariance only, and both
+    ref = run.alloc_fit_out(n)
+    run.fit(ctx, gg, dh, seeds, ref)
+    torch.cuda.synchronize()
+    want = ref["cov"].cpu().numpy().astype(np.float32)
+    hh = {k: torch.from_numpy(np.ascontiguousarray(tk[k])).pin_memory() for k in ("offsets", "layer", "x", "y", "z")}
+    for with64 in (False, True):
+        c32 = torch.full((21, n), float("nan"), dtype=torch.float32).pin_memory()
+        c64 = torch.full((21, n), float("nan"), dtype=torch.float64).pin_memory() if with64 else None
+        st = torch.full((6, n), float("nan"), dtype=torch.float64).pin_memory()
+        kf.kf_fit_host(ctx, gg, None, n, hh["offsets"], hh["layer"], hh["x"], hh["y"], hh["z"], st, c64,
+                       out_cov_f32=c32, n_chunks=5)
+        np.testing.assert_array_equal(c32.numpy(), want)
+        np.testing.assert_array_equal(st.numpy(), ref["state"].cpu().numpy())
+        if with64:
+            np.testing.assert_array_equal(c64.numpy(), ref["cov"].cpu().numpy())
+    # refit (its output turned back to the outward direction in both planes)
+    bw = run.alloc_fit_out(n)
+    c32 = torch.full((21, n), float("nan"), dtype=torch.float32, device="cuda")
+    kf.kf_refit_inward(ctx, gg, None, n, dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"], ref["state"],
+                       ref["cov"], seeds[1], ref["ndof"], 100.0, bw["state"], bw["cov"], bw["chi2"], bw["ndof"],
+                       bw["status"], out_cov_f32=c32)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(c32.cpu().numpy(), bw["cov"].cpu().numpy().astype(np.float32))
+    # building
+    ev = synth.gen_event(g, 2000, synth.BASE_SEED + 28)
+    for n_slots in (0, 4):
+        b = run.build_numpy(ctx, g, [ev], n_slots=n_slots, cov_f32=True)
+        np.testing.assert_array_equal(b["cov32"], b["cov64"].astype(np.float32), err_msg=f"n_slots={n_slots}")
+
+
 def test_fit_host_concurrent_calls_on_one_context(ctx):
     """kf_fit_host from two host threads on one context: the calls share the
     context's device buffers and streams, so the library runs them one at a time,
