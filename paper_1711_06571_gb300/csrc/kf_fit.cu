@@ -957,14 +957,20 @@ int persistent_blocks_per_sm(bool fp64, int block)
 // ------------------------------------------------------------------ processing order
 
 // Counting sort of the tracks into buckets of (hit count, descending) x (seed
-// phase with a disk hit first) x (seed |1/pT|, 64 bins of 1/32 GeV^-1, clamped,
-// descending): a warp then takes tracks that cross nearly the same layers, bend
-// alike and run the same seed phase, so the layer loop, the seed phase (FP64 with
-// a disk hit, double-float without) and the near-tangent steps (low-pT tracks at
-// their apex) diverge little, and the costliest tracks (most hits, then the FP64
-// seed phase, then lowest pT: widest build windows, most near-tangent steps) come
-// first, so that the short ones fill the launch's tail.  The order inside a bucket
-// is that of the atomics, which does not change any track's result.
+// phase with a disk hit first) x (seed |1/pT|, descending): a warp then takes
+// tracks that cross nearly the same layers, bend alike and run the same seed
+// phase, so the layer loop, the seed phase (FP64 with a disk hit, double-float
+// without) and the near-tangent steps (low-pT tracks at their apex) diverge
+// little, and the costliest tracks (most hits, then the FP64 seed phase, then
+// lowest pT: widest build windows, most near-tangent steps) come first, so that
+// the short ones fill the launch's tail.  |1/pT| takes one bin below ip_one, the
+// curvature at which the helix meets the outermost surface at a transverse
+// crossing sine of 0.6 (no near-tangent crossing below it), and 63 bins of 1/32
+// GeV^-1 above.  Inside a bucket the tracks keep their input order warp by warp
+// (ranks from a warp vote; the warps of a block and the blocks reserve their
+// ranges in the order of their atomics): the bucket of the common stiff tracks is
+// then dense in t, and its SoA loads and output stores share 32-byte sectors.
+// The order does not change any track's result.
 //
 // Sorting groups of consecutive tracks instead (so that the per-track SoA outputs
 // of a group share 32-byte sectors) was measured: groups of 4 made the fit 1.9x
@@ -979,6 +985,8 @@ struct OrderIn {
     const float *ip;            // seed 1/pT [n]
     const uint8_t *layer;       // surface of each hit, or null (no disk bit)
     unsigned long long disk;    // bit s set: surface s is a disk
+    float ip_one;               // |1/pT| below this: one bin
+    float pad_;
 };
 
 __device__ __forceinline__ int order_key(const OrderIn &in, int t)
@@ -990,8 +998,18 @@ __device__ __forceinline__ int order_key(const OrderIn &in, int t)
         if (in.layer)
             for (int j = 0; j < min(nh, in.nseed); ++j) disk |= (int)((in.disk >> in.layer[o + j]) & 1ull);
     }
-    const int b = min((int)(fabsf(in.ip[t]) * 32.f), 63);
+    const float ip = fabsf(in.ip[t]);
+    const int b = ip < in.ip_one ? 0 : 1 + min((int)((ip - in.ip_one) * 32.f), 62);
     return ((64 - nh) * 2 + (1 - disk)) * 64 + (63 - b);
+}
+// this lane's rank among the active lanes of its warp with the same key, and
+// the number of them (lane order)
+__device__ __forceinline__ int warp_rank(int key, bool live, int &count)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, live);
+    const unsigned same = __match_any_sync(0xffffffffu, live ? key : -1) & act;
+    count = __popc(same);
+    return __popc(same & ((1u << (threadIdx.x & 31)) - 1u));
 }
 // Histogram and scatter count in shared memory per block and touch global
 // memory once per non-empty bucket and block: the keys of neighbouring tracks
@@ -1053,15 +1071,21 @@ __global__ void __launch_bounds__(1024) order_scatter_kernel(OrderIn in, int32_t
     for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int key = t < in.n ? order_key(in, t) : 0;
+    const bool live = t < in.n;
+    const int key = live ? order_key(in, t) : 0;
+    // one shared atomic per (warp, key), by the key's first lane; the others add their rank
+    int count;
+    const int rank = warp_rank(key, live, count);
     int local = 0;
-    if (t < in.n) local = atomicAdd(&cnt[key], 1);
+    if (live && rank == 0) local = atomicAdd(&cnt[key], count);
+    const unsigned same = __match_any_sync(0xffffffffu, live ? key : -1) & __ballot_sync(0xffffffffu, live);
+    local = __shfl_sync(0xffffffffu, local, same ? __ffs(same) - 1 : 0) + rank;
     __syncthreads();
     // reserve this block's range in every bucket it uses
     for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x)
         if (cnt[b]) cnt[b] = atomicAdd(&cursor[b], cnt[b]);
     __syncthreads();
-    if (t < in.n) order[cnt[key] + local] = t;
+    if (live) order[cnt[key] + local] = t;
 }
 
 size_t order_scratch_ints() { return ORDER_BUCKETS; }
@@ -1079,9 +1103,18 @@ cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const 
     in.ip = seed_ip;
     in.layer = off && g ? layer : nullptr;
     in.disk = 0;
-    if (g)
-        for (int s = 0; s < g->n && s < 64; ++s)
+    in.ip_one = 0.f;
+    in.pad_ = 0.f;
+    if (g) {
+        float rmax = 0.f;
+        for (int s = 0; s < g->n && s < 64; ++s) {
             if (g->s[s].kind == 1) in.disk |= 1ull << s;
+            rmax = std::max(rmax, g->s[s].kind == 0 ? g->s[s].pos : g->s[s].rout);
+        }
+        // the curvature |c| = |kb| / pT at which a helix from the beam line meets
+        // radius rmax at transverse crossing sine rmax |c| / 2 = 0.6
+        if (rmax > 0.f && g->kb != 0.f) in.ip_one = 1.2f / (std::fabs(g->kb) * rmax);
+    }
     const int b = 1024, grid = (n + b - 1) / b;
     order_hist_kernel<<<grid, b, 0, st>>>(in, hist);
     order_scan_kernel<<<1, 1024, 0, st>>>(hist);
