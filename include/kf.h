@@ -30,6 +30,22 @@
  *     change sign during a fit (the physical curvature is -q * kappa * Bz / pT).
  *     Covariances are packed lower triangles, row-major, i >= j:
  *     entry (i, j) at index i*(i+1)/2 + j, 21 values.
+ *
+ * Calls and the problem statement they follow
+ *   kf_fit (seeds, hits, layer geometry -> fitted states, covariances, chi2)
+ *   and kf_build_besthit (seeds, binned hits per layer -> hit indices per layer
+ *   plus fitted states) are the two forms of the hot path.  Three choices of
+ *   this interface differ from a one-call-per-concern layout:
+ *   - the arithmetic precision is a field of kf_fit_params (precision,
+ *     n_fp64_updates, seed_update), passed with every fit and build call,
+ *     not a context-wide setter, so that calls of different precision can
+ *     share a context and run concurrently;
+ *   - serving statistics are read with kf_server_stats_get, which fills a
+ *     caller-owned kf_server_stats structure (the structure takes the plain
+ *     name);
+ *   - kf_server_poll reports a finished event's latency and leaves the
+ *     results in the caller's output arrays named at submission, instead of
+ *     returning a result record that the library would own.
  */
 #ifndef KF_H
 #define KF_H

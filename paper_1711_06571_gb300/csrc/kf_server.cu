@@ -573,7 +573,7 @@ int kf_server::launch(Batch &b)
     // best-hit build of all events
     int32_t *idx = reinterpret_cast<int32_t *>(dp(d_idx));
     int32_t *ord1 = reinterpret_cast<int32_t *>(dp(d_ord1));
-    if (e == cudaSuccess) e = launch_order(N, nullptr, seed + 3 * (size_t)N, nullptr, nullptr, 0, ord1, ord1 + order_scratch_ints(),
+    if (e == cudaSuccess) e = launch_order(N, nullptr, seed + 3 * (size_t)N, nullptr, &geom, 0, ord1, ord1 + order_scratch_ints(),
                                               st);
     if (e == cudaSuccess) {
         BuildArgs a;
