@@ -746,6 +746,22 @@ def main():
     d2h = (48 + 168 + 8 + 4 + 4) * n
     # the host results equal the device-resident run
     same = np.array_equal(ho["chi2"].numpy(), out["chi2"].cpu().numpy())
+    # the same call with the covariance returned in FP32 (kf_tracks_out.cov_f32: the
+    # mixed path's own covariance precision, 84 instead of 168 bytes per track)
+    ho32 = torch.empty((21, n), dtype=torch.float32).pin_memory()
+
+    def e2e_step32():
+        kf.kf_fit_host(ctx, g, params, n, hh["offsets"], hh["layer"], hh["x"], hh["y"], hh["z"], ho["state"],
+                       None, ho["chi2"], ho["ndof"], ho["status"], out_cov_f32=ho32)
+
+    for _ in range(2):
+        e2e_step32()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        e2e_step32()
+    t_e2e32 = max_over_ranks((time.perf_counter() - t0) / e2e_reps, world)
+    d2h32 = (48 + 84 + 8 + 4 + 4) * n
 
     # best-hit build of 10 events x 20,000 tracks
     build = build_bench(ctx, geom, max(10, args.steps // 4), max(3, args.warmup // 2))
@@ -804,7 +820,9 @@ def main():
                             parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
                 roofline=roofline, cpu_baseline=cpu_baseline,
                 e2e=dict(value=total_updates / t_e2e, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-                         ms_per_step=t_e2e * 1e3, api="kf_fit_host", host_matches_device=bool(same)),
+                         ms_per_step=t_e2e * 1e3, api="kf_fit_host", host_matches_device=bool(same),
+                         cov_f32=dict(value=total_updates / t_e2e32, unit=UNIT, ms_per_step=t_e2e32 * 1e3,
+                                      d2h_bytes_per_step=d2h32)),
                 fp64_path=dict(value=updates_per_step * world / (ms64 * 1e-3), unit=UNIT, fit_ms=ms64,
                                speedup_of_mixed=ms64 / fit_avg),
                 gpu_launches=6 * args.steps, clocks=clk, parity_vs_oracle=parity, build=build, uneven_batch=uneven,

@@ -412,7 +412,8 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
             a.timing_events = ctx->tev[ctx->tcalls % kf_ctx::TRING].data();
             ++ctx->tcalls;
         }
-        cudaError_t e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hits->layer, &G, nseed, hist, order, st);
+        cudaError_t e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, seeds->state + 5 * (size_t)n,
+                                     hits->layer, &G, nseed, hist, order, st);
         if (e == cudaSuccess) e = launch_fit(G, a, fp64, 128, st);
         return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "fit kernel");
     }
@@ -430,7 +431,9 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
     a.chunk = tu.chunk;
     if (force) {
         cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
-        if (e == cudaSuccess) e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hits->layer, &G, nseed, hist, order, st);
+        if (e == cudaSuccess)
+            e = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, seeds->state + 5 * (size_t)n,
+                             hits->layer, &G, nseed, hist, order, st);
         if (e == cudaSuccess) e = launch_fit_persistent(G, a, fp64, tu.block, tu.grid, st);
         return e == cudaSuccess ? KF_OK : cuda_fail(ctx, e, "persistent fit");
     }
@@ -450,7 +453,9 @@ static int fit_impl(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *p
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
         cudaError_t e1 = cudaMemsetAsync(queue, 0, sizeof(int32_t), cs);
-        if (e1 == cudaSuccess) e1 = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, hits->layer, &G, nseed, hist, order, cs);
+        if (e1 == cudaSuccess)
+            e1 = launch_order(n, hits->offsets, seeds->state + 3 * (size_t)n, seeds->state + 5 * (size_t)n,
+                              hits->layer, &G, nseed, hist, order, cs);
         if (e1 == cudaSuccess) e1 = launch_fit_persistent(G, a, fp64, tu.block, tu.grid, cs);
         e = cudaStreamEndCapture(cs, &graph);
         if (e1 != cudaSuccess || e != cudaSuccess) {
@@ -663,8 +668,9 @@ int kf_fit_host(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *param
             if (e == cudaSuccess) e = cudaMemcpyAsync(d_z + h0, hits->z + h0, (size_t)(h1 - h0) * 4, cudaMemcpyHostToDevice, st);
         }
         if (e == cudaSuccess) e = launch_seeds(G, cnt, n, t0, d_off, d_x, d_y, d_z, d_seed, d_q, st);
-        if (e == cudaSuccess) e = launch_order(cnt, d_off + t0, d_seed + 3 * (size_t)n + t0, d_lay, &G, std::max(3, P.n_fp64_updates),
-                                               hist, order, st);
+        if (e == cudaSuccess)
+            e = launch_order(cnt, d_off + t0, d_seed + 3 * (size_t)n + t0, d_seed + 5 * (size_t)n + t0, d_lay, &G,
+                             std::max(3, P.n_fp64_updates), hist, order, st);
         if (e == cudaSuccess) {
             FitArgs a;
             memset(&a, 0, sizeof a);
@@ -980,7 +986,8 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
         return rc;
     int32_t *hist = reinterpret_cast<int32_t *>(rest);
     int32_t *order = hist + nhist;
-    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, &G, 0, hist, order, st);
+    cudaError_t eo =
+        launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, nullptr, &G, 0, hist, order, st);
     if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
     BuildArgs a;
     memset(&a, 0, sizeof a);
@@ -1061,7 +1068,8 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
         return rc;
     int32_t *hist = reinterpret_cast<int32_t *>(rest);
     int32_t *order = hist + nhist;
-    cudaError_t eo = launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, &G, 0, hist, order, st);
+    cudaError_t eo =
+        launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, nullptr, &G, 0, hist, order, st);
     if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
     CkfArgs c;
     memset(&c, 0, sizeof c);

@@ -737,9 +737,11 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) fit_persistent_kernel(cons
 }
 
 // phase 2 of the mixed fit in the persistent form (the work queue of
-// fit_persistent_kernel over processing positions; phase 1 ran as a grid)
+// fit_persistent_kernel over processing positions; phase 1 ran as a grid); 768
+// threads (24 warps) per SM whatever the block size, at most 85 registers a
+// thread: on the 2e6-track barrel+disk batch 9.96 ms against 10.21 at 16 warps
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 512 / BLOCK) fit_loop_persistent_kernel(const Geom g, const FitArgs a)
+__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) fit_loop_persistent_kernel(const Geom g, const FitArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
     __shared__ int s_base;
@@ -986,9 +988,12 @@ struct OrderIn {
     const float *ip;            // seed 1/pT [n]
     const uint8_t *layer;       // surface of each hit, or null (no disk bit)
     unsigned long long disk;    // bit s set: surface s is a disk
-    float ip_one;               // |1/pT| below this: one bin
+    float ip_one;               // |1/pT| below this: one bin (or ETA_BINS bins of |cot theta|)
     float pad_;
+    const float *th;            // seed theta [n], or null: with disks in the geometry, the stiff
+                                // tracks are binned by |cot theta| (their barrel / disk sequence)
 };
+constexpr int ETA_BINS = 16;
 
 __device__ __forceinline__ int order_key(const OrderIn &in, int t)
 {
@@ -1000,7 +1005,19 @@ __device__ __forceinline__ int order_key(const OrderIn &in, int t)
             for (int j = 0; j < min(nh, in.nseed); ++j) disk |= (int)((in.disk >> in.layer[o + j]) & 1ull);
     }
     const float ip = fabsf(in.ip[t]);
-    const int b = ip < in.ip_one ? 0 : 1 + min((int)((ip - in.ip_one) * 32.f), 62);
+    int b;
+    if (in.th) {  // disks in the geometry: ETA_BINS bins of |cot theta| for the stiff tracks
+        if (ip < in.ip_one) {
+            float sth, cth;
+            __sincosf(in.th[t], &sth, &cth);
+            const float cot = fabsf(cth) / fmaxf(fabsf(sth), 1e-6f);
+            b = min((int)(cot * 2.5f), ETA_BINS - 1);
+        } else {
+            b = ETA_BINS + min((int)((ip - in.ip_one) * 32.f), 63 - ETA_BINS);
+        }
+    } else {
+        b = ip < in.ip_one ? 0 : 1 + min((int)((ip - in.ip_one) * 32.f), 62);
+    }
     return ((64 - nh) * 2 + (1 - disk)) * 64 + (63 - b);
 }
 // this lane's rank among the active lanes of its warp with the same key, and
@@ -1091,8 +1108,9 @@ __global__ void __launch_bounds__(1024) order_scatter_kernel(OrderIn in, int32_t
 
 size_t order_scratch_ints() { return ORDER_BUCKETS; }
 
-cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const uint8_t *layer,
-                         const Geom *g, int nseed, int32_t *hist, int32_t *order, cudaStream_t st)
+cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const float *seed_th,
+                         const uint8_t *layer, const Geom *g, int nseed, int32_t *hist, int32_t *order,
+                         cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(hist, 0, ORDER_BUCKETS * sizeof(int32_t), st);
@@ -1106,6 +1124,7 @@ cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const 
     in.disk = 0;
     in.ip_one = 0.f;
     in.pad_ = 0.f;
+    in.th = nullptr;
     if (g) {
         float rmax = 0.f;
         for (int s = 0; s < g->n && s < 64; ++s) {
@@ -1115,6 +1134,7 @@ cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const 
         // the curvature |c| = |kb| / pT at which a helix from the beam line meets
         // radius rmax at transverse crossing sine rmax |c| / 2 = 0.6
         if (rmax > 0.f && g->kb != 0.f) in.ip_one = 1.2f / (std::fabs(g->kb) * rmax);
+        if (in.disk && in.off) in.th = seed_th;
     }
     const int b = 1024, grid = (n + b - 1) / b;
     order_hist_kernel<<<grid, b, 0, st>>>(in, hist);

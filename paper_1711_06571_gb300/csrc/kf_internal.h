@@ -68,9 +68,10 @@ cudaError_t launch_fit_persistent(const Geom &g, const FitArgs &a, bool fp64, in
 int persistent_blocks_per_sm(bool fp64, int block);
 size_t order_scratch_ints();
 // processing order: tracks bucketed by (hit count, a disk among the first nseed
-// hits' surfaces -- needs off, layer and g --, seed 1/pT); off null: by 1/pT alone
-cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const uint8_t *layer, const Geom *g,
-                         int nseed, int32_t *hist, int32_t *order, cudaStream_t st);
+// hits' surfaces -- needs off, layer and g --, seed 1/pT, and for geometries with
+// disks the seed theta of the stiff tracks); off null: by 1/pT alone
+cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const float *seed_th, const uint8_t *layer,
+                         const Geom *g, int nseed, int32_t *hist, int32_t *order, cudaStream_t st);
 
 // outward-inward refit (kf_fit.cu): cnt[t] = hits the forward fit used, then
 // (after an exclusive scan of cnt into roff) those hits reversed into roff's CSR

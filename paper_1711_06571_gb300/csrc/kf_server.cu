@@ -573,8 +573,9 @@ int kf_server::launch(Batch &b)
     // best-hit build of all events
     int32_t *idx = reinterpret_cast<int32_t *>(dp(d_idx));
     int32_t *ord1 = reinterpret_cast<int32_t *>(dp(d_ord1));
-    if (e == cudaSuccess) e = launch_order(N, nullptr, seed + 3 * (size_t)N, nullptr, &geom, 0, ord1, ord1 + order_scratch_ints(),
-                                              st);
+    if (e == cudaSuccess)
+        e = launch_order(N, nullptr, seed + 3 * (size_t)N, nullptr, nullptr, &geom, 0, ord1,
+                         ord1 + order_scratch_ints(), st);
     if (e == cudaSuccess) {
         BuildArgs a;
         memset(&a, 0, sizeof a);
@@ -612,8 +613,9 @@ int kf_server::launch(Batch &b)
     int8_t *fq = reinterpret_cast<int8_t *>(dp(d_fq));
     int32_t *ord2 = reinterpret_cast<int32_t *>(dp(d_ord2));
     if (e == cudaSuccess) e = launch_seeds(geom, N, N, 0, goff, gx, gy, gz, fseed, fq, st);
-    if (e == cudaSuccess) e = launch_order(N, goff, fseed + 3 * (size_t)N, glay, &geom, std::max(3, p.fit.n_fp64_updates), ord2,
-                                              ord2 + order_scratch_ints(), st);
+    if (e == cudaSuccess)
+        e = launch_order(N, goff, fseed + 3 * (size_t)N, fseed + 5 * (size_t)N, glay, &geom,
+                         std::max(3, p.fit.n_fp64_updates), ord2, ord2 + order_scratch_ints(), st);
     if (e == cudaSuccess) {
         FitArgs a;
         memset(&a, 0, sizeof a);
