@@ -41,7 +41,7 @@ WORKLOAD = ("KF fit of 1,000,000 tracks x 17 barrel layers (R 4-100 cm), Bz 3.8 
 # DRAM bytes (read + write) of one fit_loop_kernel launch on this workload, from
 # an ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum); None whenever the kernel changes until it is captured again
-LOOP_KERNEL_DRAM_BYTES = None
+LOOP_KERNEL_DRAM_BYTES = 1.447e9
 FP64_FLOP_PHASE1_BARREL = 194.0
 FP64_FLOP_PER_FP32_UPDATE = 44.0
 FP32_FLOP_PER_FP32_UPDATE = 900.0

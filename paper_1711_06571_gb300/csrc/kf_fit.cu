@@ -271,7 +271,7 @@ struct MixedIOD {
 template <bool M1>
 static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int k, double alpha, double mass2,
                                                                  int ms_on, const Surf *sf, float hx, float hy,
-                                                                 float hz)
+                                                                 float hz, bool seeded)
 {
     Track<double, double> sd;
     sd.x = to_d(m.st.x);
@@ -280,7 +280,7 @@ static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int
     sd.phi = to_d(m.st.phi);
     sd.ip = m.st.ip;
     sd.th = to_d(m.st.th);
-    m.ok = fit_step<true, double, M1>(sd, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status);
+    m.ok = fit_step<true, double, M1>(sd, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status, seeded);
     if (m.ok) {
         m.st.x = ff_from_d(sd.x);
         m.st.y = ff_from_d(sd.y);
@@ -480,8 +480,9 @@ __device__ __forceinline__ bool fit_phase1(int t, const FitArgs &a, const Surf *
                 for (int i = 0; i < 21; ++i) m.p[i] = pd[i];
                 m.chi2 = chi2;
                 m.status = status;
+                // k == 1 after the structured seed-hit update: the transport skips its zero blocks
                 m = fp64_step_pd_out_of_line<M1>(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
-                                             a.hz[h]);
+                                                 a.hz[h], !P0 && k == 1);
                 st = m.st;
 #pragma unroll
                 for (int i = 0; i < 21; ++i) pd[i] = m.p[i];
@@ -969,10 +970,14 @@ int persistent_blocks_per_sm(bool fp64, int block)
 // the short ones fill the launch's tail.  |1/pT| takes one bin below ip_one, the
 // curvature at which the helix meets the outermost surface at a transverse
 // crossing sine of 0.6 (no near-tangent crossing below it), and 63 bins of 1/32
-// GeV^-1 above.  Inside a bucket the tracks keep their input order warp by warp
-// (ranks from a warp vote; the warps of a block and the blocks reserve their
-// ranges in the order of their atomics): the bucket of the common stiff tracks is
-// then dense in t, and its SoA loads and output stores share 32-byte sectors.
+// GeV^-1 above; where the geometry has disks, and for building, the stiff tracks
+// are split further into 16 bins of |cot theta| (tracks of one bin cross barrels
+// and disks in the same sequence, and have alike build windows) and the 1/pT
+// bins above ip_one are 48.  Inside a bucket the tracks keep their input order
+// warp by warp (ranks from a warp vote; the warps of a block and the blocks
+// reserve their ranges in the order of their atomics): the bucket of the common
+// stiff tracks is then dense in t, and its SoA loads and output stores share
+// 32-byte sectors.
 // The order does not change any track's result.
 //
 // Sorting groups of consecutive tracks instead (so that the per-track SoA outputs
@@ -990,8 +995,9 @@ struct OrderIn {
     unsigned long long disk;    // bit s set: surface s is a disk
     float ip_one;               // |1/pT| below this: one bin (or ETA_BINS bins of |cot theta|)
     float pad_;
-    const float *th;            // seed theta [n], or null: with disks in the geometry, the stiff
-                                // tracks are binned by |cot theta| (their barrel / disk sequence)
+    const float *th;            // seed theta [n], or null: with disks in the geometry (their barrel /
+                                // disk sequence), or for building (window sizes), the stiff tracks
+                                // are binned by |cot theta|
 };
 constexpr int ETA_BINS = 16;
 
@@ -1006,7 +1012,7 @@ __device__ __forceinline__ int order_key(const OrderIn &in, int t)
     }
     const float ip = fabsf(in.ip[t]);
     int b;
-    if (in.th) {  // disks in the geometry: ETA_BINS bins of |cot theta| for the stiff tracks
+    if (in.th) {  // ETA_BINS bins of |cot theta| for the stiff tracks
         if (ip < in.ip_one) {
             float sth, cth;
             __sincosf(in.th[t], &sth, &cth);
@@ -1134,7 +1140,7 @@ cudaError_t launch_order(int n, const int32_t *off, const float *seed_ip, const 
         // the curvature |c| = |kb| / pT at which a helix from the beam line meets
         // radius rmax at transverse crossing sine rmax |c| / 2 = 0.6
         if (rmax > 0.f && g->kb != 0.f) in.ip_one = 1.2f / (std::fabs(g->kb) * rmax);
-        if (in.disk && in.off) in.th = seed_th;
+        if (seed_th && (in.disk || !in.off)) in.th = seed_th;
     }
     const int b = 1024, grid = (n + b - 1) / b;
     order_hist_kernel<<<grid, b, 0, st>>>(in, hist);

@@ -705,6 +705,41 @@ def test_refit_inward_statistics_at_first_hit(oracle_mod):
     assert abs(chi2.mean() - 5.0) < 5 * np.sqrt(10.0 / m)
 
 
+def test_refit_inward_counts_the_forward_fit_at_weight_one_over_scale(oracle_mod):
+    """The backward pass starts from the forward estimate with its covariance times
+    cov_scale, so (no scattering: every hit's information adds) the forward fit's
+    information enters once more at weight 1 / cov_scale.  The forward covariance
+    holds the information of the same hits, so the covariance at the first hit with
+    cov_scale = 100 is the one with a diffuse start (cov_scale = 1e8) divided by
+    1 + 1/100: each variance by 1.01.  A start that counted the forward
+    information at full weight (halving the variances), or not at all, fails.  Per
+    track the ratio scatters by up to a few percent (the two passes and the forward
+    fit linearise the helix at slightly different states); its mean over the tracks
+    is held to 3e-4."""
+    g = synth.geometry("barrel10")
+    tk = synth.gen_tracks(g, 300, 35, ms_on=False)
+    fw = oracle_mod.fit(g, tk, ms_on=False)
+    b100 = oracle_mod.refit_inward(g, tk, fw["state"], fw["cov"], fw["q"], fw["ndof"], cov_scale=100.0,
+                                   ms_on=False)
+    bdif = oracle_mod.refit_inward(g, tk, fw["state"], fw["cov"], fw["q"], fw["ndof"], cov_scale=1e8,
+                                   ms_on=False)
+    ok = (fw["status"] == 0) & (b100["status"] == 0) & (bdif["status"] == 0)
+    assert ok.mean() > 0.95
+    # the five free directions: 1/pT, phi, theta and the two position coordinates on the first layer
+    first = tk["offsets"][:-1]
+    x, y = tk["x"][first][ok].astype(float), tk["y"][first][ok].astype(float)
+    r = np.hypot(x, y)
+    v100, vdif = b100["cov"][ok], bdif["cov"][ok]
+    ratios = [v100[:, i, i] / vdif[:, i, i] for i in (3, 4, 5)]
+    # r-phi position variance: t = (-y, x) / r
+    def tt(c):
+        return (y * y * c[:, 0, 0] - 2 * x * y * c[:, 1, 0] + x * x * c[:, 1, 1]) / (r * r)
+    ratios += [tt(v100) / tt(vdif), v100[:, 2, 2] / vdif[:, 2, 2]]
+    for rt in ratios:
+        np.testing.assert_allclose(rt, 1.0 / 1.01, rtol=5e-2)
+        assert abs(rt.mean() * 1.01 - 1.0) < 3e-4, rt.mean() * 1.01
+
+
 # ---------------------------------------------------------------------- measurement model 1 (Sec. 4.1)
 
 def test_update2d_equals_information_form(oracle_mod):
