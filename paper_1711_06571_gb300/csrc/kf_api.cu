@@ -987,8 +987,7 @@ int kf_build_besthit(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *
     int32_t *hist = reinterpret_cast<int32_t *>(rest);
     int32_t *order = hist + nhist;
     cudaError_t eo =
-        launch_order(n, nullptr, seeds->state + 3 * (size_t)n, seeds->state + 5 * (size_t)n, nullptr, &G, 0, hist,
-                     order, st);
+        launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, nullptr, &G, 0, hist, order, st);
     if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
     BuildArgs a;
     memset(&a, 0, sizeof a);
@@ -1070,8 +1069,7 @@ int kf_build_ckf(kf_ctx *ctx, const kf_geometry *geom, const kf_fit_params *fit,
     int32_t *hist = reinterpret_cast<int32_t *>(rest);
     int32_t *order = hist + nhist;
     cudaError_t eo =
-        launch_order(n, nullptr, seeds->state + 3 * (size_t)n, seeds->state + 5 * (size_t)n, nullptr, &G, 0, hist,
-                     order, st);
+        launch_order(n, nullptr, seeds->state + 3 * (size_t)n, nullptr, nullptr, &G, 0, hist, order, st);
     if (eo != cudaSuccess) return cuda_fail(ctx, eo, "build order");
     CkfArgs c;
     memset(&c, 0, sizeof c);

@@ -574,7 +574,7 @@ int kf_server::launch(Batch &b)
     int32_t *idx = reinterpret_cast<int32_t *>(dp(d_idx));
     int32_t *ord1 = reinterpret_cast<int32_t *>(dp(d_ord1));
     if (e == cudaSuccess)
-        e = launch_order(N, nullptr, seed + 3 * (size_t)N, seed + 5 * (size_t)N, nullptr, &geom, 0, ord1,
+        e = launch_order(N, nullptr, seed + 3 * (size_t)N, nullptr, nullptr, &geom, 0, ord1,
                          ord1 + order_scratch_ints(), st);
     if (e == cudaSuccess) {
         BuildArgs a;
