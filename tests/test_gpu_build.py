@@ -221,6 +221,16 @@ def classify_build(oracle_mod, g, ev, orc, gidx, gpred, gq, t_sel=None, meas_mod
     return steps, allowed, unexplained
 
 
+def _check_build_cov(res, status, mask):
+    """The covariance tolerance of the fits, for built tracks: 1e-3 of sqrt(C_ii C_jj);
+    tracks that met a crossing within a few degrees of tangent (KF_ST_GRAZING) are
+    held to 1e-2 (the mixed build's double-float step with an FP32 Jacobian leaves up
+    to 7.3e-3 there; an FP64 step for such crossings cost 17% of the build)."""
+    graz = (status[mask].astype(np.uint32) & kf.KF_ST_GRAZING) != 0
+    assert res["dcov"][~graz].max(initial=0.0) <= parity.TOL_COV_NORM, res["dcov"][~graz].max()
+    assert res["dcov"][graz].max(initial=0.0) <= 10 * parity.TOL_COV_NORM, res["dcov"][graz].max()
+
+
 @pytest.mark.parametrize("warp_coop", [True, False])
 @pytest.mark.parametrize("precision", [kf.KF_PREC_MIXED, kf.KF_PREC_FP64])
 def test_build_parity(ctx, oracle_mod, warp_coop, precision):
@@ -250,6 +260,7 @@ def test_build_parity(ctx, oracle_mod, warp_coop, precision):
               parity.summary(res))
         assert res["max_pull"].max() <= parity.TOL_PARAM_SIGMA
         assert res["chi2rel"].max() <= parity.TOL_CHI2_REL
+        _check_build_cov(res, orc["status"], same)
         t0 += n
     print(f"build prec={precision} coop={warp_coop}: {tot_allowed} allowed differences in {tot_steps} steps")
     assert tot_allowed <= 2e-3 * tot_steps
@@ -287,6 +298,7 @@ def test_build_parity_hit_2d_staggered(ctx, oracle_mod, precision):
                   "oracle", orc["state"][t].tolist(), "gpu", g_slice["state"][t].tolist())
         assert res["max_pull"].max() <= parity.TOL_PARAM_SIGMA
         assert res["chi2rel"].max() <= parity.TOL_CHI2_REL
+        _check_build_cov(res, orc["status"], same)
         where = ev["truth_where"][:, 3:]
         has = where >= 0
         effs.append(np.mean(gidx[:, 3:][has] == where[has]))
@@ -387,6 +399,7 @@ def test_ckf_parity(ctx, oracle_mod, n_slots):
         print("   ", parity.summary(res))
         assert res["max_pull"].max() <= parity.TOL_PARAM_SIGMA
         assert res["chi2rel"].max() <= parity.TOL_CHI2_REL
+        _check_build_cov(res, orc["status"], ok)
         np.testing.assert_array_equal(gpu["ndof"][t0:t0 + n][ok], orc["ndof"][ok])
         t0 += n
 
@@ -472,3 +485,4 @@ def test_gather_and_final_fit(ctx, oracle_mod):
     res = parity.compare_fits(gfit, ofit, np.zeros(n, int), ok)
     print("final fit:", parity.summary(res))
     assert res["max_pull"].max() <= parity.TOL_PARAM_SIGMA
+    assert res["dcov"].max() <= parity.TOL_COV_NORM
