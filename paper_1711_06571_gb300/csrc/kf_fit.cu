@@ -675,12 +675,12 @@ __global__ void __launch_bounds__(128, 4) fit_seed_kernel(const Geom g, const Fi
     else a.carry.k[i] = -1;  // finished in phase 1
 }
 
-// phase 2 of the mixed fit, grid schedule; six blocks of 128 per SM (at most 85
-// registers: 1.209 ms per 1e6 barrel tracks against 1.227 with five, and 5.96
-// against 6.16 ms on the 2e6-track barrel+disk batch; with the earlier
-// per-track-random bucket order five had been the best, 1.43 against 1.46)
+// phase 2 of the mixed fit, grid schedule; seven blocks of 128 per SM (at most
+// 72 registers: 1.175 ms per 1e6 barrel tracks against 1.211 with six, 1.183
+// with eight; with the earlier per-track-random bucket order five had been the
+// best, 1.43 against 1.46)
 template <bool M1>
-__global__ void __launch_bounds__(128, 6) fit_loop_kernel(const Geom g, const FitArgs a)
+__global__ void __launch_bounds__(128, 7) fit_loop_kernel(const Geom g, const FitArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
     load_geom(g, s_surf);
