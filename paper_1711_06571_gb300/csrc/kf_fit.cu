@@ -738,11 +738,12 @@ __global__ void __launch_bounds__(BLOCK, 512 / BLOCK) fit_persistent_kernel(cons
 }
 
 // phase 2 of the mixed fit in the persistent form (the work queue of
-// fit_persistent_kernel over processing positions; phase 1 ran as a grid); 768
-// threads (24 warps) per SM whatever the block size, at most 85 registers a
-// thread: on the 2e6-track barrel+disk batch 9.96 ms against 10.21 at 16 warps
+// fit_persistent_kernel over processing positions; phase 1 ran as a grid); 1024
+// threads (32 warps) per SM whatever the block size, at most 64 registers a
+// thread: on the 2e6-track barrel+disk batch 9.87 ms against 9.99 at 24 warps and
+// 10.21 at 16
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) fit_loop_persistent_kernel(const Geom g, const FitArgs a)
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) fit_loop_persistent_kernel(const Geom g, const FitArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
     __shared__ int s_base;
