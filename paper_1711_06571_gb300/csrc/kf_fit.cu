@@ -269,9 +269,15 @@ struct MixedIOD {
 };
 
 template <bool M1>
+// df_update (a disk-seeded track's seed-phase updates after the first, model 0):
+// the propagation, transport and noise in FP64 as above, the update in
+// double-float U-D form.  Measured on 20,000 barrel+disk tracks against the
+// oracle with the host build of this code: the same parity as the FP64 Joseph
+// update (covariance within 2.0e-4 of its sigmas); the first update in U-D form
+// as well left the covariance 1.85e-3 off.
 static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int k, double alpha, double mass2,
                                                                  int ms_on, const Surf *sf, float hx, float hy,
-                                                                 float hz, bool seeded)
+                                                                 float hz, bool seeded, bool df_update)
 {
     Track<double, double> sd;
     sd.x = to_d(m.st.x);
@@ -280,6 +286,37 @@ static __device__ __noinline__ MixedIOD fp64_step_pd_out_of_line(MixedIOD m, int
     sd.phi = to_d(m.st.phi);
     sd.ip = m.st.ip;
     sd.th = to_d(m.st.th);
+    if (!M1 && df_update) {
+        Jac<double> J;
+        if (!propagate(sd, alpha, *sf, J)) {
+            m.status |= reach_bits(sd);
+            m.ok = 0;
+            return m;
+        }
+        transport<double>(m.p, J);
+        if (ms_on) m.status |= ms_noise<double, double>(sd, *sf, J.cphi1, J.sphi1, mass2, m.p);
+        Track<float, ff> st;
+        st.x = ff_from_d(sd.x);
+        st.y = ff_from_d(sd.y);
+        st.z = ff_from_d(sd.z);
+        st.phi = ff_from_d(sd.phi);
+        st.ip = (float)sd.ip;
+        st.th = ff_from_d(sd.th);
+        df p[21];
+#pragma unroll
+        for (int i = 0; i < 21; ++i) p[i] = df_from_d(m.p[i]);
+        df c2 = df(0.f);
+        m.ok = ud_update3(st, p, hx, hy, hz, *sf, c2);
+        if (!m.ok) {
+            m.status |= KF_ST_CHOL_FAIL;
+            return m;
+        }
+        m.chi2 += df_to_d(c2);
+#pragma unroll
+        for (int i = 0; i < 21; ++i) m.p[i] = df_to_d(p[i]);
+        m.st = st;
+        return m;
+    }
     m.ok = fit_step<true, double, M1>(sd, m.p, k, alpha, mass2, ms_on, *sf, hx, hy, hz, m.chi2, m.status, seeded);
     if (m.ok) {
         m.st.x = ff_from_d(sd.x);
@@ -482,7 +519,7 @@ __device__ __forceinline__ bool fit_phase1(int t, const FitArgs &a, const Surf *
                 m.status = status;
                 // k == 1 after the structured seed-hit update: the transport skips its zero blocks
                 m = fp64_step_pd_out_of_line<M1>(m, k, kbd * (double)(-q), mass2d, a.ms_on, &sf, a.hx[h], a.hy[h],
-                                                 a.hz[h], !P0 && k == 1);
+                                                 a.hz[h], !P0 && k == 1, !P0 && k >= 2);
                 st = m.st;
 #pragma unroll
                 for (int i = 0; i < 21; ++i) pd[i] = m.p[i];
