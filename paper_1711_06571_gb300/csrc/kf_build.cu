@@ -148,6 +148,24 @@ __device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[
     int ncand = 0;
     Dir<T> dir;
     if constexpr (M1) dir = direction(st);  // shared by the candidates' second steps
+    // A screen in FP32 before each candidate's FP64 chi2 (mixed path, shared S):
+    // the same forward substitution with the factor rounded to FP32.  A candidate
+    // whose FP32 chi2 exceeds the best FP64 chi2 so far by more than 1% cannot
+    // become the best (the FP32 value is within ~1e-6 relative of the FP64 one),
+    // so its FP64 chi2 is not needed; every decision is still taken on FP64
+    // values, and the choice is the one the full FP64 scan makes.
+    constexpr bool SCREEN = !M1 && sizeof(T) == 4;
+    float sl21 = 0.f, sl31 = 0.f, sl32 = 0.f, si1 = 0.f, si2 = 0.f, si3 = 0.f;
+    if constexpr (SCREEN) {
+        if (shared) {
+            sl21 = d2f(fs.l21);
+            sl31 = d2f(fs.l31);
+            sl32 = d2f(fs.l32);
+            si1 = d2f(fs.i1);
+            si2 = d2f(fs.i2);
+            si3 = d2f(fs.i3);
+        }
+    }
     for (int zb = w.z_lo; zb <= w.z_hi && !capped; ++zb) {
         const int row = zb * KF_NPHI;
         const int first = w.phi_lo, last = w.phi_lo + w.nphi - 1;
@@ -169,6 +187,14 @@ __device__ __forceinline__ void score_own(const Track<T, P> &st, const float pw[
                 }
                 ++ncand;
                 const float4 h = ly.packed[j];
+                if constexpr (SCREEN) {
+                    if (shared && best >= 0) {
+                        const float r0 = resid(h.x, st.x), r1 = resid(h.y, st.y), r2 = resid(h.z, st.z);
+                        const float z2 = fmaf(-sl21, r0, r1), z3 = fmaf(-sl32, z2, fmaf(-sl31, r0, r2));
+                        const float c32 = fmaf(z3 * si3, z3, fmaf(z2 * si2, z2, r0 * si1 * r0));
+                        if (c32 > (float)bchi * 1.01f + 1e-4f) continue;
+                    }
+                }
                 double c2;
                 if constexpr (M1) c2 = cand_chi2_m1(st, dir, pc, sf, alpha, h);
                 else c2 = cand_chi2(st, pw, sf, shared, fs, h);
