@@ -1011,12 +1011,12 @@ int persistent_blocks_per_sm(bool fp64, int block)
 // GeV^-1 above; where the geometry has disks, the stiff tracks of a fit are split
 // further into 16 bins of |cot theta| (tracks of one bin cross barrels and disks
 // in the same sequence) and the 1/pT bins above ip_one are 48 (for building the
-// same bins measured no faster: 2.083 against 2.076 ms).  Inside a bucket the tracks keep their input order
-// warp by warp (ranks from a warp vote; the warps of a block and the blocks
-// reserve their ranges in the order of their atomics): the bucket of the common
-// stiff tracks is then dense in t, and its SoA loads and output stores share
-// 32-byte sectors.
-// The order does not change any track's result.
+// same bins measured no faster: 2.083 against 2.076 ms).  Inside a bucket the
+// tracks keep their input order warp by warp (ranks from a warp vote; the warps
+// of a block and the blocks reserve their ranges in the order of their atomics):
+// the bucket of the common stiff tracks is then dense in t, and its SoA loads and
+// output stores share 32-byte sectors.  The order does not change any track's
+// result.
 //
 // Sorting groups of consecutive tracks instead (so that the per-track SoA outputs
 // of a group share 32-byte sectors) was measured: groups of 4 made the fit 1.9x
