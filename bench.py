@@ -423,12 +423,12 @@ def layout_study(ctx, sizes=(32 * 1024, 256 * 1024, 2 * 1024 * 1024, 8 * 1024 * 
     return dict(workload="P' = J P J^T, FP32, one matrix per thread; J 36 + P 21 floats in, 21 out", rows=out)
 
 
-SERVING_WORKLOAD = ("serving loop: Poisson arrivals, event sizes log-uniform 500-50,000 tracks (16-event pool at the "
-                    "log-uniform quantiles), 17 barrel layers, 20% noise hits per layer, best-hit build + final "
-                    "fit per event, 40 GB device-memory budget")
+SERVING_WORKLOAD = ("serving loop: Poisson arrivals, event sizes log-uniform 500-50,000 tracks (a pool of 64 "
+                    "distinct events drawn at random per request), 17 barrel layers, 20% noise hits per layer, "
+                    "best-hit build + final fit per event, 40 GB device-memory budget")
 
 
-def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0, memory="pinned", zero_copy=True):
+def serving_sweep(ctx, geom, rates=None, pool_size=64, seconds_per_rate=4.0, memory="pinned", zero_copy=True):
     """Events through kf_server: first as fast as they can be submitted (the
     saturation throughput), then Poisson streams at fractions of it.  Latency is
     the library's own submit -> results-in-caller-arrays time per event.
@@ -445,10 +445,12 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0, mem
         a = np.ascontiguousarray(a)
         return torch.from_numpy(a).pin_memory().numpy() if memory == "pinned" else a
 
-    sizes = np.exp(np.linspace(np.log(500), np.log(50000), pool_size)).astype(np.int64)
+    rng = np.random.default_rng(synth.BASE_SEED + 499)
+    sizes = np.exp(rng.uniform(np.log(500), np.log(50000), pool_size)).astype(np.int64)
     pool = []
     for i, sz in enumerate(sizes):
-        ev = synth.gen_event(geom, int(sz), synth.BASE_SEED + 500 + i)
+        # particles simulated on the GPU (the host generator takes seconds per large event)
+        ev = synth.gen_event(geom, int(sz), synth.BASE_SEED + 500 + i, device="cuda")
         L = len(ev["layers"])
         lay = [ev["layers"][l] if l >= 3 else None for l in range(L)]
         xs = [None if ly is None else host(np.asarray(ly["x"], np.float32)) for ly in lay]
@@ -463,6 +465,7 @@ def serving_sweep(ctx, geom, rates=None, pool_size=16, seconds_per_rate=4.0, mem
         # page-locked result buffers allocated once, reused round robin
         L = pool[0][6]
         per = max(p[0] for p in pool) * (4 * L + 48 + 168 + 8 + 4 + 4) + 6 * 64
+        per = -(-per // 64) * 64  # every slot (and so every array in it) 64-byte aligned
         arena = torch.empty(per * ring, dtype=torch.uint8).pin_memory().numpy()
     srv = kf.kf_server_create(ctx, geom, kf.server_params(mem_budget_bytes=40 << 30, max_batches=4,
                                                           max_batch_events=16))

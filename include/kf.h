@@ -16,8 +16,10 @@
  *     message for the last error (kf_ctx_last_error).  Per-track problems never
  *     fail a call: they are reported in the per-track status word (KF_ST_*).
  *   - Arrays marked "device" must be device memory of the context's GPU
- *     (cudaMalloc / torch CUDA tensors); a host pointer there is rejected with
- *     KF_EINVAL.  Arrays marked "host" are host memory.
+ *     (cudaMalloc / torch CUDA tensors), at an address that is a multiple of
+ *     the element size (16 bytes for packed hits, read as 4-float vectors); a
+ *     host pointer or a misaligned one is rejected with KF_EINVAL before
+ *     anything is launched.  Arrays marked "host" are host memory.
  *   - The caller owns every array passed in or out.  The context owns its
  *     scratch (workspace, autotune results, CUDA graphs) and frees it in
  *     kf_ctx_destroy.
@@ -489,7 +491,8 @@ typedef struct {
  *     arena before kf_server_submit returns; KF_EVENT_ZERO_COPY = the caller
  *     keeps them unchanged until the ticket completes and the kernels read them
  *     in place (any host memory on a GPU that reads pageable memory, such as a
- *     Grace-Blackwell board; elsewhere page-locked memory, else they are copied).
+ *     Grace-Blackwell board; elsewhere page-locked memory, else they are copied;
+ *     an array not at a multiple of 4 bytes is copied as well).
  * The small arrays (surface, n_hits and the x, y, z pointer arrays) are read
  * during the call only. */
 #define KF_EVENT_ZERO_COPY 1
@@ -507,9 +510,11 @@ typedef struct {
 } kf_event;
 
 /* Where an event's results go: host arrays the caller keeps alive until the
- * ticket has completed.  A kernel writes them in place where the GPU can reach
- * them (any host memory on a GPU that reads pageable memory, else page-locked
- * memory); otherwise the dispatcher thread copies them from staging.  Any may
+ * ticket has completed.  A kernel writes them in place when all of them are
+ * page-locked and each sits at a multiple of its element size (4 bytes for
+ * the int32 arrays, 8 for the doubles); otherwise the dispatcher thread copies
+ * them from the server's staging (a GPU write into pageable memory pulls every
+ * fresh page through the host, and a misaligned store would fault).  Any may
  * be NULL.
  *   hit_idx [n_layers][n_tracks]: as kf_build_besthit's hit_idx_out.
  *   state [6][n_tracks], cov [21][n_tracks], chi2, ndof: final fit over the

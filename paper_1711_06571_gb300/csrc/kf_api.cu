@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kf_internal.h"
@@ -80,11 +81,14 @@ int cuda_fail(kf_ctx *c, cudaError_t e, const char *what)
     return fail(c, KF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// device memory of GPU dev (where the context's kernels run) or managed memory;
-// another GPU's memory is refused: without peer access the kernels would fault on it
-bool is_device_ptr_on(const void *p, int dev)
+// device memory of GPU dev (where the context's kernels run) or managed memory,
+// at an address that is a multiple of align; another GPU's memory is refused
+// (without peer access the kernels would fault on it), and so is a misaligned
+// address: the kernels load and store whole elements (16-byte float4 for packed
+// hits), and a misaligned element access faults the GPU
+bool is_device_ptr_on(const void *p, int dev, size_t align = 1)
 {
-    if (!p) return false;
+    if (!p || (reinterpret_cast<uintptr_t>(p) & (align - 1))) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
@@ -93,14 +97,28 @@ bool is_device_ptr_on(const void *p, int dev)
     return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
 }
 
-#define NEED_DEV(ptr, name)                                                                 \
-    do {                                                                                    \
-        if (!is_device_ptr_on(ptr, ctx->device)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
+// alignment of the element type a pointer points to (1 for void)
+template <class T>
+constexpr size_t elem_align(const T *)
+{
+    if constexpr (std::is_void_v<T>)
+        return 1;
+    else
+        return alignof(T);
+}
+
+#define NEED_DEV_AL(ptr, name, al)                                                                  \
+    do {                                                                                            \
+        if (!is_device_ptr_on(ptr, ctx->device, al))                                                \
+            return fail(ctx, KF_EINVAL, "%s must be device memory aligned to %zu bytes", name, (size_t)(al)); \
     } while (0)
-#define OPT_DEV(ptr, name)                                                                  \
-    do {                                                                                    \
-        if ((ptr) && !is_device_ptr_on(ptr, ctx->device)) return fail(ctx, KF_EINVAL, "%s must be device memory", name); \
+#define OPT_DEV_AL(ptr, name, al)                                                                   \
+    do {                                                                                            \
+        if ((ptr) && !is_device_ptr_on(ptr, ctx->device, al))                                       \
+            return fail(ctx, KF_EINVAL, "%s must be device memory aligned to %zu bytes", name, (size_t)(al)); \
     } while (0)
+#define NEED_DEV(ptr, name) NEED_DEV_AL(ptr, name, elem_align(ptr))
+#define OPT_DEV(ptr, name) OPT_DEV_AL(ptr, name, elem_align(ptr))
 
 int to_geom(kf_ctx *ctx, const kf_geometry *g, Geom &G)
 {
@@ -827,7 +845,7 @@ int kf_bin_hits(kf_ctx *ctx, int32_t n_hits, const float *x, const float *y, con
         NEED_DEV(y, "y");
         NEED_DEV(z, "z");
         NEED_DEV(perm_out, "perm_out");
-        OPT_DEV(packed_out, "packed_out");
+        OPT_DEV_AL(packed_out, "packed_out", 16);
     }
     cudaStream_t st = (cudaStream_t)stream;
     void *wsp = nullptr;
@@ -858,7 +876,7 @@ int kf_bin_hits_batched(kf_ctx *ctx, int32_t n_segments, const int32_t *segment_
         NEED_DEV(y, "y");
         NEED_DEV(z, "z");
         NEED_DEV(perm_out, "perm_out");
-        OPT_DEV(packed_out, "packed_out");
+        OPT_DEV_AL(packed_out, "packed_out", 16);
     }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t so = ((size_t)(n_segments + 1) * sizeof(int32_t) + 255) & ~(size_t)255;
@@ -931,15 +949,15 @@ static int check_events(kf_ctx *ctx, const kf_geometry *geom, int n_events, int 
             return fail(ctx, KF_EINVAL, "layer %d: surface index out of range", i);
         if (geom->surfaces[L.surface].kind != 0) return fail(ctx, KF_EINVAL, "layer %d: building needs barrels", i);
         if (i % n_layers >= 3 && L.n_hits > 0) {
-            if (!is_device_ptr_on(L.packed, ctx->device) || !is_device_ptr_on(L.offsets, ctx->device))
-                return fail(ctx, KF_EINVAL, "layer %d: packed and offsets must be device memory", i);
-        } else if (i % n_layers >= 3 && !is_device_ptr_on(L.offsets, ctx->device)) {
-            return fail(ctx, KF_EINVAL, "layer %d: offsets must be device memory", i);
+            if (!is_device_ptr_on(L.packed, ctx->device, 16) || !is_device_ptr_on(L.offsets, ctx->device, 4))
+                return fail(ctx, KF_EINVAL, "layer %d: packed and offsets must be device memory (16- and 4-byte aligned)", i);
+        } else if (i % n_layers >= 3 && !is_device_ptr_on(L.offsets, ctx->device, 4)) {
+            return fail(ctx, KF_EINVAL, "layer %d: offsets must be device memory, 4-byte aligned", i);
         }
         if (need_xyz && i % n_layers >= 3 && L.n_hits > 0 &&
-            (!is_device_ptr_on(L.x, ctx->device) || !is_device_ptr_on(L.y, ctx->device) ||
-             !is_device_ptr_on(L.z, ctx->device)))
-            return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory", i);
+            (!is_device_ptr_on(L.x, ctx->device, 4) || !is_device_ptr_on(L.y, ctx->device, 4) ||
+             !is_device_ptr_on(L.z, ctx->device, 4)))
+            return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory, 4-byte aligned", i);
     }
     return KF_OK;
 }
@@ -1116,9 +1134,9 @@ int kf_gather_hits(kf_ctx *ctx, int32_t n_events, int32_t n_layers, const kf_bin
                     KF_MAX_SURFACES);
     for (int i = 0; i < n_events * n_layers; ++i)
         if (i % n_layers >= 3 && layers[i].n_hits > 0 &&
-            (!is_device_ptr_on(layers[i].x, ctx->device) || !is_device_ptr_on(layers[i].y, ctx->device) ||
-             !is_device_ptr_on(layers[i].z, ctx->device)))
-            return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory", i);
+            (!is_device_ptr_on(layers[i].x, ctx->device, 4) || !is_device_ptr_on(layers[i].y, ctx->device, 4) ||
+             !is_device_ptr_on(layers[i].z, ctx->device, 4)))
+            return fail(ctx, KF_EINVAL, "layer %d: x, y, z must be device memory, 4-byte aligned", i);
     const int n = event_offsets[n_events];
     NEED_DEV(offsets_out, "offsets_out");
     if (n == 0) {

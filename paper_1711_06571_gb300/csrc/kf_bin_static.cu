@@ -36,12 +36,13 @@ cudaError_t scratch_address(void **out)
     return cudaSuccess;
 }
 
-// device memory of GPU dev, or managed memory (another GPU's memory is refused:
-// without peer access the kernels would fault on it)
-bool on_device(const void *p, int dev)
+// device memory of GPU dev, or managed memory, at a multiple of align bytes
+// (another GPU's memory is refused: without peer access the kernels would fault
+// on it; so is a misaligned address: the kernels access whole elements)
+bool on_device(const void *p, int dev, uintptr_t align)
 {
     cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) & (align - 1)) || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -60,9 +61,9 @@ extern "C" int kf_bin_hits_static(int32_t n_hits, const float *x, const float *y
         cudaGetLastError();
         return KF_ECUDA;
     }
-    if (!on_device(offsets_out, dev)) return KF_EINVAL;
-    if (n_hits > 0 && (!on_device(x, dev) || !on_device(y, dev) || !on_device(z, dev) || !on_device(perm_out, dev) ||
-                       (packed_out && !on_device(packed_out, dev))))
+    if (!on_device(offsets_out, dev, 4)) return KF_EINVAL;
+    if (n_hits > 0 && (!on_device(x, dev, 4) || !on_device(y, dev, 4) || !on_device(z, dev, 4) ||
+                       !on_device(perm_out, dev, 4) || (packed_out && !on_device(packed_out, dev, 16))))
         return KF_EINVAL;
     void *scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) {

@@ -385,6 +385,14 @@ static const void *device_view(const kf_server *s, const void *p)
     return nullptr;
 }
 
+// device_view of an array of floats, or null where either address is not a
+// multiple of 4 bytes
+static const void *float_view(const kf_server *s, const void *p)
+{
+    const void *v = device_view(s, p);
+    return (reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(v)) & 3 ? nullptr : v;
+}
+
 size_t kf_server::event_bytes(int n, int L, int64_t hb) const
 {
     const size_t nseg = (size_t)(L - 3);
@@ -930,29 +938,35 @@ int kf_server_submit(kf_server *s, const kf_event *ev, const kf_event_result *re
     x.z.assign(L, nullptr);
     // results: written by the kernels into page-locked arrays; pageable arrays get
     // them from staging (a GPU write into pageable memory faults every fresh page
-    // in through the host, which measured slower than a host copy)
+    // in through the host, which measured slower than a host copy), and so do
+    // arrays not aligned to their element size (the kernels store whole 4- and
+    // 8-byte elements, and a misaligned store faults the GPU; the host copy out
+    // of staging takes any alignment)
     {
         const void *r[6] = {x.res.hit_idx, x.res.state, x.res.cov, x.res.chi2, x.res.ndof, x.res.status};
+        const uintptr_t a[6] = {4, 8, 8, 8, 4, 4};
         const void *v[6];
         bool all = true;
         for (int i = 0; i < 6; ++i) {
             v[i] = pinned_view(r[i]);
-            all = all && (!r[i] || v[i]);
+            const bool al_ok = !((reinterpret_cast<uintptr_t>(r[i]) | reinterpret_cast<uintptr_t>(v[i])) & (a[i] - 1));
+            all = all && (!r[i] || (v[i] && al_ok));
         }
         x.direct_out = all;
         x.dres = kf_event_result{(int32_t *)v[0], (double *)v[1], (double *)v[2], (double *)v[3], (int32_t *)v[4],
                                  (uint32_t *)v[5]};
     }
-    // inputs: read in place (zero-copy) where the kernels can reach them, else staged
+    // inputs: read in place (zero-copy) where the kernels can reach them at
+    // float alignment, else staged (the host copy takes any alignment)
     bool in_place = (ev->flags & KF_EVENT_ZERO_COPY) != 0;
     if (in_place) {
-        x.seed_hits = static_cast<const float *>(device_view(s, ev->seed_hits));
+        x.seed_hits = static_cast<const float *>(float_view(s, ev->seed_hits));
         in_place = x.seed_hits != nullptr;
         for (int l = 3; l < L && in_place; ++l) {
             if (ev->n_hits[l] == 0) continue;
-            x.x[l] = static_cast<const float *>(device_view(s, ev->x[l]));
-            x.y[l] = static_cast<const float *>(device_view(s, ev->y[l]));
-            x.z[l] = static_cast<const float *>(device_view(s, ev->z[l]));
+            x.x[l] = static_cast<const float *>(float_view(s, ev->x[l]));
+            x.y[l] = static_cast<const float *>(float_view(s, ev->y[l]));
+            x.z[l] = static_cast<const float *>(float_view(s, ev->z[l]));
             in_place = x.x[l] && x.y[l] && x.z[l];
         }
     }

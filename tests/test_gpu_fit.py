@@ -378,6 +378,44 @@ def test_fit_rejects_host_pointers(ctx):
                   dh["offsets"], dh["layer"], dh["x"], dh["y"], dh["z"])
 
 
+def test_fit_rejects_misaligned_device_pointers(ctx):
+    """Device arrays must sit at a multiple of their element size (the kernels
+    load and store whole elements, and a misaligned access faults the GPU): the
+    entry points refuse them with KF_EINVAL before anything is launched.  The
+    misaligned pointers are byte views a few bytes into device buffers."""
+    g = synth.geometry("barrel10")
+    tk = synth.gen_tracks(g, 10, 1)
+    dh = run.hits_to_device(tk)
+    n = dh["n"]
+    seeds = run.make_seeds(ctx, kf.make_geometry(g), dh)
+    out = run.alloc_fit_out(n)
+    state_buf = torch.empty(48 * n + 8, dtype=torch.uint8, device="cuda")
+    x_buf = torch.empty(dh["x"].numel() * 4 + 4, dtype=torch.uint8, device="cuda")
+    for bad in (dict(out_state=state_buf[4:4 + 48 * n]), dict(x=x_buf[2:2 + 4 * dh["x"].numel()])):
+        args = dict(x=dh["x"], out_state=out["state"])
+        args.update(bad)
+        with pytest.raises(kf.KfError) as ei:
+            kf.kf_fit(ctx, kf.make_geometry(g), None, n, seeds[0], seeds[1], dh["offsets"], dh["layer"],
+                      args["x"], dh["y"], dh["z"], args["out_state"], out["cov"], out["chi2"], out["ndof"],
+                      out["status"])
+        assert ei.value.code == kf.KF_EINVAL and "aligned" in str(ei.value)
+    # packed hits are read as 16-byte vectors: an 8-byte aligned packed_out is refused
+    h = 64
+    hx = torch.zeros(h, device="cuda")
+    perm = torch.empty(h, dtype=torch.int32, device="cuda")
+    offs = torch.empty(kf.KF_NBINS + 1, dtype=torch.int32, device="cuda")
+    pk_buf = torch.empty(16 * h + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(kf.KfError) as ei:
+        kf.kf_bin_hits(ctx, h, hx, hx, hx, 40.0, perm, offs, pk_buf[8:8 + 16 * h])
+    assert ei.value.code == kf.KF_EINVAL
+    # the same calls with aligned arrays still run
+    kf.kf_fit(ctx, kf.make_geometry(g), None, n, seeds[0], seeds[1], dh["offsets"], dh["layer"], dh["x"],
+              dh["y"], dh["z"], out["state"], out["cov"], out["chi2"], out["ndof"], out["status"])
+    kf.kf_bin_hits(ctx, h, hx, hx, hx, 40.0, perm, offs, pk_buf[:16 * h])
+    torch.cuda.synchronize()
+    assert torch.isfinite(out["state"]).all()
+
+
 def test_fit_parity_million_tracks_sampled(ctx, oracle_mod):
     """The full 1,000,000-track, 17-layer workload on the GPU, in the launch the
     benchmark times; the oracle checks a sample of 2,000 tracks."""

@@ -115,6 +115,54 @@ def test_server_alone_and_mixed_match_direct_path(ctx, geom):
         kf.kf_server_destroy(srv)
 
 
+def _pinned_at(a, shift):
+    """A copy of a in page-locked memory at `shift` bytes past a 64-byte boundary."""
+    buf = torch.empty(a.nbytes + 64 + shift, dtype=torch.uint8).pin_memory().numpy()
+    base = (-buf.ctypes.data) % 64 + shift
+    v = buf[base:base + a.nbytes].view(a.dtype).reshape(a.shape)
+    v[...] = a
+    return v
+
+
+def test_server_misaligned_arrays_are_staged(ctx, geom):
+    """Page-locked arrays that are not aligned to their element size (doubles at
+    4 bytes past an 8-byte boundary, floats at 2 bytes past a 4-byte one) are
+    not handed to the kernels: the server stages them through its own aligned
+    buffers, and the results are those of the direct path.  Merged in one batch
+    with an event whose aligned page-locked arrays are read and written in place."""
+    events = _events(geom, [1501, 999, 2000], 90)
+    exp = [direct(ctx, geom, ev) for ev in events]
+    srv = kf.kf_server_create(ctx, geom, kf.server_params(max_batch_events=16, batch_window_ms=2000))
+    try:
+        subs = []
+        for i, ev in enumerate(events):
+            surf, xs, ys, zs, sh = _event_arrays(ev)
+            n, L = ev["n"], len(surf)
+            res = _result_arrays(n, L)
+            if i == 0:  # results misaligned, inputs aligned and read in place
+                res = {k: _pinned_at(v, 4) for k, v in res.items()}
+                xs, ys, zs = ([None if a is None else _pinned_at(a, 0) for a in c] for c in (xs, ys, zs))
+                sh = _pinned_at(sh, 0)
+            elif i == 1:  # inputs misaligned (zero-copy asked for), results aligned
+                res = {k: _pinned_at(v, 0) for k, v in res.items()}
+                xs, ys, zs = ([None if a is None else _pinned_at(a, 2) for a in c] for c in (xs, ys, zs))
+                sh = _pinned_at(sh, 2)
+            else:  # everything aligned and page-locked
+                res = {k: _pinned_at(v, 0) for k, v in res.items()}
+                xs, ys, zs = ([None if a is None else _pinned_at(a, 0) for a in c] for c in (xs, ys, zs))
+                sh = _pinned_at(sh, 0)
+            rc, t = kf.kf_server_submit(srv, n, surf, xs, ys, zs, sh, zero_copy=True, **res)
+            assert rc == kf.KF_OK
+            subs.append((t, res))
+        for (t, res), e, i in zip(subs, exp, range(len(events))):
+            assert kf.kf_server_wait(srv, t, 60000)[0] == kf.KF_OK
+            assert_identical(res, e, f"event {i}")
+        st = kf.kf_server_stats_get(srv)
+        assert st["completed"] == len(events) and st["batches"] == 1 and st["rc"] == kf.KF_OK, st
+    finally:
+        kf.kf_server_destroy(srv)
+
+
 def test_server_many_events_overlapping_batches(ctx, geom):
     """A stream of events of mixed sizes through several batches in flight."""
     events = _events(geom, [400, 2500, 60, 1200, 3100, 900, 10, 2000, 1500, 700], 60)
