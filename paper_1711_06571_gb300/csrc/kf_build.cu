@@ -830,8 +830,13 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
     }
     if (active)
         for (int L = 0; L < 3; ++L) a.hit_idx[(size_t)L * n + t] = -1;
-    // build layers
+    // build layers.  A block barrier per layer keeps the block's four warps in
+    // the same layer step, so that they run the same stretch of the long loop
+    // body and share the instruction cache (instruction fetch was the largest
+    // stall): 1.39 ms for 10 x 20,000 tracks against 1.75 without it.  Every
+    // thread runs every layer (no thread leaves the loop early).
     for (int L = 3; L < a.n_layers; ++L) {
+        __syncthreads();
         const LayerDev ly = lays[L];
         const Surf &sf = s_surf[ly.surface];
         StepKnobs knl = kn;
@@ -1091,7 +1096,11 @@ __global__ void __launch_bounds__(128, 4) ckf_kernel(const Geom g, const CkfArgs
     bool stopped = false;
     if (active && slot == 0)
         for (int L = 0; L < 3; ++L) a.hit_idx[(size_t)L * n + t] = -1;
+    // a block barrier per layer keeps the block's warps in the same layer step
+    // (the instruction cache; as in the best-hit kernel): 4.81 ms for four slots
+    // of 10 x 20,000 seeds against 5.30 without it.  No thread leaves the loop early.
     for (int L = 3; L < a.n_layers; ++L) {
+        __syncthreads();
         const LayerDev ly = lays[L];
         const Surf &sf = s_surf[ly.surface];
         // 1. prediction (a candidate that cannot reach the layer stops, unchanged)
