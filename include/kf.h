@@ -345,7 +345,7 @@ int kf_bin_hits_batched(kf_ctx *ctx, int32_t n_segments, const int32_t *segment_
  * host framework that owns all device memory and hands it out itself, or a
  * real-time (trigger) process whose memory footprint is fixed at start-up.
  * It needs no context: its scratch is a fixed array in device memory,
- * 4 * (2 * KF_STATIC_MAX_HITS + KF_NBINS) bytes (about 2.4 MB), which every
+ * 4 * (5 * KF_STATIC_MAX_HITS + KF_NBINS) bytes (about 5.5 MB), which every
  * GPU that loads the library holds until the process exits.
  *   - Arguments, layouts and results are those of kf_bin_hits; n_hits may be
  *     at most KF_STATIC_MAX_HITS, larger sizes return KF_ESIZE and do nothing.
@@ -356,9 +356,9 @@ int kf_bin_hits_batched(kf_ctx *ctx, int32_t n_segments, const int32_t *segment_
  *     harmless; the first call on a device also loads the library's code
  *     there, so make that first call before any stream capture.
  *   - All calls on a device share the array and it keeps the last call's
- *     contents (nothing in it needs clearing: each call writes every scratch
- *     word it reads).  Calls whose work overlaps on the GPU, from different
- *     streams or threads, race on it; serialise them.
+ *     contents (each call clears the one counter it starts from and writes
+ *     every other scratch word before reading it).  Calls whose work overlaps
+ *     on the GPU, from different streams or threads, race on it; serialise them.
  *   - It calls no allocation routine of any kind. */
 #define KF_STATIC_MAX_HITS 262144
 int kf_bin_hits_static(int32_t n_hits, const float *x, const float *y, const float *z, double half_len,

@@ -8,17 +8,18 @@
 // memory, reserved when the library is loaded onto a device.
 //
 // The array is shared by every call on a device and keeps the last call's
-// contents.  Nothing in it has to start at zero: every scratch word the
-// kernels read is written earlier in the same call (the per-bin counts live
-// in the caller's offsets array, which the call clears).  Calls whose work
-// overlaps on the GPU (two streams, or two threads) race on the array.
+// contents.  Only one word of it has to start at zero, the count of hits keyed
+// in FP64, and the call clears it; every other scratch word the kernels read is
+// written earlier in the same call (the per-bin counts live in the caller's
+// offsets array, which the call clears).  Calls whose work overlaps on the GPU
+// (two streams, or two threads) race on the array.
 #include "kf_internal.h"
 
 namespace {
 
 constexpr int STATIC_MAX_HITS = KF_STATIC_MAX_HITS;
-// key[n] + cursor[KF_NBINS] + tmp[n] int32, as launch_bin lays them out
-constexpr size_t STATIC_SCRATCH_INTS = 2 * (size_t)STATIC_MAX_HITS + KF_NBINS;
+// rec[n] float4 + key[n] + cursor[KF_NBINS] int32, as launch_bin lays them out
+constexpr size_t STATIC_SCRATCH_INTS = 5 * (size_t)STATIC_MAX_HITS + KF_NBINS;
 
 static __device__ __align__(256) int32_t g_bin_scratch[STATIC_SCRATCH_INTS];
 

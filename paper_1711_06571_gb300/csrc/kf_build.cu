@@ -733,9 +733,11 @@ size_t build_seed_scratch_bytes(int n)
 // Pre-pass of the mixed-path best-hit build: the seed fit of every track (its
 // FP64 phase) in a kernel of its own, so that the layer kernel's code holds the
 // layer loop alone (warps at different stages of one kernel share its
-// instruction cache).  Tracks in processing order, as the layer kernel.
+// instruction cache).  Tracks in processing order, as the layer kernel.  Four
+// blocks per SM (128 registers instead of 168 at three): the build call 1.34 ms
+// against 1.38 for 10 x 20,000 tracks.
 template <bool M1>
-__global__ void __launch_bounds__(128) build_seed_kernel(const Geom g, const BuildArgs a)
+__global__ void __launch_bounds__(128, 4) build_seed_kernel(const Geom g, const BuildArgs a)
 {
     __shared__ Surf s_surf[MAX_SURF];
     for (int i = threadIdx.x; i < g.n; i += blockDim.x) s_surf[i] = g.s[i];
@@ -964,7 +966,7 @@ cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp
 // candidate at the end.
 
 // pre-pass: the seed fit, one thread per seed
-__global__ void __launch_bounds__(128) ckf_seed_kernel(const Geom g, const CkfArgs c)
+__global__ void __launch_bounds__(128, 4) ckf_seed_kernel(const Geom g, const CkfArgs c)
 {
     const BuildArgs &a = c.b;
     __shared__ Surf s_surf[MAX_SURF];

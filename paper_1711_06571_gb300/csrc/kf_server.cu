@@ -400,7 +400,7 @@ size_t kf_server::event_bytes(int n, int L, int64_t hb) const
     b += 3 * al(4 * (size_t)hb);                                // x, y, z
     b += al(4 * (size_t)hb) + al(16 * (size_t)hb);              // perm, packed
     b += al(4 * nseg * (KF_NBINS + 1));                         // offsets
-    b += al(4 * (2 * (size_t)hb + nseg * KF_NBINS));            // bin scratch
+    b += al(bin_segments_scratch_bytes((int)hb, (int)nseg));     // bin scratch
     b += 3 * al(12 * (size_t)n) + al(36 * (size_t)n);          // seed hits csr, [9][n]
     b += al(24 * (size_t)n) + al((size_t)n) + al(4 * (size_t)n + 4);  // seeds, q, seed offsets
     b += al(4 * (size_t)L * n) + al(4 * (size_t)n);             // idx, build status
