@@ -67,6 +67,41 @@ def test_seed_parity(ctx, oracle_mod):
     assert same_q.mean() > 0.99
 
 
+def test_seed_hit_choice_at_the_2cm_threshold(ctx, oracle_mod):
+    """The seed-hit rule (hits at least 2 cm apart, transverse) decided exactly as
+    the oracle's FP64 test decides it, also for hits whose distance is within a
+    few ulp of 2 cm (where the kernel's single-precision pre-test defers to FP64).
+    The kernel's seeds from the whole track must equal its seeds from the three
+    hits the oracle picks."""
+    rng = np.random.default_rng(synth.BASE_SEED + 77)
+    n, nh = 4096, 6
+    x0, y0 = rng.uniform(-50, 50, n), rng.uniform(-50, 50, n)
+    hx, hy, hz = np.zeros((n, nh), np.float32), np.zeros((n, nh), np.float32), np.zeros((n, nh), np.float32)
+    hx[:, 0], hy[:, 0] = x0, y0
+    for j in range(1, nh):
+        # distances 2 cm * (1 + k * 2^-24), |k| <= 12: the float grid around the threshold
+        d = 2.0 * (1.0 + rng.integers(-12, 13, n) * 2.0 ** -24)
+        a = rng.uniform(-np.pi, np.pi, n)
+        hx[:, j], hy[:, j] = x0 + d * np.cos(a), y0 + d * np.sin(a)
+    hz[:] = 0.7 * np.arange(nh, dtype=np.float32)
+    d2 = (hx[:, 1].astype(np.float64) - hx[:, 0]) ** 2 + (hy[:, 1].astype(np.float64) - hy[:, 0]) ** 2
+    assert np.sum(np.abs(d2 / 4.0 - 1.0) < 1e-6) > n // 2  # most first distances are in the FP64 band
+    picks = np.array([oracle_mod.seed_hits(hx[t], hy[t]) for t in range(n)])
+    assert len(set(map(tuple, picks[:, 1:]))) > 3  # the rule picks several different hit pairs
+    g = kf.make_geometry(synth.geometry("barrel10"))
+    full = run.hits_to_device(dict(offsets=(np.arange(n + 1) * nh).astype(np.int32), layer=np.zeros(n * nh, np.uint8),
+                                   x=hx.reshape(-1), y=hy.reshape(-1), z=hz.reshape(-1)))
+    rows = np.arange(n)[:, None]
+    three = run.hits_to_device(dict(offsets=(np.arange(n + 1) * 3).astype(np.int32), layer=np.zeros(n * 3, np.uint8),
+                                    x=hx[rows, picks].reshape(-1), y=hy[rows, picks].reshape(-1),
+                                    z=hz[rows, picks].reshape(-1)))
+    st_a, q_a = run.make_seeds(ctx, g, full)
+    st_b, q_b = run.make_seeds(ctx, g, three)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(st_a.cpu().numpy(), st_b.cpu().numpy())
+    np.testing.assert_array_equal(q_a.cpu().numpy(), q_b.cpu().numpy())
+
+
 @pytest.mark.parametrize("precision", [kf.KF_PREC_MIXED, kf.KF_PREC_FP64])
 def test_fit_parity_1000_tracks_10_layers(ctx, oracle_mod, precision):
     g = synth.geometry("barrel10")
