@@ -775,13 +775,22 @@ __global__ void __launch_bounds__(128, 4) build_seed_kernel(const Geom g, const 
     f.alive[t] = alive ? 1 : 0;
 }
 
+// Launch shape of the layer kernel.  Model 0: blocks of 256 threads, two per SM
+// (at most 128 registers a thread: 16 warps to hide the FP64 and memory
+// latencies), so that eight warps step each layer together under the block
+// barrier and share the instruction cache: 1.26 ms per build call for
+// 10 x 20,000 tracks against 1.34 with four blocks of 128 and 1.53 with eight of
+// 64.  M1, measurement model 1 (per-thread scoring): two blocks of 128 (208
+// registers; its larger step spills less), 5.5 ms against 6.7 with one block of
+// 256 and 6.3 with three of 128.
+template <bool M1>
+constexpr int build_block_threads()
+{
+    return M1 ? 128 : 256;
+}
+
 template <bool FP64, bool COOP, bool M1>
-// Model 0: four blocks per SM (at most 128 registers a thread): 16 warps to hide
-// the FP64 and memory latencies of the layer steps (2.05 ms for 10 x 20,000
-// tracks against 2.11 with three blocks, 2.20 with two).  M1, measurement model 1
-// (per-thread scoring): two blocks (255 registers; its larger step spills less),
-// 6.31 ms against 6.94 with three and 7.06 with four.
-__global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, const BuildArgs a)
+__global__ void __launch_bounds__(build_block_threads<M1>(), 2) build_kernel(const Geom g, const BuildArgs a)
 {
     using T = typename sel_t<FP64>::T;
     using P = typename sel_t<FP64>::P;
@@ -932,21 +941,27 @@ __global__ void __launch_bounds__(128, M1 ? 2 : 4) build_kernel(const Geom g, co
 cudaError_t launch_build(const Geom &g, const BuildArgs &a, bool fp64, bool warp_coop, cudaStream_t st)
 {
     if (a.n <= 0) return cudaSuccess;
-    const int b = 128, grid = (a.n + b - 1) / b;
+    const int b = 128, grid = (a.n + b - 1) / b;  // the seed pre-pass
     if (!fp64) {
         if (!a.seed_scratch) return cudaErrorInvalidValue;
         if (a.meas_model == 1) build_seed_kernel<true><<<grid, b, 0, st>>>(g, a);
         else build_seed_kernel<false><<<grid, b, 0, st>>>(g, a);
     }
     if (a.meas_model == 1) {  // per-thread scoring
-        if (fp64) build_kernel<true, false, true><<<grid, b, 0, st>>>(g, a);
-        else build_kernel<false, false, true><<<grid, b, 0, st>>>(g, a);
-    } else if (fp64) {
-        if (warp_coop) build_kernel<true, true, false><<<grid, b, 0, st>>>(g, a);
-        else build_kernel<true, false, false><<<grid, b, 0, st>>>(g, a);
+        constexpr int b1 = build_block_threads<true>();
+        const int grid1 = (a.n + b1 - 1) / b1;
+        if (fp64) build_kernel<true, false, true><<<grid1, b1, 0, st>>>(g, a);
+        else build_kernel<false, false, true><<<grid1, b1, 0, st>>>(g, a);
     } else {
-        if (warp_coop) build_kernel<false, true, false><<<grid, b, 0, st>>>(g, a);
-        else build_kernel<false, false, false><<<grid, b, 0, st>>>(g, a);
+        constexpr int b0 = build_block_threads<false>();
+        const int grid0 = (a.n + b0 - 1) / b0;
+        if (fp64) {
+            if (warp_coop) build_kernel<true, true, false><<<grid0, b0, 0, st>>>(g, a);
+            else build_kernel<true, false, false><<<grid0, b0, 0, st>>>(g, a);
+        } else {
+            if (warp_coop) build_kernel<false, true, false><<<grid0, b0, 0, st>>>(g, a);
+            else build_kernel<false, false, false><<<grid0, b0, 0, st>>>(g, a);
+        }
     }
     return cudaGetLastError();
 }
@@ -1056,10 +1071,18 @@ __device__ __forceinline__ ff shfl_ff(ff v, int src)
     return ff{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
 
-// four blocks per SM (at most 128 registers a thread): 3.15 / 6.27 / 13.0 ms for
-// 2 / 4 / 8 slots on 10 x 20,000 tracks, against 3.24 / 6.43 / 13.7 with three
+// At most 128 registers a thread (16 warps per SM).  Four and eight slots: blocks
+// of 256 threads, two per SM, eight warps stepping each layer together under the
+// block barrier: 4.62 / 10.08 ms on 10 x 20,000 tracks against 4.78 / 10.52 with
+// four blocks of 128; two slots: four blocks of 128 (2.27 ms, against 2.32).
 template <int NS>
-__global__ void __launch_bounds__(128, 4) ckf_kernel(const Geom g, const CkfArgs c)
+constexpr int ckf_block_threads()
+{
+    return NS >= 4 ? 256 : 128;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(ckf_block_threads<NS>(), NS >= 4 ? 2 : 4) ckf_kernel(const Geom g, const CkfArgs c)
 {
     const BuildArgs &a = c.b;
     __shared__ Surf s_surf[MAX_SURF];
@@ -1332,12 +1355,12 @@ cudaError_t launch_ckf(const Geom &g, const CkfArgs &c, cudaStream_t st)
     if (n <= 0) return cudaSuccess;
     ckf_seed_kernel<<<(n + 127) / 128, 128, 0, st>>>(g, c);
     const long long threads = (long long)n * c.n_slots;
-    const int grid = (int)((threads + 127) / 128);
+    auto grid = [threads](int b) { return (int)((threads + b - 1) / b); };
     switch (c.n_slots) {
-    case 1: ckf_kernel<1><<<grid, 128, 0, st>>>(g, c); break;
-    case 2: ckf_kernel<2><<<grid, 128, 0, st>>>(g, c); break;
-    case 4: ckf_kernel<4><<<grid, 128, 0, st>>>(g, c); break;
-    case 8: ckf_kernel<8><<<grid, 128, 0, st>>>(g, c); break;
+    case 1: ckf_kernel<1><<<grid(ckf_block_threads<1>()), ckf_block_threads<1>(), 0, st>>>(g, c); break;
+    case 2: ckf_kernel<2><<<grid(ckf_block_threads<2>()), ckf_block_threads<2>(), 0, st>>>(g, c); break;
+    case 4: ckf_kernel<4><<<grid(ckf_block_threads<4>()), ckf_block_threads<4>(), 0, st>>>(g, c); break;
+    case 8: ckf_kernel<8><<<grid(ckf_block_threads<8>()), ckf_block_threads<8>(), 0, st>>>(g, c); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
