@@ -428,6 +428,33 @@ SERVING_WORKLOAD = ("serving loop: Poisson arrivals, event sizes log-uniform 500
                     "best-hit build + final fit per event, 40 GB device-memory budget")
 
 
+def result_arrays_layout(n, L):
+    """(name, shape, dtype) of an event's result arrays, as kf_server_submit takes them."""
+    return (("hit_idx", (L, n), np.int32), ("state", (6, n), np.float64), ("cov", (21, n), np.float64),
+            ("chi2", (n,), np.float64), ("ndof", (n,), np.int32), ("status", (n,), np.uint32))
+
+
+def result_slot_bytes(max_n, L):
+    """Bytes of one slot of the serving client's ring of result buffers: the
+    arrays of an event of up to max_n tracks, each at a 64-byte boundary within
+    the slot, and the slot itself a multiple of 64 bytes, so that every array of
+    every slot is aligned to its element size when the ring's base is (the
+    server writes page-locked results in place only at that alignment)."""
+    return sum((int(np.prod(sh)) * np.dtype(dt).itemsize + 63) // 64 * 64
+               for _, sh, dt in result_arrays_layout(max_n, L))
+
+
+def result_views(ring_buf, slot_bytes, slot, n, L):
+    """The result arrays of an event of n tracks in slot `slot` of ring_buf (a
+    flat uint8 array of whole slots)."""
+    out, off = {}, slot * slot_bytes
+    for k, sh, dt in result_arrays_layout(n, L):
+        nb = int(np.prod(sh)) * np.dtype(dt).itemsize
+        out[k] = ring_buf[off:off + nb].view(dt).reshape(sh)
+        off += (nb + 63) // 64 * 64
+    return out
+
+
 def serving_sweep(ctx, geom, rates=None, pool_size=64, seconds_per_rate=4.0, memory="pinned", zero_copy=True):
     """Events through kf_server: first as fast as they can be submitted (the
     saturation throughput), then Poisson streams at fractions of it.  Latency is
@@ -461,26 +488,17 @@ def serving_sweep(ctx, geom, rates=None, pool_size=64, seconds_per_rate=4.0, mem
     max_events = 600
     ring = 96  # result buffers of the client: at most this many requests outstanding
     arena = None
+    per = result_slot_bytes(max(p[0] for p in pool), pool[0][6])
     if memory == "pinned":
         # page-locked result buffers allocated once, reused round robin
-        L = pool[0][6]
-        per = max(p[0] for p in pool) * (4 * L + 48 + 168 + 8 + 4 + 4) + 6 * 64
-        per = -(-per // 64) * 64  # every slot (and so every array in it) 64-byte aligned
         arena = torch.empty(per * ring, dtype=torch.uint8).pin_memory().numpy()
     srv = kf.kf_server_create(ctx, geom, kf.server_params(mem_budget_bytes=40 << 30, max_batches=4,
                                                           max_batch_events=16))
 
     def results(n, L, slot):
-        shapes = (("hit_idx", (L, n), np.int32), ("state", (6, n), np.float64), ("cov", (21, n), np.float64),
-                  ("chi2", (n,), np.float64), ("ndof", (n,), np.int32), ("status", (n,), np.uint32))
         if arena is None:
-            return {k: np.empty(sh, dt) for k, sh, dt in shapes}
-        out, off = {}, (slot % ring) * (len(arena) // ring)
-        for k, sh, dt in shapes:
-            nb = int(np.prod(sh)) * np.dtype(dt).itemsize
-            out[k] = arena[off:off + nb].view(dt).reshape(sh)
-            off += (nb + 63) // 64 * 64
-        return out
+            return {k: np.empty(sh, dt) for k, sh, dt in result_arrays_layout(n, L)}
+        return result_views(arena, per, slot % ring, n, L)
 
     def stream(rate, n_ev, seed):
         t_arr, _ = synth.serving_stream(seed, n_ev, rate if rate else 1.0)

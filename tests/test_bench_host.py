@@ -46,3 +46,31 @@ def test_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     s = bench.ClockSampler(0)
     s.start()
     assert s.stop() is None
+
+
+def test_serving_result_ring_keeps_every_array_aligned():
+    """The serving client's ring of page-locked result buffers: every array of
+    every slot at a multiple of its element size and inside its slot, for the
+    largest event and smaller ones (an odd largest track count once gave slots
+    4 bytes off an 8-byte boundary; the server now stages such arrays, and the
+    ring no longer produces them)."""
+    import numpy as np
+    for max_n, L in ((47015, 17), (50000, 17), (1, 4), (12345, 9)):
+        per = bench.result_slot_bytes(max_n, L)
+        assert per % 64 == 0
+        ring = 5
+        raw = np.zeros(per * ring + 64, np.uint8)
+        base = (-raw.ctypes.data) % 64
+        buf = raw[base:base + per * ring]
+        for slot in range(ring):
+            for n in (max_n, max(1, max_n // 3), 1):
+                views = bench.result_views(buf, per, slot, n, L)
+                assert [k for k, _, _ in bench.result_arrays_layout(n, L)] == list(views)
+                ends = []
+                for k, a in views.items():
+                    assert a.flags.aligned and a.ctypes.data % a.dtype.itemsize == 0, (max_n, L, slot, n, k)
+                    off = a.ctypes.data - buf.ctypes.data
+                    assert slot * per <= off and off + a.nbytes <= (slot + 1) * per
+                    ends.append((off, off + a.nbytes))
+                ends.sort()
+                assert all(e0[1] <= e1[0] for e0, e1 in zip(ends, ends[1:]))  # no overlap
