@@ -288,7 +288,9 @@ def build_bench(ctx, geom, steps, warmup, n_events=10, n_tracks=20000, meas_mode
                 ms_per_step=t_step, bin_and_seed_ms=t_bin, build_launch_ms=t_build,
                 build_kernel_steps_per_s=units / (t_build * 1e-3), hits_binned=H, tracks=n,
                 steps_measured=steps, fraction_of_steps_with_a_hit=found, true_hit_efficiency=eff_best,
-                gpu_launches_per_step=5 + 1 + 4, combinatorial=ckf)
+                # binning (key, FP64 keys, scan, scatter, rank), seed estimate, order pass (3),
+                # seed pre-pass, layer kernel
+                gpu_launches_per_step=5 + 1 + 3 + 2, combinatorial=ckf)
 
 
 NONIDEAL_WORKLOAD = ("non-ideal barrel (Sec. 4.1): 17 layers whose modules sit at alternating radii "
